@@ -1,0 +1,234 @@
+/*
+ * snn.h -- C ABI of a clock-driven GB300 (sm_103a) simulator of the Potjans-Diesmann
+ * cortical microcircuit, following the model and the push-based step loop of
+ * Lindqvist & Podobas, "Fast Algorithms for Spiking Neural Network Simulation with
+ * FPGAs" (arXiv 2405.02019).
+ *
+ * What one simulation step computes (all on the GPU, no host round trip):
+ *   - thalamic drive: a Poisson count T per neuron with mean nu_th K dt (§2.2, the
+ *     sentence after Eq. ref);
+ *   - the exact-integration LIF update with refractoriness, threshold and reset
+ *     (§2.2, Eqs. mem, psc, ref; Listing push of §3.1);
+ *   - deferred push delivery (Listing push2, §3.1) of every spike through the
+ *     sender's synapses into a 64-row wrap-around ring W[(t + d) mod 64][target]
+ *     (§3.2), read and cleared by the target at step t + d.
+ *
+ * Numerics (plain mode): FP32 neuron state with every product and sum rounded
+ * separately (no FMA); synaptic input accumulated as int32 counts of 2^-12 pA, so
+ * delivery order cannot change the result; FP64 only on the host for the
+ * propagators.  The raster is reproducible bit for bit.
+ *
+ * Conventions for every function:
+ *   - returns an snn_status (SNN_OK = 0); no exceptions cross the ABI, nothing exits;
+ *     snn_last_error() gives a message for the calling thread's last failure;
+ *   - host pointers are read during the call only, unless stated otherwise;
+ *   - device memory is owned by the caller: one arena of snn_sizes.arena_bytes bytes
+ *     (256-byte aligned), which must outlive the network handle; the library never
+ *     allocates device memory itself;
+ *   - `cuda_stream` is a cudaStream_t (NULL = legacy default stream); calls on one
+ *     handle must not run concurrently.
+ */
+#ifndef SNN_H
+#define SNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SNN_ABI_VERSION 1u
+#define SNN_MAX_POPS 8       /* populations per circuit (the microcircuit has 8) */
+#define SNN_MAX_OVERRIDES 4  /* per-pair amplitude overrides (the doubled L4E->L23E pathway) */
+#define SNN_D_MAX 64         /* ring rows; delays are whole steps in [1, SNN_D_MAX-1] (§3.2) */
+#define SNN_FX_SHIFT 12      /* synaptic input unit: 2^-SNN_FX_SHIFT pA */
+#define SNN_POISSON_KMAX 24  /* entries of a thalamic Poisson threshold table */
+
+typedef enum snn_status {
+    SNN_OK = 0,
+    SNN_EINVAL = 1,    /* invalid argument or specification */
+    SNN_ENOMEM = 2,    /* host allocation failed, or the device arena is too small */
+    SNN_ECUDA = 3,     /* a CUDA runtime call failed */
+    SNN_EOVERFLOW = 4, /* the device raster filled before it was read (sticky) */
+    SNN_ETIMEOUT = 5,  /* reserved for bounded device waits */
+    SNN_ESTATE = 6,    /* call out of order (e.g. after a sticky device error) */
+    SNN_ENOTSUP = 7    /* feature not available in this build */
+} snn_status;
+
+/*
+ * Parameters of the circuit model: Tables params, params2 and params3 of §2.2.
+ * Units: ms, pF, mV, Hz.  conn_p[target][source] is the connection probability of
+ * a (source, target) neuron pair.  Synaptic amplitude and delay laws are
+ * Gaussians of the *source* population; an override replaces the amplitude law
+ * of one (source, target) population pair.
+ */
+typedef struct snn_model {
+    int32_t n_pops;
+    int32_t n_overrides;
+    double dt_ms, C_m_pF, tau_m_ms, tau_ref_ms, tau_syn_ms;
+    double u_rest_mV, u_reset_mV, u_thr_mV, nu_th_hz, w_ext_mV;
+    int64_t n_full[SNN_MAX_POPS];   /* population sizes at scale 1 */
+    double k_ext[SNN_MAX_POPS];     /* thalamic in-degree K per neuron */
+    double u0_mean_mV[SNN_MAX_POPS], u0_sd_mV[SNN_MAX_POPS];
+    double w_mean_mV[SNN_MAX_POPS], w_sd_mV[SNN_MAX_POPS];
+    double d_mean_ms[SNN_MAX_POPS], d_sd_ms[SNN_MAX_POPS];
+    double conn_p[SNN_MAX_POPS][SNN_MAX_POPS];
+    int32_t ovr_source[SNN_MAX_OVERRIDES], ovr_target[SNN_MAX_OVERRIDES];
+    double ovr_w_mean_mV[SNN_MAX_OVERRIDES], ovr_w_sd_mV[SNN_MAX_OVERRIDES];
+} snn_model;
+
+/*
+ * A network given edge by edge instead of sampled from the model (hand-built test
+ * circuits, or any user topology).  Neuron dynamics and thalamic drive still come
+ * from `model`; neurons [pop_offsets[b], pop_offsets[b+1]) belong to population b
+ * (pop_offsets[0] = 0, pop_offsets[model.n_pops] = n_neurons).  Weights are int32
+ * counts of 2^-12 pA, delays whole steps in [1, 63], u0 the initial membrane
+ * potential relative to rest (mV).
+ */
+typedef struct snn_custom_net {
+    int64_t n_neurons;
+    int64_t n_synapses;
+    const int32_t *pre;
+    const int32_t *post;
+    const int32_t *w_fx;
+    const uint8_t *delay;
+    const float *u0;
+    int64_t pop_offsets[SNN_MAX_POPS + 1];
+} snn_custom_net;
+
+/*
+ * What to simulate.
+ *   scale_n_permille / scale_k_permille: population sizes N_b = round_half_up(N_full_b *
+ *     scale_n / 1000); pair counts K_ab = round(p[b][a] * (N_full_a * scale_k / 1000) * N_b),
+ *     the paper's expected count N_pre N_post p (§2.2);
+ *   seed: network, initial-state and thalamic streams (Philox4x64-10);
+ *   steps_per_graph: steps captured in one CUDA graph (0 = 1000);
+ *   raster_capacity: spikes the device holds between reads (0 = 1<<24);
+ *   deliver_blocks: CTAs of the delivery kernel (0 = 2 per SM);
+ *   custom: NULL, or an explicit network (then the scales are ignored);
+ *   n_threads: host threads for network construction (0 = all cores).
+ */
+typedef struct snn_spec {
+    uint32_t abi_version; /* must be SNN_ABI_VERSION */
+    int32_t scale_n_permille;
+    int32_t scale_k_permille;
+    int32_t steps_per_graph;
+    uint64_t seed;
+    int64_t raster_capacity;
+    int32_t deliver_blocks;
+    int32_t n_threads;
+    snn_model model;
+    const snn_custom_net *custom;
+} snn_spec;
+
+/* Sizes for a spec.  arena_bytes is the device arena snn_build_network needs
+ * (an upper bound: rows are padded after sampling). */
+typedef struct snn_sizes {
+    uint64_t arena_bytes;
+    int64_t n_neurons;
+    int64_t n_neurons_padded;     /* ring row stride: n_neurons rounded up to 128 */
+    int64_t n_synapses;           /* synapses (exact) */
+    int64_t n_synapses_padded_max;
+    int64_t raster_capacity;
+} snn_sizes;
+
+/* Byte offsets of the device buffers inside the arena (for inspection).  Layouts:
+ * U, I float[n_neurons_padded]; R uint8[n_neurons_padded] (refractory steps left);
+ * ring int32[64][n_neurons_padded]; row_ptr int64[n_neurons+1] into the padded
+ * synapse arrays; syn_tgt, syn_w int32[n_synapses_padded], syn_delay uint8[...]
+ * (rows sorted by delay, each padded to a multiple of 4 with zero-weight entries);
+ * rast_neuron, rast_step int32[raster_capacity]. */
+typedef struct snn_layout {
+    uint64_t ctl, U, I, R, ring, row_ptr, syn_tgt, syn_w, syn_delay, rast_neuron, rast_step, params;
+    int64_t n_neurons_padded;
+    int64_t n_synapses_padded;
+} snn_layout;
+
+/* Constants and counters of a built network. */
+typedef struct snn_info {
+    int64_t n_neurons;
+    int64_t n_synapses;
+    int64_t n_synapses_padded;
+    int64_t t;            /* steps enqueued so far */
+    int64_t spikes_read;  /* spikes moved to the host so far */
+    int64_t events_read;  /* recurrent synaptic events (sum of the senders' out-degrees) of those */
+    int32_t n_pops;
+    int32_t t_ref_steps;
+    int64_t pop_offsets[SNN_MAX_POPS + 1];
+    double w_f, p11, p22, p21;     /* FP64 constants of §2.2 */
+    float p11_f32, p21_f32, p22_f32, theta_f32, u_reset_f32;
+    int32_t w_ext_fx;              /* thalamic PSC, 2^-12 pA units */
+    uint64_t poisson_thresholds[SNN_MAX_POPS][SNN_POISSON_KMAX];
+    int32_t max_row_length;
+    int32_t chunks_per_row;
+    int32_t steps_per_graph;
+    int32_t deliver_blocks;
+    uint32_t device_error;         /* sticky device error bits (1 = raster overflow) */
+    int32_t reserved;
+} snn_info;
+
+typedef struct snn_net snn_net;
+
+/* Host only (no GPU needed).  Validates `spec` and fills `out`.
+ * Errors: SNN_EINVAL for an invalid spec (message via snn_last_error). */
+int snn_query_sizes(const snn_spec *spec, snn_sizes *out);
+
+/* Builds the network on the host (constants of §2.2 in FP64; every synapse of
+ * every population pair drawn with replacement, §2.2; rows grouped by sender and
+ * sorted by delay, the indexed store of §3.5), uploads it into the caller's device
+ * arena on `cuda_stream`, initialises U from the u_init Gaussians, I = R = 0, the
+ * ring to zero, and captures the step loop into a CUDA graph.  Returns when the
+ * upload is complete.  On success *out owns host-side state; free it with
+ * snn_destroy.  Errors: SNN_EINVAL (spec), SNN_ENOMEM (host memory, or arena_bytes
+ * below snn_query_sizes' figure), SNN_ECUDA. */
+int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_bytes, void *cuda_stream,
+                      snn_net **out);
+
+/* Enqueues n_steps steps (Listing push / push2 of §3.1; one step = dt) on
+ * `cuda_stream` and returns without waiting.  n_steps = 0 is a no-op.
+ * Errors: SNN_EINVAL (n_steps < 0), SNN_ESTATE (after a sticky device error),
+ * SNN_ECUDA. */
+int snn_step_n(snn_net *net, int64_t n_steps, void *cuda_stream);
+
+/* Waits for the enqueued steps, moves the device raster to the host and returns
+ * spikes not yet returned, ordered by (step, neuron).  steps/neurons are
+ * caller-allocated arrays of `capacity` entries; *n_written receives how many were
+ * written (the rest stay for the next call).  With steps == neurons == NULL it only
+ * reports the number of unread spikes.  Errors: SNN_EOVERFLOW if the raster filled
+ * between reads (the dynamics after that point are invalid), SNN_ECUDA. */
+int snn_read_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t capacity, int64_t *n_written);
+
+/* Waits for the enqueued steps and returns the mean firing rate (Hz) of each
+ * population over steps [t_begin, t_end) (§4.1's rate statistic), from all spikes
+ * recorded so far.  pop_rates_hz has n_pops entries; neuron_counts (n_neurons
+ * entries, may be NULL) receives per-neuron spike counts in the window.
+ * Errors: SNN_EINVAL (empty or negative window), SNN_EOVERFLOW, SNN_ECUDA. */
+int snn_read_rates(snn_net *net, int64_t t_begin, int64_t t_end, double *pop_rates_hz, int32_t *neuron_counts);
+
+/* Fills `out` with the network's constants and counters (host only, no wait). */
+int snn_get_info(const snn_net *net, snn_info *out);
+
+/* Fills `out` with the arena layout (host only). */
+int snn_get_layout(const snn_net *net, snn_layout *out);
+
+/* Runs n_steps steps kernel by kernel (no graph), timing each kernel with CUDA
+ * events on `cuda_stream`, and returns after they finish.  ms_update / ms_deliver
+ * receive the summed milliseconds of the update and delivery kernels.  Same
+ * dynamics as snn_step_n.  Errors as snn_step_n. */
+int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *ms_update, double *ms_deliver);
+
+/* Releases host-side state (not the caller's arena).  NULL is ignored. */
+void snn_destroy(snn_net *net);
+
+/* Static description of a status code. */
+const char *snn_strerror(int code);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *snn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNN_H */

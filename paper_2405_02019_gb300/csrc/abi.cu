@@ -1,0 +1,489 @@
+// C ABI of the simulator: network setup, the CUDA-graph step engine and raster readout.
+//
+// The step engine captures `steps_per_graph` steps (each: k_update then k_deliver,
+// the two phases of Listing push2, §3.1) plus one counter advance into a CUDA graph
+// at build time and replays it; remainders are launched directly.  The step index
+// lives on the device (Ctl::t_base), so a replay needs no host-side parameter update
+// and no host round trip happens between steps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.hpp"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+#define SNN_CUDA_TRY(expr)                                                                     \
+    do {                                                                                       \
+        cudaError_t err_ = (expr);                                                             \
+        if (err_ != cudaSuccess)                                                               \
+            return fail(SNN_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(err_));      \
+    } while (0)
+
+}  // namespace
+
+struct snn_net {
+    snn_spec spec{};
+    snn::Constants c{};
+    snn::Layout L{};
+    snn::StepArgs args{};
+    int64_t n = 0, npad = 0, n_syn = 0, n_syn_padded = 0;
+    int32_t max_row = 0, chunks_per_row = 1;
+    std::vector<int64_t> pop_off;
+    std::vector<int32_t> out_degree;
+    uint8_t *arena = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    int update_grid = 0;
+    int deliver_grid = 0;
+    int steps_per_graph = 0;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaEvent_t ev_done = nullptr;
+    bool ev_recorded = false;
+    int64_t t = 0;
+    uint32_t device_error = 0;
+    // drained raster, ordered by (step, neuron)
+    std::vector<int32_t> hist_t, hist_i;
+    int64_t read_pos = 0;
+    int64_t events_read = 0;
+    int32_t *pin_nrn = nullptr, *pin_t = nullptr;
+    int64_t pin_cap = 0;
+};
+
+namespace {
+
+int launch_steps_direct(snn_net *net, int64_t m, cudaStream_t st)
+{
+    for (int64_t k = 0; k < m; ++k) {
+        snn::launch_update(net->args, static_cast<int>(k), net->update_grid, st);
+        snn::launch_deliver(net->args, static_cast<int>(k), net->deliver_grid, st);
+    }
+    snn::launch_advance(net->args.ctl, m, st);
+    SNN_CUDA_TRY(cudaGetLastError());
+    return SNN_OK;
+}
+
+int capture_graph(snn_net *net)
+{
+    SNN_CUDA_TRY(cudaStreamCreateWithFlags(&net->capture_stream, cudaStreamNonBlocking));
+    SNN_CUDA_TRY(cudaStreamBeginCapture(net->capture_stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < net->steps_per_graph; ++k) {
+        snn::launch_update(net->args, k, net->update_grid, net->capture_stream);
+        snn::launch_deliver(net->args, k, net->deliver_grid, net->capture_stream);
+    }
+    snn::launch_advance(net->args.ctl, net->steps_per_graph, net->capture_stream);
+    cudaError_t launch_err = cudaGetLastError();
+    cudaGraph_t g = nullptr;
+    cudaError_t end_err = cudaStreamEndCapture(net->capture_stream, &g);
+    if (launch_err != cudaSuccess) return fail(SNN_ECUDA, std::string("capture: ") + cudaGetErrorString(launch_err));
+    if (end_err != cudaSuccess) return fail(SNN_ECUDA, std::string("end capture: ") + cudaGetErrorString(end_err));
+    net->graph = g;
+    SNN_CUDA_TRY(cudaGraphInstantiate(&net->graph_exec, net->graph, 0));
+    return SNN_OK;
+}
+
+int wait_done(snn_net *net)
+{
+    if (net->ev_recorded) SNN_CUDA_TRY(cudaEventSynchronize(net->ev_done));
+    return SNN_OK;
+}
+
+// Move the device raster to the host history and reset the device cursor.
+int drain(snn_net *net)
+{
+    int rc = wait_done(net);
+    if (rc) return rc;
+    snn::Ctl ctl;
+    SNN_CUDA_TRY(cudaMemcpy(&ctl, net->arena + net->L.ctl, sizeof(ctl), cudaMemcpyDeviceToHost));
+    net->device_error |= ctl.err;
+    const int64_t cap = net->L.rast_cap;
+    const int64_t cnt = std::min<int64_t>(ctl.cursor, cap);
+    if (cnt > 0) {
+        if (cnt > net->pin_cap) {
+            if (net->pin_nrn) cudaFreeHost(net->pin_nrn);
+            if (net->pin_t) cudaFreeHost(net->pin_t);
+            net->pin_nrn = net->pin_t = nullptr;
+            net->pin_cap = 0;
+            const int64_t want = std::max<int64_t>(cnt, 1 << 16);
+            SNN_CUDA_TRY(cudaMallocHost(&net->pin_nrn, sizeof(int32_t) * want));
+            SNN_CUDA_TRY(cudaMallocHost(&net->pin_t, sizeof(int32_t) * want));
+            net->pin_cap = want;
+        }
+        SNN_CUDA_TRY(cudaMemcpy(net->pin_nrn, net->arena + net->L.rast_nrn, sizeof(int32_t) * cnt,
+                                cudaMemcpyDeviceToHost));
+        SNN_CUDA_TRY(cudaMemcpy(net->pin_t, net->arena + net->L.rast_t, sizeof(int32_t) * cnt,
+                                cudaMemcpyDeviceToHost));
+        std::vector<int64_t> key(cnt);
+        for (int64_t j = 0; j < cnt; ++j)
+            key[j] = (static_cast<int64_t>(net->pin_t[j]) << 32) | static_cast<uint32_t>(net->pin_nrn[j]);
+        std::sort(key.begin(), key.end());
+        const size_t base = net->hist_t.size();
+        net->hist_t.resize(base + cnt);
+        net->hist_i.resize(base + cnt);
+        for (int64_t j = 0; j < cnt; ++j) {
+            net->hist_t[base + j] = static_cast<int32_t>(key[j] >> 32);
+            const int32_t i = static_cast<int32_t>(key[j] & 0xFFFFFFFFll);
+            net->hist_i[base + j] = i;
+            net->events_read += net->out_degree[i];
+        }
+    }
+    if (ctl.cursor != 0) {
+        uint32_t zero[3] = {0, 0, 0};  // cursor, step_begin[0], step_begin[1]
+        SNN_CUDA_TRY(cudaMemcpy(net->arena + net->L.ctl + offsetof(snn::Ctl, cursor), zero, sizeof(zero),
+                                cudaMemcpyHostToDevice));
+    }
+    if (net->device_error & snn::kErrRaster)
+        return fail(SNN_EOVERFLOW, "device raster filled before it was read; raise raster_capacity");
+    return SNN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *snn_strerror(int code)
+{
+    switch (code) {
+    case SNN_OK: return "ok";
+    case SNN_EINVAL: return "invalid argument";
+    case SNN_ENOMEM: return "out of memory";
+    case SNN_ECUDA: return "CUDA error";
+    case SNN_EOVERFLOW: return "raster overflow";
+    case SNN_ETIMEOUT: return "device wait timed out";
+    case SNN_ESTATE: return "invalid state";
+    case SNN_ENOTSUP: return "not supported";
+    default: return "unknown status";
+    }
+}
+
+const char *snn_last_error(void) { return g_last_error.c_str(); }
+
+int snn_query_sizes(const snn_spec *spec, snn_sizes *out)
+{
+    if (!spec || !out) return fail(SNN_EINVAL, "null argument");
+    try {
+        std::string why;
+        if (!snn::validate_spec(*spec, why)) return fail(SNN_EINVAL, why);
+        const snn::Layout L = snn::make_layout(*spec);
+        out->arena_bytes = L.total;
+        out->n_neurons = snn::count_neurons(*spec);
+        out->n_neurons_padded = L.npad;
+        out->n_synapses = snn::count_synapses(*spec);
+        out->n_synapses_padded_max = L.syn_padded_max;
+        out->raster_capacity = L.rast_cap;
+    } catch (const std::bad_alloc &) {
+        return fail(SNN_ENOMEM, "host allocation failed");
+    }
+    return SNN_OK;
+}
+
+int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_bytes, void *cuda_stream,
+                      snn_net **out)
+{
+    if (!spec || !out || !dev_arena) return fail(SNN_EINVAL, "null argument");
+    *out = nullptr;
+    if (reinterpret_cast<uintptr_t>(dev_arena) % 256 != 0) return fail(SNN_EINVAL, "arena not 256-byte aligned");
+    std::string why;
+    if (!snn::validate_spec(*spec, why)) return fail(SNN_EINVAL, why);
+    cudaPointerAttributes attr;
+    SNN_CUDA_TRY(cudaPointerGetAttributes(&attr, dev_arena));
+    if (attr.type != cudaMemoryTypeDevice) return fail(SNN_EINVAL, "arena is not device memory");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+    snn_net *net = nullptr;
+    try {
+        net = new snn_net();
+        net->spec = *spec;
+        net->spec.custom = nullptr;
+        net->L = snn::make_layout(*spec);
+        if (arena_bytes < net->L.total) {
+            delete net;
+            return fail(SNN_ENOMEM, "arena smaller than snn_query_sizes().arena_bytes");
+        }
+        snn::compute_constants(spec->model, net->c);
+        snn::HostNetwork hn;
+        if (!snn::build_host_network(*spec, net->c, hn, why)) {
+            delete net;
+            return fail(SNN_EINVAL, why);
+        }
+        net->arena = static_cast<uint8_t *>(dev_arena);
+        net->device = attr.device;
+        net->n = hn.n;
+        net->npad = hn.npad;
+        net->n_syn = hn.n_syn;
+        net->n_syn_padded = hn.n_syn_padded;
+        net->max_row = hn.max_row;
+        net->chunks_per_row = std::max(1, (hn.max_row + snn::kChunk - 1) / snn::kChunk);
+        net->pop_off = hn.pop_off;
+        net->out_degree = std::move(hn.out_degree);
+
+        int rc = SNN_OK;
+        auto cuda_ok = [&](cudaError_t e, const char *what) {
+            if (e != cudaSuccess && rc == SNN_OK) rc = fail(SNN_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+            return e == cudaSuccess;
+        };
+        cuda_ok(cudaSetDevice(net->device), "cudaSetDevice");
+        cuda_ok(cudaDeviceGetAttribute(&net->num_sms, cudaDevAttrMultiProcessorCount, net->device), "attr");
+        uint8_t *A = net->arena;
+        const snn::Layout &L = net->L;
+        snn::StaticTables tabs{};
+        std::memcpy(tabs.thresholds, net->c.thresholds, sizeof(tabs.thresholds));
+        for (int b = 0; b <= SNN_MAX_POPS; ++b) tabs.pop_off[b] = b < (int)hn.pop_off.size() ? hn.pop_off[b] : hn.n;
+        tabs.n_pops = spec->model.n_pops;
+        std::vector<float> u0(net->npad, 0.0f);
+        std::copy(hn.u0.begin(), hn.u0.end(), u0.begin());
+        cuda_ok(cudaMemsetAsync(A + L.ctl, 0, sizeof(snn::Ctl), st), "memset ctl");
+        cuda_ok(cudaMemcpyAsync(A + L.tables, &tabs, sizeof(tabs), cudaMemcpyHostToDevice, st), "tables");
+        cuda_ok(cudaMemcpyAsync(A + L.U, u0.data(), 4 * net->npad, cudaMemcpyHostToDevice, st), "U");
+        cuda_ok(cudaMemsetAsync(A + L.I, 0, 4 * net->npad, st), "I");
+        cuda_ok(cudaMemsetAsync(A + L.R, 0, net->npad, st), "R");
+        cuda_ok(cudaMemsetAsync(A + L.ring, 0, uint64_t{4} * snn::kDMax * net->npad, st), "ring");
+        cuda_ok(cudaMemcpyAsync(A + L.row_ptr, hn.row_ptr.data(), 8 * (net->n + 1), cudaMemcpyHostToDevice, st),
+                "row_ptr");
+        if (net->n_syn_padded > 0) {
+            cuda_ok(cudaMemcpyAsync(A + L.syn_tgt, hn.tgt.data(), 4 * net->n_syn_padded, cudaMemcpyHostToDevice, st),
+                    "tgt");
+            cuda_ok(cudaMemcpyAsync(A + L.syn_w, hn.w.data(), 4 * net->n_syn_padded, cudaMemcpyHostToDevice, st), "w");
+            cuda_ok(cudaMemcpyAsync(A + L.syn_d, hn.d.data(), net->n_syn_padded, cudaMemcpyHostToDevice, st), "d");
+        }
+        cuda_ok(cudaStreamSynchronize(st), "upload sync");
+        if (rc != SNN_OK) {
+            delete net;
+            return rc;
+        }
+
+        snn::StepArgs &a = net->args;
+        a.ctl = reinterpret_cast<snn::Ctl *>(A + L.ctl);
+        a.tables = reinterpret_cast<const snn::StaticTables *>(A + L.tables);
+        a.U = reinterpret_cast<float *>(A + L.U);
+        a.I = reinterpret_cast<float *>(A + L.I);
+        a.R = A + L.R;
+        a.ring = reinterpret_cast<int32_t *>(A + L.ring);
+        a.row_ptr = reinterpret_cast<const int64_t *>(A + L.row_ptr);
+        a.syn_tgt = reinterpret_cast<const int32_t *>(A + L.syn_tgt);
+        a.syn_w = reinterpret_cast<const int32_t *>(A + L.syn_w);
+        a.syn_d = A + L.syn_d;
+        a.rast_nrn = reinterpret_cast<int32_t *>(A + L.rast_nrn);
+        a.rast_t = reinterpret_cast<int32_t *>(A + L.rast_t);
+        a.n = net->n;
+        a.npad = net->npad;
+        a.seed = spec->seed;
+        a.rast_cap = static_cast<uint32_t>(L.rast_cap);
+        a.chunks_per_row = net->chunks_per_row;
+        a.p11 = net->c.p11f;
+        a.p21 = net->c.p21f;
+        a.p22 = net->c.p22f;
+        a.theta = net->c.theta;
+        a.u_reset = net->c.u_reset;
+        a.t_ref = net->c.t_ref;
+        a.w_ext_fx = net->c.w_ext_fx;
+        net->update_grid = snn::update_grid(net->n);
+        net->deliver_grid = spec->deliver_blocks > 0 ? spec->deliver_blocks : 2 * net->num_sms;
+        net->steps_per_graph = spec->steps_per_graph > 0 ? spec->steps_per_graph : 1000;
+        rc = capture_graph(net);
+        if (rc == SNN_OK && cudaEventCreateWithFlags(&net->ev_done, cudaEventDisableTiming) != cudaSuccess)
+            rc = fail(SNN_ECUDA, "event create");
+        if (rc != SNN_OK) {
+            snn_destroy(net);
+            return rc;
+        }
+    } catch (const std::bad_alloc &) {
+        delete net;
+        return fail(SNN_ENOMEM, "host allocation failed while building the network");
+    }
+    *out = net;
+    return SNN_OK;
+}
+
+int snn_step_n(snn_net *net, int64_t n_steps, void *cuda_stream)
+{
+    if (!net) return fail(SNN_EINVAL, "null network");
+    if (n_steps < 0) return fail(SNN_EINVAL, "n_steps < 0");
+    if (net->device_error) return fail(SNN_ESTATE, "a previous device error is pending");
+    if (n_steps == 0) return SNN_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int64_t full = n_steps / net->steps_per_graph;
+    const int64_t rem = n_steps % net->steps_per_graph;
+    for (int64_t g = 0; g < full; ++g) SNN_CUDA_TRY(cudaGraphLaunch(net->graph_exec, st));
+    if (rem > 0) {
+        int rc = launch_steps_direct(net, rem, st);
+        if (rc) return rc;
+    }
+    SNN_CUDA_TRY(cudaEventRecord(net->ev_done, st));
+    net->ev_recorded = true;
+    net->t += n_steps;
+    return SNN_OK;
+}
+
+int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *ms_update, double *ms_deliver)
+{
+    if (!net) return fail(SNN_EINVAL, "null network");
+    if (n_steps < 0) return fail(SNN_EINVAL, "n_steps < 0");
+    if (net->device_error) return fail(SNN_ESTATE, "a previous device error is pending");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    double su = 0.0, sd = 0.0;
+    const int64_t batch = 256;
+    std::vector<cudaEvent_t> ev(3 * batch);
+    for (auto &e : ev) SNN_CUDA_TRY(cudaEventCreate(&e));
+    int rc = SNN_OK;
+    for (int64_t done = 0; done < n_steps && rc == SNN_OK; done += batch) {
+        const int64_t m = std::min(batch, n_steps - done);
+        for (int64_t k = 0; k < m; ++k) {
+            cudaEventRecord(ev[3 * k], st);
+            snn::launch_update(net->args, static_cast<int>(k), net->update_grid, st);
+            cudaEventRecord(ev[3 * k + 1], st);
+            snn::launch_deliver(net->args, static_cast<int>(k), net->deliver_grid, st);
+            cudaEventRecord(ev[3 * k + 2], st);
+        }
+        snn::launch_advance(net->args.ctl, m, st);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[3 * m - 1]);
+        if (e != cudaSuccess) {
+            rc = fail(SNN_ECUDA, std::string("profile: ") + cudaGetErrorString(e));
+            break;
+        }
+        for (int64_t k = 0; k < m; ++k) {
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, ev[3 * k], ev[3 * k + 1]);
+            cudaEventElapsedTime(&b, ev[3 * k + 1], ev[3 * k + 2]);
+            su += a;
+            sd += b;
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (rc != SNN_OK) return rc;
+    SNN_CUDA_TRY(cudaStreamSynchronize(st));
+    net->t += n_steps;
+    if (ms_update) *ms_update = su;
+    if (ms_deliver) *ms_deliver = sd;
+    return SNN_OK;
+}
+
+int snn_read_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t capacity, int64_t *n_written)
+{
+    if (!net || !n_written) return fail(SNN_EINVAL, "null argument");
+    *n_written = 0;
+    int rc = drain(net);
+    const int64_t avail = static_cast<int64_t>(net->hist_t.size()) - net->read_pos;
+    if (!steps && !neurons) {
+        *n_written = avail;
+        return rc;
+    }
+    if (!steps || !neurons || capacity < 0) return fail(SNN_EINVAL, "bad output arrays");
+    const int64_t m = std::min(avail, capacity);
+    for (int64_t j = 0; j < m; ++j) {
+        steps[j] = net->hist_t[net->read_pos + j];
+        neurons[j] = net->hist_i[net->read_pos + j];
+    }
+    net->read_pos += m;
+    *n_written = m;
+    return rc;
+}
+
+int snn_read_rates(snn_net *net, int64_t t_begin, int64_t t_end, double *pop_rates_hz, int32_t *neuron_counts)
+{
+    if (!net || !pop_rates_hz) return fail(SNN_EINVAL, "null argument");
+    if (t_begin < 0 || t_end <= t_begin) return fail(SNN_EINVAL, "empty or negative window");
+    int rc = drain(net);
+    const int P = net->spec.model.n_pops;
+    std::vector<int64_t> pop_cnt(P, 0);
+    if (neuron_counts) std::fill(neuron_counts, neuron_counts + net->n, 0);
+    const auto lo = std::lower_bound(net->hist_t.begin(), net->hist_t.end(), t_begin) - net->hist_t.begin();
+    const auto hi = std::lower_bound(net->hist_t.begin(), net->hist_t.end(), t_end) - net->hist_t.begin();
+    for (auto j = lo; j < hi; ++j) {
+        const int32_t i = net->hist_i[j];
+        int b = 0;
+        while (b + 1 < P && i >= net->pop_off[b + 1]) ++b;
+        ++pop_cnt[b];
+        if (neuron_counts) ++neuron_counts[i];
+    }
+    const double secs = static_cast<double>(t_end - t_begin) * net->spec.model.dt_ms * 1e-3;
+    for (int b = 0; b < P; ++b) {
+        const int64_t nb = net->pop_off[b + 1] - net->pop_off[b];
+        pop_rates_hz[b] = nb > 0 ? static_cast<double>(pop_cnt[b]) / (static_cast<double>(nb) * secs) : 0.0;
+    }
+    return rc;
+}
+
+int snn_get_info(const snn_net *net, snn_info *out)
+{
+    if (!net || !out) return fail(SNN_EINVAL, "null argument");
+    std::memset(out, 0, sizeof(*out));
+    out->n_neurons = net->n;
+    out->n_synapses = net->n_syn;
+    out->n_synapses_padded = net->n_syn_padded;
+    out->t = net->t;
+    out->spikes_read = static_cast<int64_t>(net->hist_t.size());
+    out->events_read = net->events_read;
+    out->n_pops = net->spec.model.n_pops;
+    out->t_ref_steps = net->c.t_ref;
+    for (int b = 0; b <= SNN_MAX_POPS; ++b)
+        out->pop_offsets[b] = b < (int)net->pop_off.size() ? net->pop_off[b] : net->n;
+    out->w_f = net->c.w_f;
+    out->p11 = net->c.p11;
+    out->p22 = net->c.p22;
+    out->p21 = net->c.p21;
+    out->p11_f32 = net->c.p11f;
+    out->p21_f32 = net->c.p21f;
+    out->p22_f32 = net->c.p22f;
+    out->theta_f32 = net->c.theta;
+    out->u_reset_f32 = net->c.u_reset;
+    out->w_ext_fx = net->c.w_ext_fx;
+    std::memcpy(out->poisson_thresholds, net->c.thresholds, sizeof(out->poisson_thresholds));
+    out->max_row_length = net->max_row;
+    out->chunks_per_row = net->chunks_per_row;
+    out->steps_per_graph = net->steps_per_graph;
+    out->deliver_blocks = net->deliver_grid;
+    out->device_error = net->device_error;
+    return SNN_OK;
+}
+
+int snn_get_layout(const snn_net *net, snn_layout *out)
+{
+    if (!net || !out) return fail(SNN_EINVAL, "null argument");
+    const snn::Layout &L = net->L;
+    out->ctl = L.ctl;
+    out->params = L.tables;
+    out->U = L.U;
+    out->I = L.I;
+    out->R = L.R;
+    out->ring = L.ring;
+    out->row_ptr = L.row_ptr;
+    out->syn_tgt = L.syn_tgt;
+    out->syn_w = L.syn_w;
+    out->syn_delay = L.syn_d;
+    out->rast_neuron = L.rast_nrn;
+    out->rast_step = L.rast_t;
+    out->n_neurons_padded = net->npad;
+    out->n_synapses_padded = net->n_syn_padded;
+    return SNN_OK;
+}
+
+void snn_destroy(snn_net *net)
+{
+    if (!net) return;
+    if (net->ev_recorded) cudaEventSynchronize(net->ev_done);
+    if (net->graph_exec) cudaGraphExecDestroy(net->graph_exec);
+    if (net->graph) cudaGraphDestroy(net->graph);
+    if (net->capture_stream) cudaStreamDestroy(net->capture_stream);
+    if (net->ev_done) cudaEventDestroy(net->ev_done);
+    if (net->pin_nrn) cudaFreeHost(net->pin_nrn);
+    if (net->pin_t) cudaFreeHost(net->pin_t);
+    delete net;
+}
+
+}  // extern "C"

@@ -1,0 +1,440 @@
+// Host side of network construction (setup; not part of the timed step loop, as in
+// the paper's RTF definition of §4.2).
+//
+//  - model constants of §2.2 (w_f, p11, p22, beta, gamma, p21) in FP64, rounded once
+//    to FP32 for the device;
+//  - thalamic Poisson thresholds: the CDF of Poisson(nu_th K dt) scaled to 63 bits;
+//  - population sizes and the expected pair counts N_pre N_post p of §2.2;
+//  - every synapse drawn with replacement from counter-based Philox streams, so the
+//    result does not depend on the thread count;
+//  - the indexed synapse store of §3.5: rows grouped by sender and sorted by delay,
+//    each padded to a multiple of four entries with zero-weight synapses so that
+//    every row starts on a 16-byte boundary for vector loads.
+//
+// Built with -ffp-contract=off: every FP64 product and sum is rounded on its own.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <thread>
+
+#include "internal.hpp"
+#include "philox.cuh"
+
+namespace snn {
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586;
+constexpr double kInv2Pow53 = 1.0 / 9007199254740992.0;
+constexpr double kTwoPow63 = 9223372036854775808.0;
+
+inline double unit_open(uint64_t x) { return (static_cast<double>(x >> 11) + 0.5) * kInv2Pow53; }
+
+// Uniform integer in [0, n): the high word of x * n.
+inline int64_t scale_below(uint64_t x, int64_t n)
+{
+    uint64_t hi, lo;
+    mul_wide(x, static_cast<uint64_t>(n), hi, lo);
+    return static_cast<int64_t>(hi);
+}
+
+// Box-Muller transform of two uniforms: (r cos th, r sin th), r = sqrt(-2 ln u), th = 2 pi v.
+inline void gauss_pair(uint64_t u, uint64_t v, double &zc, double &zs)
+{
+    const double r = std::sqrt(-2.0 * std::log(unit_open(u)));
+    const double th = kTwoPi * unit_open(v);
+    zc = r * std::cos(th);
+    zs = r * std::sin(th);
+}
+
+void parallel_for(int nthreads, int64_t n, const std::function<void(int, int64_t, int64_t)> &body)
+{
+    if (n <= 0) return;
+    nthreads = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(nthreads, n)));
+    if (nthreads == 1) {
+        body(0, 0, n);
+        return;
+    }
+    std::vector<std::thread> pool;
+    pool.reserve(nthreads);
+    for (int t = 0; t < nthreads; ++t) {
+        const int64_t lo = n * t / nthreads, hi = n * (t + 1) / nthreads;
+        pool.emplace_back(body, t, lo, hi);
+    }
+    for (auto &th : pool) th.join();
+}
+
+}  // namespace
+
+int resolve_threads(int32_t requested)
+{
+    if (requested > 0) return requested;
+    const unsigned hc = std::thread::hardware_concurrency();
+    return hc ? static_cast<int>(std::min(hc, 64u)) : 4;
+}
+
+void compute_constants(const snn_model &m, Constants &c)
+{
+    const double ts = m.tau_syn_ms, tm = m.tau_m_ms, C = m.C_m_pF, dt = m.dt_ms;
+    // PSC amplitude that gives a 1 mV PSP peak (§2.2)
+    const double d = ts - tm;
+    const double p = ts * tm;
+    const double q = tm / ts;
+    c.w_f = C * d / (p * (std::pow(q, tm / d) - std::pow(q, ts / d)));
+    // one-step propagators (§2.2)
+    c.p11 = std::exp(-dt / ts);
+    c.p22 = std::exp(-dt / tm);
+    c.beta = ts * tm / (tm - ts);
+    c.gamma = c.beta / C;
+    c.p21 = c.p11 * c.gamma * (std::exp(dt / c.beta) - 1.0);
+    c.p11f = static_cast<float>(c.p11);
+    c.p21f = static_cast<float>(c.p21);
+    c.p22f = static_cast<float>(c.p22);
+    c.theta = static_cast<float>(m.u_thr_mV - m.u_rest_mV);
+    c.u_reset = static_cast<float>(m.u_reset_mV - m.u_rest_mV);
+    c.t_ref = static_cast<int32_t>(std::llround(m.tau_ref_ms / dt));
+    c.w_ext_fx = static_cast<int32_t>(std::llround(c.w_f * m.w_ext_mV * 4096.0));
+    // Poisson(lambda) CDF thresholds, lambda = nu_th K dt
+    std::memset(c.thresholds, 0, sizeof(c.thresholds));
+    for (int b = 0; b < m.n_pops; ++b) {
+        const double lam = m.k_ext[b] * m.nu_th_hz * dt * 1e-3;
+        double pk = std::exp(-lam);
+        double cdf = pk;
+        for (int k = 0; k < kPK; ++k) {
+            if (k > 0) {
+                pk = pk * lam / static_cast<double>(k);
+                cdf = cdf + pk;
+            }
+            const bool saturated = (k == kPK - 1) || cdf >= 1.0;
+            c.thresholds[b][k] = saturated ? (1ull << 63) : static_cast<uint64_t>(cdf * kTwoPow63);
+        }
+    }
+}
+
+void population_sizes(const snn_model &m, int32_t scale_n, int64_t out[SNN_MAX_POPS])
+{
+    for (int b = 0; b < SNN_MAX_POPS; ++b)
+        out[b] = b < m.n_pops ? (m.n_full[b] * static_cast<int64_t>(scale_n) + 500) / 1000 : 0;
+}
+
+int64_t pair_count(const snn_model &m, int32_t scale_n, int32_t scale_k, int target, int source)
+{
+    int64_t nb[SNN_MAX_POPS];
+    population_sizes(m, scale_n, nb);
+    const double src = static_cast<double>(m.n_full[source] * static_cast<int64_t>(scale_k)) / 1000.0;
+    return static_cast<int64_t>(std::llround(m.conn_p[target][source] * src * static_cast<double>(nb[target])));
+}
+
+int64_t count_neurons(const snn_spec &spec)
+{
+    if (spec.custom) return spec.custom->n_neurons;
+    int64_t nb[SNN_MAX_POPS];
+    population_sizes(spec.model, spec.scale_n_permille, nb);
+    int64_t n = 0;
+    for (int b = 0; b < spec.model.n_pops; ++b) n += nb[b];
+    return n;
+}
+
+int64_t count_synapses(const snn_spec &spec)
+{
+    if (spec.custom) return spec.custom->n_synapses;
+    int64_t s = 0;
+    for (int a = 0; a < spec.model.n_pops; ++a)
+        for (int b = 0; b < spec.model.n_pops; ++b)
+            s += pair_count(spec.model, spec.scale_n_permille, spec.scale_k_permille, b, a);
+    return s;
+}
+
+bool validate_spec(const snn_spec &spec, std::string &why)
+{
+    const snn_model &m = spec.model;
+    auto fail = [&](const char *msg) {
+        why = msg;
+        return false;
+    };
+    if (spec.abi_version != SNN_ABI_VERSION) return fail("abi_version mismatch");
+    if (m.n_pops < 1 || m.n_pops > SNN_MAX_POPS) return fail("n_pops out of [1, SNN_MAX_POPS]");
+    if (m.n_overrides < 0 || m.n_overrides > SNN_MAX_OVERRIDES) return fail("n_overrides out of range");
+    if (!(m.dt_ms > 0) || !(m.C_m_pF > 0) || !(m.tau_m_ms > 0) || !(m.tau_syn_ms > 0) || !(m.tau_ref_ms >= 0))
+        return fail("time constants, dt and C_m must be positive");
+    if (m.tau_m_ms == m.tau_syn_ms) return fail("tau_m == tau_syn is not supported (w_f and p21 are singular)");
+    if (!(m.nu_th_hz >= 0)) return fail("nu_th must be >= 0");
+    const double tref_steps = m.tau_ref_ms / m.dt_ms;
+    if (tref_steps > 255.0) return fail("tau_ref / dt must be <= 255 steps");
+    for (int b = 0; b < m.n_pops; ++b) {
+        if (!(m.k_ext[b] >= 0)) return fail("k_ext must be >= 0");
+        const double lam = m.k_ext[b] * m.nu_th_hz * m.dt_ms * 1e-3;
+        if (lam > 8.0) return fail("thalamic mean per step above 8 exceeds the Poisson table");
+        if (m.n_full[b] < 0) return fail("n_full must be >= 0");
+    }
+    for (int o = 0; o < m.n_overrides; ++o)
+        if (m.ovr_source[o] < 0 || m.ovr_source[o] >= m.n_pops || m.ovr_target[o] < 0 || m.ovr_target[o] >= m.n_pops)
+            return fail("override population out of range");
+    if (spec.raster_capacity < 0 || spec.raster_capacity > (int64_t{1} << 31) - 1)
+        return fail("raster_capacity out of [0, 2^31-1]");
+    if (spec.steps_per_graph < 0 || spec.steps_per_graph > 100000) return fail("steps_per_graph out of [0, 100000]");
+    if (spec.deliver_blocks < 0 || spec.deliver_blocks > 65535) return fail("deliver_blocks out of range");
+    if (spec.custom) {
+        const snn_custom_net &c = *spec.custom;
+        if (c.n_neurons < 1 || c.n_neurons > (int64_t{1} << 30)) return fail("custom n_neurons out of [1, 2^30]");
+        if (c.n_synapses < 0) return fail("custom n_synapses < 0");
+        if (c.n_synapses > 0 && (!c.pre || !c.post || !c.w_fx || !c.delay))
+            return fail("custom synapse arrays missing");
+        if (!c.u0) return fail("custom u0 missing");
+        if (c.pop_offsets[0] != 0 || c.pop_offsets[m.n_pops] != c.n_neurons)
+            return fail("custom pop_offsets must run from 0 to n_neurons");
+        for (int b = 0; b < m.n_pops; ++b)
+            if (c.pop_offsets[b + 1] < c.pop_offsets[b]) return fail("custom pop_offsets must be nondecreasing");
+    } else {
+        if (spec.scale_n_permille < 1 || spec.scale_k_permille < 0 || spec.scale_n_permille > 100000 ||
+            spec.scale_k_permille > 100000)
+            return fail("scales out of range");
+        int64_t nb[SNN_MAX_POPS];
+        population_sizes(m, spec.scale_n_permille, nb);
+        int64_t n = 0;
+        for (int b = 0; b < m.n_pops; ++b) n += nb[b];
+        if (n < 1 || n > (int64_t{1} << 30)) return fail("neuron count out of [1, 2^30]");
+        for (int a = 0; a < m.n_pops; ++a)
+            for (int b = 0; b < m.n_pops; ++b) {
+                if (!(m.conn_p[b][a] >= 0)) return fail("connection probability < 0");
+                const int64_t k = pair_count(m, spec.scale_n_permille, spec.scale_k_permille, b, a);
+                if (k > 0 && (nb[a] == 0 || nb[b] == 0)) return fail("synapses requested for an empty population");
+                if (!(m.d_sd_ms[a] >= 0) || !(m.w_sd_mV[a] >= 0)) return fail("negative SD");
+            }
+        if (count_synapses(spec) > (int64_t{1} << 34)) return fail("more than 2^34 synapses");
+    }
+    return true;
+}
+
+Layout make_layout(const snn_spec &spec)
+{
+    auto up = [](uint64_t x) { return (x + 255) & ~uint64_t{255}; };
+    Layout L{};
+    const int64_t n = count_neurons(spec);
+    const int64_t s = count_synapses(spec);
+    L.npad = (n + kNeuronAlign - 1) / kNeuronAlign * kNeuronAlign;
+    L.syn_padded_max = s + int64_t{kRowAlign - 1} * n;
+    L.rast_cap = spec.raster_capacity > 0 ? spec.raster_capacity : (int64_t{1} << 24);
+    uint64_t o = 0;
+    L.ctl = o; o = up(o + sizeof(Ctl));
+    L.tables = o; o = up(o + sizeof(StaticTables));
+    L.U = o; o = up(o + 4 * L.npad);
+    L.I = o; o = up(o + 4 * L.npad);
+    L.R = o; o = up(o + L.npad);
+    L.ring = o; o = up(o + uint64_t{4} * kDMax * L.npad);
+    L.row_ptr = o; o = up(o + 8 * (n + 1));
+    L.syn_tgt = o; o = up(o + 4 * L.syn_padded_max);
+    L.syn_w = o; o = up(o + 4 * L.syn_padded_max);
+    L.syn_d = o; o = up(o + L.syn_padded_max + 16);
+    L.rast_nrn = o; o = up(o + 4 * L.rast_cap);
+    L.rast_t = o; o = up(o + 4 * L.rast_cap);
+    L.total = o;
+    return L;
+}
+
+namespace {
+
+// Amplitude law of a synapse from population a to population b.
+void amplitude_law(const snn_model &m, int a, int b, double &mu, double &sd)
+{
+    mu = m.w_mean_mV[a];
+    sd = m.w_sd_mV[a];
+    for (int o = 0; o < m.n_overrides; ++o)
+        if (m.ovr_source[o] == a && m.ovr_target[o] == b) {
+            mu = m.ovr_w_mean_mV[o];
+            sd = m.ovr_w_sd_mV[o];
+        }
+}
+
+struct EdgeList {
+    std::vector<int32_t> pre, post, w;
+    std::vector<uint8_t> d;
+};
+
+// Sample every synapse of the microcircuit.  Synapse k of pair (a -> b) uses Philox
+// counter (k, a, b, 0) under key (seed, kStreamConnect); the list is in (a, b, k) order.
+void sample_edges(const snn_spec &spec, const Constants &c, EdgeList &e, int nthreads)
+{
+    const snn_model &m = spec.model;
+    const int P = m.n_pops;
+    int64_t nb[SNN_MAX_POPS], off[SNN_MAX_POPS + 1];
+    population_sizes(m, spec.scale_n_permille, nb);
+    off[0] = 0;
+    for (int b = 0; b < P; ++b) off[b + 1] = off[b] + nb[b];
+    // pair bases in (a, b) order
+    std::vector<int64_t> base(P * P + 1, 0);
+    for (int a = 0; a < P; ++a)
+        for (int b = 0; b < P; ++b)
+            base[a * P + b + 1] = base[a * P + b] + pair_count(m, spec.scale_n_permille, spec.scale_k_permille, b, a);
+    const int64_t S = base[P * P];
+    e.pre.resize(S);
+    e.post.resize(S);
+    e.w.resize(S);
+    e.d.resize(S);
+    const uint64_t seed = spec.seed;
+    const double w_f = c.w_f, dt = m.dt_ms;
+    parallel_for(nthreads, S, [&](int, int64_t lo, int64_t hi) {
+        int pair = static_cast<int>(std::upper_bound(base.begin(), base.end(), lo) - base.begin()) - 1;
+        for (int64_t s = lo; s < hi; ++s) {
+            while (s >= base[pair + 1]) ++pair;
+            const int a = pair / P, b = pair % P;
+            const int64_t k = s - base[pair];
+            const Block4 r = philox4x64_10(static_cast<uint64_t>(k), static_cast<uint64_t>(a),
+                                           static_cast<uint64_t>(b), 0, seed, kStreamConnect);
+            e.pre[s] = static_cast<int32_t>(off[a] + scale_below(r.w[0], nb[a]));
+            e.post[s] = static_cast<int32_t>(off[b] + scale_below(r.w[1], nb[b]));
+            double zc, zs;
+            gauss_pair(r.w[2], r.w[3], zc, zs);
+            double mu, sd;
+            amplitude_law(m, a, b, mu, sd);
+            double amp = mu + sd * zc;
+            if (mu >= 0.0) amp = amp < 0.0 ? 0.0 : amp;  // excitatory stays >= 0
+            else amp = amp > 0.0 ? 0.0 : amp;            // inhibitory stays <= 0
+            e.w[s] = static_cast<int32_t>(std::llround(amp * w_f * 4096.0));
+            const double delay_ms = m.d_mean_ms[a] + m.d_sd_ms[a] * zs;
+            long long steps = std::llround(delay_ms / dt);
+            steps = std::min<long long>(std::max<long long>(steps, 1), kDMax - 1);
+            e.d[s] = static_cast<uint8_t>(steps);
+        }
+    });
+}
+
+}  // namespace
+
+bool build_host_network(const snn_spec &spec, const Constants &c, HostNetwork &net, std::string &why)
+{
+    const int nthreads = resolve_threads(spec.n_threads);
+    const snn_model &m = spec.model;
+    const int64_t n = count_neurons(spec);
+    net.n = n;
+    net.npad = (n + kNeuronAlign - 1) / kNeuronAlign * kNeuronAlign;
+    net.pop_off.assign(SNN_MAX_POPS + 1, n);
+    EdgeList e;
+    if (spec.custom) {
+        const snn_custom_net &cn = *spec.custom;
+        for (int b = 0; b <= m.n_pops; ++b) net.pop_off[b] = cn.pop_offsets[b];
+        const int64_t S = cn.n_synapses;
+        e.pre.assign(cn.pre, cn.pre + S);
+        e.post.assign(cn.post, cn.post + S);
+        e.w.assign(cn.w_fx, cn.w_fx + S);
+        e.d.assign(cn.delay, cn.delay + S);
+        for (int64_t s = 0; s < S; ++s) {
+            if (e.pre[s] < 0 || e.pre[s] >= n || e.post[s] < 0 || e.post[s] >= n) {
+                why = "custom synapse endpoint out of [0, n_neurons)";
+                return false;
+            }
+            if (e.d[s] < 1 || e.d[s] > kDMax - 1) {
+                why = "custom delay out of [1, 63]";
+                return false;
+            }
+        }
+        net.u0.assign(cn.u0, cn.u0 + n);
+    } else {
+        int64_t nb[SNN_MAX_POPS];
+        population_sizes(m, spec.scale_n_permille, nb);
+        net.pop_off[0] = 0;
+        for (int b = 0; b < m.n_pops; ++b) net.pop_off[b + 1] = net.pop_off[b] + nb[b];
+        sample_edges(spec, c, e, nthreads);
+        // initial potentials: Philox counter (i, 0, 0, 0) under key (seed, kStreamInitial)
+        net.u0.resize(n);
+        for (int b = 0; b < m.n_pops; ++b) {
+            const int64_t lo = net.pop_off[b], hi = net.pop_off[b + 1];
+            const double mu = m.u0_mean_mV[b], sd = m.u0_sd_mV[b], rest = m.u_rest_mV;
+            parallel_for(nthreads, hi - lo, [&](int, int64_t a0, int64_t a1) {
+                for (int64_t i = lo + a0; i < lo + a1; ++i) {
+                    const Block4 r = philox4x64_10(static_cast<uint64_t>(i), 0, 0, 0, spec.seed, kStreamInitial);
+                    double zc, zs;
+                    gauss_pair(r.w[0], r.w[1], zc, zs);
+                    net.u0[i] = static_cast<float>(mu + sd * zc - rest);
+                }
+            });
+        }
+    }
+    const int64_t S = static_cast<int64_t>(e.pre.size());
+    net.n_syn = S;
+
+    // Pass 1: stable counting sort by sender (per-thread histograms keep it deterministic).
+    const int T = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(nthreads, S / 65536 + 1)));
+    std::vector<std::vector<int64_t>> hist(T, std::vector<int64_t>(n + 1, 0));
+    parallel_for(T, S, [&](int t, int64_t lo, int64_t hi) {
+        auto &h = hist[t];
+        for (int64_t s = lo; s < hi; ++s) ++h[e.pre[s]];
+    });
+    std::vector<int64_t> row_len(n, 0);
+    {
+        int64_t run = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            for (int t = 0; t < T; ++t) {
+                const int64_t cnt = hist[t][i];
+                hist[t][i] = run;
+                run += cnt;
+                row_len[i] += cnt;
+            }
+        }
+    }
+    std::vector<int32_t> s_post(S), s_w(S);
+    std::vector<uint8_t> s_d(S);
+    parallel_for(T, S, [&](int t, int64_t lo, int64_t hi) {
+        auto &h = hist[t];
+        for (int64_t s = lo; s < hi; ++s) {
+            const int64_t dst = h[e.pre[s]]++;
+            s_post[dst] = e.post[s];
+            s_w[dst] = e.w[s];
+            s_d[dst] = e.d[s];
+        }
+    });
+    hist.clear();
+    hist.shrink_to_fit();
+    EdgeList().pre.swap(e.pre);
+    EdgeList().post.swap(e.post);
+    EdgeList().w.swap(e.w);
+    EdgeList().d.swap(e.d);
+
+    // Pass 2: within each row, stable counting sort by delay into the padded layout.
+    net.row_ptr.assign(n + 1, 0);
+    net.out_degree.resize(n);
+    std::vector<int64_t> src_ptr(n + 1, 0);
+    int64_t maxrow = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t padded = (row_len[i] + kRowAlign - 1) / kRowAlign * kRowAlign;
+        net.row_ptr[i + 1] = net.row_ptr[i] + padded;
+        src_ptr[i + 1] = src_ptr[i] + row_len[i];
+        net.out_degree[i] = static_cast<int32_t>(row_len[i]);
+        maxrow = std::max(maxrow, padded);
+    }
+    net.max_row = static_cast<int32_t>(maxrow);
+    net.n_syn_padded = net.row_ptr[n];
+    net.tgt.assign(net.n_syn_padded, 0);
+    net.w.assign(net.n_syn_padded, 0);
+    net.d.assign(net.n_syn_padded, 1);
+    parallel_for(nthreads, n, [&](int, int64_t lo, int64_t hi) {
+        int64_t cnt[kDMax];
+        for (int64_t i = lo; i < hi; ++i) {
+            std::fill(cnt, cnt + kDMax, 0);
+            for (int64_t s = src_ptr[i]; s < src_ptr[i + 1]; ++s) ++cnt[s_d[s]];
+            int64_t pos = net.row_ptr[i];
+            for (int k = 0; k < kDMax; ++k) {
+                const int64_t c0 = cnt[k];
+                cnt[k] = pos;
+                pos += c0;
+            }
+            for (int64_t s = src_ptr[i]; s < src_ptr[i + 1]; ++s) {
+                const int64_t dst = cnt[s_d[s]]++;
+                net.tgt[dst] = s_post[s];
+                net.w[dst] = s_w[s];
+                net.d[dst] = s_d[s];
+            }
+            // padding entries: zero weight onto the sender itself, delay 1
+            for (int64_t s = pos; s < net.row_ptr[i + 1]; ++s) {
+                net.tgt[s] = static_cast<int32_t>(i);
+                net.w[s] = 0;
+                net.d[s] = 1;
+            }
+        }
+    });
+    return true;
+}
+
+}  // namespace snn

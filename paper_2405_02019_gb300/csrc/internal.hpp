@@ -1,0 +1,111 @@
+// Internal declarations shared by the host builder, the kernels and the ABI layer.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/snn.h"
+
+namespace snn {
+
+constexpr int kDMax = SNN_D_MAX;             // ring rows (§3.2)
+constexpr int kDMask = SNN_D_MAX - 1;
+constexpr int kPK = SNN_POISSON_KMAX;
+constexpr int64_t kNeuronAlign = 128;        // ring row stride granularity
+constexpr int kRowAlign = 4;                 // synapse rows padded to whole int4 quads
+constexpr int kChunk = 256;                  // synapses per delivery work item (32 lanes x 2 quads)
+constexpr int kUpdateThreads = 128;          // 4 neurons per thread
+constexpr int kDeliverThreads = 256;
+constexpr uint32_t kErrRaster = 1u;
+
+// Device control block (first bytes of the arena).
+struct alignas(64) Ctl {
+    int64_t t_base;          // first step of the next graph replay / launch batch
+    uint32_t cursor;         // spikes appended to the raster since the last drain
+    uint32_t step_begin[2];  // raster index where step t's spikes start, by t mod 2
+    uint32_t err;            // sticky error bits
+    uint32_t pad[10];
+};
+
+// Tables the update kernel stages in shared memory (in the arena, read-only).
+struct alignas(16) StaticTables {
+    uint64_t thresholds[SNN_MAX_POPS][kPK];  // 63-bit Poisson CDF thresholds
+    int64_t pop_off[SNN_MAX_POPS + 1];
+    int32_t n_pops;
+    int32_t pad;
+};
+
+// Kernel arguments (by value; small).
+struct StepArgs {
+    Ctl *ctl;
+    const StaticTables *tables;
+    float *U;
+    float *I;
+    uint8_t *R;
+    int32_t *ring;
+    const int64_t *row_ptr;
+    const int32_t *syn_tgt;
+    const int32_t *syn_w;
+    const uint8_t *syn_d;
+    int32_t *rast_nrn;
+    int32_t *rast_t;
+    int64_t n;        // neurons
+    int64_t npad;     // ring row stride
+    uint64_t seed;
+    uint32_t rast_cap;
+    int32_t chunks_per_row;
+    float p11, p21, p22, theta, u_reset;
+    int32_t t_ref;
+    int32_t w_ext_fx;
+};
+
+// Host constants of one model (§2.2).
+struct Constants {
+    double w_f, p11, p22, beta, gamma, p21;
+    float p11f, p21f, p22f, theta, u_reset;
+    int32_t t_ref;
+    int32_t w_ext_fx;
+    uint64_t thresholds[SNN_MAX_POPS][kPK];
+};
+
+// Network in host memory, in the device layout.
+struct HostNetwork {
+    int64_t n = 0;
+    int64_t npad = 0;
+    int64_t n_syn = 0;         // true synapses
+    int64_t n_syn_padded = 0;  // including row padding
+    int32_t max_row = 0;
+    std::vector<int64_t> pop_off;
+    std::vector<int64_t> row_ptr;   // padded offsets, n+1
+    std::vector<int32_t> out_degree;  // true row lengths
+    std::vector<int32_t> tgt;
+    std::vector<int32_t> w;
+    std::vector<uint8_t> d;
+    std::vector<float> u0;
+};
+
+// Arena layout for a spec.
+struct Layout {
+    uint64_t ctl, tables, U, I, R, ring, row_ptr, syn_tgt, syn_w, syn_d, rast_nrn, rast_t, total;
+    int64_t npad, syn_padded_max, rast_cap;
+};
+
+// builder.cpp
+bool validate_spec(const snn_spec &spec, std::string &why);
+void compute_constants(const snn_model &m, Constants &c);
+void population_sizes(const snn_model &m, int32_t scale_n, int64_t out[SNN_MAX_POPS]);
+int64_t pair_count(const snn_model &m, int32_t scale_n, int32_t scale_k, int target, int source);
+int64_t count_neurons(const snn_spec &spec);
+int64_t count_synapses(const snn_spec &spec);
+Layout make_layout(const snn_spec &spec);
+bool build_host_network(const snn_spec &spec, const Constants &c, HostNetwork &net, std::string &why);
+int resolve_threads(int32_t requested);
+
+// kernels.cu
+void launch_update(const StepArgs &a, int k, int grid, void *stream);
+void launch_deliver(const StepArgs &a, int k, int grid, void *stream);
+void launch_advance(Ctl *ctl, int64_t m, void *stream);
+int update_grid(int64_t n);
+
+}  // namespace snn

@@ -1,0 +1,343 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Plain mode is bit-exact by construction (FP32 without FMA on both sides, int32
+fixed-point input, the same Philox streams), so rasters, states and networks are
+compared element by element with no tolerance.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2405_02019_gb300 as snn  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2405_02019_gb300 import build
+
+    build.build()
+    oracle.build()
+
+
+def _state(net):
+    n = net.n_neurons
+    U = net.device_view("U", torch.float32, n).cpu().numpy()
+    I = net.device_view("I", torch.float32, n).cpu().numpy()
+    R = net.device_view("R", torch.uint8, n).cpu().numpy().astype(np.int32)
+    return U, I, R
+
+
+def _assert_same_state(net, sim):
+    U, I, R = _state(net)
+    assert np.array_equal(U.view(np.uint32), sim.U.view(np.uint32))
+    assert np.array_equal(I.view(np.uint32), sim.I.view(np.uint32))
+    assert np.array_equal(R, sim.R)
+
+
+def _device_network(net):
+    """(pre, post, delay, w) of every real synapse read back from the device arena."""
+    lay = net.layout()
+    n = net.n_neurons
+    sp = int(lay.n_synapses_padded)
+    rp = net.device_view("row_ptr", torch.int64, n + 1).cpu().numpy()
+    tg = net.device_view("syn_tgt", torch.int32, sp).cpu().numpy()
+    w = net.device_view("syn_w", torch.int32, sp).cpu().numpy()
+    d = net.device_view("syn_delay", torch.uint8, sp).cpu().numpy()
+    return rp, tg, w, d
+
+
+def _row_multisets_equal(onet, rp, tg, w, d):
+    n = onet.n
+    lens = np.diff(onet.row_ptr)
+    plen = np.diff(rp)
+    assert np.all(plen % 4 == 0) and np.all(plen >= lens) and np.all(plen - lens < 4)
+    pos = np.arange(rp[-1]) - np.repeat(rp[:-1], plen)
+    real = pos < np.repeat(lens, plen)
+    assert np.all(w[: rp[-1]][~real] == 0)
+    pre_l = np.repeat(np.arange(n), plen)[real]
+    tl, wl, dl = tg[: rp[-1]][real], w[: rp[-1]][real], d[: rp[-1]][real]
+    # rows are delay-sorted on the device (indexed store of §3.5)
+    for i in range(0, n, max(1, n // 200)):
+        seg = d[rp[i]: rp[i] + lens[i]]
+        assert np.all(np.diff(seg.astype(int)) >= 0)
+    pre_o = np.repeat(np.arange(n), lens)
+    ko = np.lexsort((onet.w_fx, onet.delay, onet.post, pre_o))
+    kl = np.lexsort((wl, dl, tl, pre_l))
+    assert np.array_equal(pre_o[ko], pre_l[kl])
+    assert np.array_equal(onet.post[ko], tl[kl])
+    assert np.array_equal(onet.delay[ko], dl[kl])
+    assert np.array_equal(onet.w_fx[ko], wl[kl])
+
+
+@pytest.fixture(scope="module")
+def model():
+    return workload.microcircuit_model()
+
+
+@pytest.fixture(scope="module")
+def tiny(model):
+    wl = workload.WORKLOADS["pd_tiny"]
+    onet = oracle.build_network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed)
+    return wl, onet
+
+
+def test_constants_bit_identical(model, tiny):
+    wl, _ = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed)
+    info = net.info()
+    c = oracle.constants(model)
+    s = oracle.step_constants(model)
+    for k in ("w_f", "p11", "p22", "p21"):
+        assert getattr(info, k) == c[k], k
+    assert np.float32(info.p11_f32) == s["p11"] and np.float32(info.p21_f32) == s["p21"]
+    assert np.float32(info.p22_f32) == s["p22"] and np.float32(info.theta_f32) == s["theta"]
+    assert np.float32(info.u_reset_f32) == s["u_reset"]
+    assert info.t_ref_steps == s["t_ref"] and info.w_ext_fx == s["w_ext_fx"]
+    thr = np.ctypeslib.as_array(info.poisson_thresholds)
+    for b in range(8):
+        assert np.array_equal(thr[b], oracle.poisson_table(model, b))
+    net.close()
+
+
+def test_network_identical_tiny(model, tiny):
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed)
+    assert net.info().n_synapses == len(onet.post)
+    _row_multisets_equal(onet, *_device_network(net))
+    U, _, _ = _state(net)
+    assert np.array_equal(U.view(np.uint32), onet.u0.view(np.uint32))
+    net.close()
+
+
+@pytest.mark.parametrize("spg", [96, 1000])
+def test_raster_bit_exact_tiny(model, tiny, spg):
+    """Tiny microcircuit (7,718 neurons, 2.85e6 synapses), 1,000 steps: identical raster
+    and final state.  spg=96 mixes graph replays with directly launched remainders."""
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, steps_per_graph=spg)
+    net.step(wl.steps)
+    g_t, g_i = net.read_spikes()
+    sim = oracle.Sim(model, onet, wl.seed)
+    o_t, o_i = sim.run(wl.steps)
+    assert len(o_t) > 1000
+    assert np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
+    _assert_same_state(net, sim)
+    info = net.info()
+    assert info.spikes_read == len(o_t)
+    assert info.events_read == int(np.diff(onet.row_ptr)[o_i].sum())
+    net.close()
+
+
+def test_incremental_reads_and_rates(model, tiny):
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, steps_per_graph=50)
+    parts = []
+    for n in (1, 7, 120, 372):
+        net.step(n)
+        parts.append(net.read_spikes())
+    g_t = np.concatenate([p[0] for p in parts])
+    g_i = np.concatenate([p[1] for p in parts])
+    sim = oracle.Sim(model, onet, wl.seed)
+    o_t, o_i = sim.run(500)
+    assert np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
+    rates, counts = net.read_rates(100, 500)
+    sel = (o_t >= 100) & (o_t < 500)
+    exp_counts = np.bincount(o_i[sel], minlength=onet.n)
+    assert np.array_equal(counts, exp_counts)
+    sizes = np.diff(onet.pop_off)
+    pops = np.searchsorted(onet.pop_off, o_i[sel], side="right") - 1
+    exp_rates = np.bincount(pops, minlength=8) / (sizes * 400 * 1e-4)
+    np.testing.assert_allclose(rates, exp_rates, rtol=1e-12)
+    net.close()
+
+
+def test_profile_steps_same_dynamics(model, tiny):
+    """The kernel-by-kernel timing path computes the same steps as the graph path."""
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, steps_per_graph=64)
+    net.step(100)
+    mu, md = net.profile_steps(300)
+    assert mu > 0 and md > 0
+    net.step(100)
+    g_t, g_i = net.read_spikes()
+    o_t, o_i = oracle.Sim(model, onet, wl.seed).run(500)
+    assert np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
+    net.close()
+
+
+# ------------------------------------------------------------ hand-placed spikes
+
+
+def _chain(d_first, d_second, w2):
+    big = 200_000_000
+    return dict(pre=[0, 1], post=[1, 2], w_fx=[big, w2], delay=[d_first, d_second], u0=[20.0, 0.0, 0.0],
+                pop_offsets=[0, 3, 3, 3, 3, 3, 3, 3, 3])
+
+
+@pytest.mark.parametrize("t1", [2, 62, 63, 64])
+@pytest.mark.parametrize("d", [1, 15, 16, 63])
+def test_hand_placed_spike_arrival(t1, d):
+    """A spike at step t1 with delay d reaches the target's current at the end of step
+    t1 + d, with the exact amplitude, on the GPU as in the oracle (ring wrap included)."""
+    m = workload.microcircuit_model().replace(k_ext=[0.0] * 8)
+    w2 = 12345 * 16
+    c = _chain(t1 - 1, d, w2)
+    net = snn.Network(m, custom=c, steps_per_graph=7)
+    onet = oracle.network_from_edges(3, c["pre"], c["post"], c["w_fx"], c["delay"], c["u0"], c["pop_offsets"])
+    sim = oracle.Sim(m, onet, 1)
+    t_arr = t1 + d
+    for step in range(t_arr + 3):
+        net.step(1)
+        sim.run(1)
+        _, I, _ = _state(net)
+        assert I.view(np.uint32)[2] == sim.I.view(np.uint32)[2], step
+        if step == t_arr - 1:
+            assert I[2] == 0.0
+        if step == t_arr:
+            assert I[2] == np.float32(w2) * np.float32(2.0**-12)
+    g_t, g_i = net.read_spikes()
+    assert list(zip(g_t.tolist(), g_i.tolist()))[:2] == [(0, 0), (t1, 1)]
+    net.close()
+
+
+# ------------------------------------------------------------------ edge cases
+
+
+def _custom_parity(m, custom, steps, spg=16, seed=5, **kw):
+    n = len(custom["u0"])
+    net = snn.Network(m, custom=custom, steps_per_graph=spg, seed=seed, **kw)
+    onet = oracle.network_from_edges(n, custom["pre"], custom["post"], custom["w_fx"], custom["delay"],
+                                     custom["u0"], custom.get("pop_offsets"))
+    sim = oracle.Sim(m, onet, seed)
+    net.step(steps)
+    g = net.read_spikes()
+    o = sim.run(steps)
+    assert np.array_equal(g[0], o[0]) and np.array_equal(g[1], o[1])
+    _assert_same_state(net, sim)
+    net.close()
+    return o
+
+
+@pytest.mark.parametrize("n", [1, 3, 13, 129, 517])
+def test_ragged_neuron_counts_no_synapses(n):
+    """Neuron counts that fill neither a quad nor a 128-wide ring row; no synapses;
+    thalamic drive only (population 0 = L23E)."""
+    m = workload.microcircuit_model()
+    rng = np.random.default_rng(n)
+    u0 = rng.uniform(0, 16, n).astype(np.float32)
+    custom = dict(pre=[], post=[], w_fx=[], delay=[], u0=u0, pop_offsets=[0] + [n] * 8)
+    o = _custom_parity(m, custom, 300)
+    assert len(o[0]) > 0
+
+
+def test_long_rows_ragged_chunks_and_all_delays():
+    """Rows longer than one 256-synapse chunk with ragged tails, every delay 1..63,
+    multapses and autapses, mixed signs, several populations."""
+    m = workload.microcircuit_model()
+    rng = np.random.default_rng(11)
+    n = 301
+    pre, post, w, d = [], [], [], []
+    for s, L in ((0, 1), (5, 255), (6, 256), (7, 257), (8, 1000), (9, 3001), (300, 513)):
+        pre += [s] * L
+        post += list(rng.integers(0, n, L))
+        w += list(rng.integers(-3_000_000, 3_000_000, L))
+        d += list(rng.integers(1, 64, L))
+    pre += [10] * 64
+    post += [10] * 64          # autapses, each delay once
+    w += [400_000] * 64
+    d += list(range(1, 64)) + [63]
+    u0 = rng.uniform(10, 16, n).astype(np.float32)
+    po = [0, 40, 80, 120, 160, 200, 240, 280, n]
+    custom = dict(pre=pre, post=post, w_fx=w, delay=d, u0=u0, pop_offsets=po)
+    o = _custom_parity(m, custom, 400, spg=33)
+    assert len(o[0]) > 50
+
+
+def test_raster_overflow_is_reported(model):
+    """A raster smaller than the spikes of the run fails loudly with SNN_EOVERFLOW."""
+    net = snn.Network(model, 20, 20, seed=1, raster_capacity=64)
+    net.step(300)
+    with pytest.raises(snn.SnnError) as e:
+        net.read_spikes()
+    assert e.value.code == snn.SNN_EOVERFLOW
+    with pytest.raises(snn.SnnError):
+        net.step(1)
+    net.close()
+
+
+@pytest.mark.parametrize("scale", [(1, 1), (5, 300), (300, 5)])
+def test_extreme_scales(model, scale):
+    sn, sk = scale
+    onet = oracle.build_network(model, sn, sk, 9)
+    net = snn.Network(model, sn, sk, seed=9, steps_per_graph=40)
+    _row_multisets_equal(onet, *_device_network(net))
+    net.step(250)
+    g = net.read_spikes()
+    sim = oracle.Sim(model, onet, 9)
+    o = sim.run(250)
+    assert np.array_equal(g[0], o[0]) and np.array_equal(g[1], o[1])
+    _assert_same_state(net, sim)
+    net.close()
+
+
+def test_zero_steps_and_empty_reads(model):
+    net = snn.Network(model, 20, 20, seed=2)
+    net.step(0)
+    t, i = net.read_spikes()
+    assert len(t) == 0
+    net.close()
+
+
+# ------------------------------------------------------- full-scale microcircuit
+
+
+@pytest.fixture(scope="module")
+def full(model):
+    wl = workload.WORKLOADS["pd_full"]
+    onet = oracle.build_network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed)
+    return wl, onet
+
+
+def test_full_scale_parity(model, full):
+    """Full microcircuit (77,169 neurons, 284,811,022 synapses) in the bench's launch
+    configuration: identical network, and an identical raster and state over the
+    first 1,200 steps (120 ms of biological time)."""
+    wl, onet = full
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed)
+    assert net.info().n_synapses == 284_811_022
+    _row_multisets_equal(onet, *_device_network(net))
+    steps = 1200
+    net.step(steps)
+    g_t, g_i = net.read_spikes()
+    sim = oracle.Sim(model, onet, wl.seed)
+    o_t, o_i = sim.run(steps)
+    assert len(o_t) > 0
+    assert np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
+    _assert_same_state(net, sim)
+    net.close()
+
+
+def test_full_scale_activity_band(model, full):
+    """The paper reports ~23 spiking neurons per step on average at full scale (a weak
+    band: flagged, not failed, outside 5..100 per step); the GPU run must stay free
+    of raster overflow over 1 s of biological time."""
+    wl, _ = full
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed)
+    net.step(10000)
+    t, i = net.read_spikes()
+    per_step = len(t) / 10000.0
+    assert per_step > 0.5
+    if not (5 <= per_step <= 100):
+        import warnings
+
+        warnings.warn(f"full-scale activity {per_step:.1f} spikes/step is outside the paper's band")
+    net.close()
