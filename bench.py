@@ -1,0 +1,371 @@
+"""Benchmark of the full-scale Potjans-Diesmann microcircuit step loop on GB300.
+
+One bench step = 1,000 simulation steps of 0.1 ms (100 ms of biological time) of the
+full microcircuit (77,169 neurons, 284,811,022 synapses, seed 1 + rank), so the
+default --steps 100 covers the paper's 10 s runs (§4).  Prints one JSON line.
+
+  value     recurrent synaptic events/s (sum of the spikers' out-degrees / seconds),
+            device-timed with CUDA events around snn_step_n graph replays
+  rtf       real-time factor = wall time / biological time (§4.2)
+  e2e       the same metric through the public API with the raster read back to
+            host memory every bench step (snn_step_n + snn_read_spikes)
+  roofline  the dominant kernel's algorithmic bytes per launch / its average
+            CUDA-event duration, against the measured HBM copy bandwidth
+  cpu_baseline  the CPU oracle (single thread) on a bounded sample of the workload
+
+--impl reference times the CPU oracle itself on the same workload (rank 0 only).
+Under torchrun with N > 1, every rank simulates its own circuit (replicas: the
+method has no data-path exchange on one circuit); value sums events over ranks and
+divides by the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workload  # noqa: E402
+
+TICKS_PER_STEP = 1000
+UPDATE_BYTES_PER_NEURON = 26   # U r/w 8 + I r/w 8 + R r/w 2 + ring slot read + clear 8
+EVENT_BYTES = 13               # tgt 4 + w 4 + delay 1 read + 4-byte ring reduction
+SPIKE_BYTES = 20               # row_ptr pair 16 + queue entry 4
+WORKLOAD = "pd_full"
+METRIC = "synaptic events/s and real-time factor (full microcircuit, 1 GB300), % HBM roofline"
+
+
+def _kernel_sources_hash() -> str:
+    import hashlib
+
+    csrc = os.path.join(ROOT, "paper_2405_02019_gb300", "csrc")
+    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("kernels.cu", "internal.hpp"))
+    return hashlib.sha256(src).hexdigest()[:16]
+
+
+def _recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu record, only if the kernel sources
+    are unchanged since it was taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernels_sha256_16") != _kernel_sources_hash() or kernel not in d:
+        return None
+    return d[kernel].get("dram_bytes_per_launch")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in self.rows for j in range(4) if r[3 + j].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _dist():
+    import torch.distributed as dist
+
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1 and not dist.is_initialized():
+        import torch
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _max_over_ranks(x: float, ws: int, device=None) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(x: float, ws: int, device=None) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def _barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def cpu_oracle_sample(model, wl, ticks: int):
+    """Time the oracle (single thread) on the first `ticks` steps of the workload."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    onet = oracle.build_network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed)
+    build_s = time.perf_counter() - t0
+    sim = oracle.Sim(model, onet, wl.seed)
+    t0 = time.perf_counter()
+    st, si = sim.run(ticks)
+    secs = time.perf_counter() - t0
+    outdeg = np.diff(onet.row_ptr)
+    events = int(outdeg[si].sum())
+    return {"value": events / secs, "unit": "synaptic events/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {ticks} steps ({ticks * 0.1:.0f} ms biological) of {wl.name}, seed {wl.seed}, "
+                      f"network build excluded ({build_s:.1f} s)",
+            "rtf": secs / (ticks * model.dt_ms * 1e-3), "seconds": secs, "events": events,
+            "spikes": int(len(st))}, onet, sim
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    model = workload.microcircuit_model()
+    wl = workload.WORKLOADS[WORKLOAD]
+    import oracle
+
+    oracle.build()
+    onet = oracle.build_network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed)
+    sim = oracle.Sim(model, onet, wl.seed)
+    outdeg = np.diff(onet.row_ptr)
+    ticks = args.reference_ticks
+    for _ in range(args.warmup):
+        sim.run(ticks)
+    events = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, si = sim.run(ticks)
+        events += int(outdeg[si].sum())
+    secs = time.perf_counter() - t0
+    value = events / secs
+    bio = args.steps * ticks * model.dt_ms * 1e-3
+    line = {
+        "impl": "reference", "metric": METRIC,
+        "value": value, "unit": "synaptic events/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32/i32", "data": "synthetic (PD microcircuit sampled from the paper's tables)",
+        "config": {"workload": f"{wl.name}: 77,169 neurons, 284,811,022 synapses, dt 0.1 ms, seed {wl.seed}",
+                   "ticks_per_step": ticks},
+        "rtf": secs / bio,
+        "cpu_baseline": {"value": value, "unit": "synaptic events/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{ticks} steps per bench step after {args.warmup * ticks} warm-up steps"},
+        "e2e": {"value": value, "unit": "synaptic events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2405_02019_gb300 as snn
+
+    model = workload.microcircuit_model()
+    wl = workload.WORKLOADS[WORKLOAD]
+    seed = wl.seed + rank
+    tps = args.ticks_per_step
+    t0 = time.perf_counter()
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, seed, steps_per_graph=tps,
+                      raster_capacity=1 << 25, device=dev)
+    build_s = time.perf_counter() - t0
+    info = net.info()
+    stream = torch.cuda.current_stream(dev)
+
+    # warm-up
+    net.step(args.warmup * tps)
+    net.read_spikes()
+    e0 = net.info().events_read
+    s0 = net.info().spikes_read
+
+    # device-timed region
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    _barrier(ws)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for _ in range(args.steps):
+            net.step(tps)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+    _barrier(ws)
+    ms = start.elapsed_time(end)
+    net.read_spikes()
+    inf = net.info()
+    events = inf.events_read - e0
+    spikes = inf.spikes_read - s0
+    secs_max = _max_over_ranks(ms / 1e3, ws, dev)
+    events_all = _sum_over_ranks(float(events), ws, dev)
+    value = events_all / secs_max
+    bio_s = args.steps * tps * model.dt_ms * 1e-3
+    rtf = secs_max / bio_s
+
+    # end to end through the public API: step + raster read into host memory per bench step
+    _barrier(ws)
+    torch.cuda.synchronize(dev)
+    e_e0 = net.info().events_read
+    d2h = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        net.step(tps)
+        st, si = net.read_spikes()
+        d2h += 8 * len(st) + 64
+    e2e_s = time.perf_counter() - t0
+    e2e_events = net.info().events_read - e_e0
+    e2e_s = _max_over_ranks(e2e_s, ws, dev)
+    e2e_value = _sum_over_ranks(float(e2e_events), ws, dev) / e2e_s
+
+    # per-kernel durations (CUDA events on the launching stream) for the roofline
+    prof_ticks = args.profile_ticks
+    net.read_spikes()
+    pe0, ps0 = net.info().events_read, net.info().spikes_read
+    ms_u, ms_d = net.profile_steps(prof_ticks)
+    net.read_spikes()
+    pe = net.info().events_read - pe0
+    pspk = net.info().spikes_read - ps0
+    n = info.n_neurons
+    upd_bytes = UPDATE_BYTES_PER_NEURON * n
+    dlv_bytes = (EVENT_BYTES * pe + SPIKE_BYTES * pspk) / prof_ticks
+    upd_gbs = upd_bytes / (ms_u / prof_ticks * 1e-3) / 1e9
+    dlv_gbs = dlv_bytes / (ms_d / prof_ticks * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    kernels = {
+        "k_update": {"avg_us": ms_u / prof_ticks * 1e3, "bytes_per_launch": upd_bytes, "gbs": upd_gbs,
+                     "share": ms_u / (ms_u + ms_d)},
+        "k_deliver": {"avg_us": ms_d / prof_ticks * 1e3, "bytes_per_launch": dlv_bytes, "gbs": dlv_gbs,
+                      "share": ms_d / (ms_u + ms_d), "events_per_launch": pe / prof_ticks,
+                      "spikes_per_launch": pspk / prof_ticks},
+    }
+    dom = "k_update" if ms_u >= ms_d else "k_deliver"
+    traffic = _recorded_traffic(dom)
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": kernels[dom]["gbs"] / peak, "traffic": traffic,
+                "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth, burst)"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu, _, _ = cpu_oracle_sample(model, wl, args.cpu_ticks)
+        try:
+            import multiprocessing
+
+            cpu["host_cores_available"] = multiprocessing.cpu_count()
+        except Exception:
+            pass
+
+    line = {
+        "metric": METRIC,
+        "value": value, "unit": "synaptic events/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs_max * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32/i32", "data": "synthetic (PD microcircuit sampled from the paper's tables)",
+        "config": {"workload": f"{wl.name}: 77,169 neurons, 284,811,022 synapses, dt 0.1 ms, seed {wl.seed}+rank",
+                   "ticks_per_step": tps, "bio_seconds": bio_s, "steps_per_graph": info.steps_per_graph,
+                   "deliver_blocks": info.deliver_blocks, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs larger than L2 (2.56 GB synapse store); ring and neuron state are L2-resident by design"},
+        "rtf": rtf, "realtime_x": 1.0 / rtf, "spikes_per_tick": spikes / (args.steps * tps),
+        "events_per_tick": events / (args.steps * tps),
+        "e2e": {"value": e2e_value, "unit": "synaptic events/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": d2h / args.steps,
+                "note": "network uploaded once by snn_build_network (setup, untimed as in the paper's RTF); "
+                        "every bench step enqueues 1,000 steps and reads the raster back to host memory"},
+        "gpu_launches": args.steps * (2 * tps + 1),
+        "roofline": roofline, "kernels": kernels,
+        "clocks": clk.summary(), "build_s": build_s,
+        "paper_context": {"fpga_best_rtf": 0.79, "hardware": "Intel Agilex 7 FPGA (horiz/multi/s)"},
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    net.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--ticks-per-step", type=int, default=TICKS_PER_STEP)
+    ap.add_argument("--profile-ticks", type=int, default=2000)
+    ap.add_argument("--cpu-ticks", type=int, default=2000)
+    ap.add_argument("--reference-ticks", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
