@@ -221,6 +221,56 @@ int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *
 /* Releases host-side state (not the caller's arena).  NULL is ignored. */
 void snn_destroy(snn_net *net);
 
+/*
+ * One simulation step that allocates no device memory (the paper has no counterpart:
+ * this is an embedding aid, not part of the method).
+ *
+ * For callers that may not call cudaMalloc -- a host application whose own allocator
+ * owns all device memory and does not let plug-ins allocate, or a control loop that
+ * cannot afford an allocation failing or stalling mid-run.  The caller passes every
+ * input and output buffer; the step's internal spike list and counter live in one
+ * fixed array inside the library (SNN_STATIC_MAX_NEURONS + 64 words, about 512 KB),
+ * which every GPU that loads the library holds until the process exits.
+ *
+ * Computes exactly one step `t` (0-based step index; the handle's own step counter is
+ * neither read nor advanced) of the network built as `net` (its constants, Poisson
+ * tables and population offsets), bit-identical to a step of snn_step_n:
+ *   io->row_ptr[n+1], syn_tgt/syn_w/syn_delay: the network in the layout of
+ *     snn_layout (rows padded to multiples of 4; syn_tgt/syn_w 16-byte aligned,
+ *     syn_delay 4-byte aligned); read only;
+ *   io->U, io->I (float), io->R (uint8): at least n rounded up to 4 entries, 16-byte
+ *     (R: 4-byte) aligned; read and written;
+ *   io->ring: int32 [64][ring_stride], ring_stride >= n, multiple of 4; read and written;
+ *   io->spikes: int32 [n] device output, this step's spiking neurons (unordered);
+ *   io->n_spikes: one int32 device output, their count.
+ * `seed` is the thalamic stream's seed (the spec's seed for parity with snn_step_n).
+ * Enqueued on `cuda_stream`; returns without waiting.
+ *
+ * The first call on a device looks up the device address of the fixed array
+ * (cudaGetSymbolAddress, with that device current); make that first call before any
+ * stream capture.  Every call reuses the same array and clears its counter first, so
+ * calls whose work overlaps on the GPU (different streams, or different handles at
+ * the same time) race and give wrong results: serialise them.
+ * Errors: SNN_EINVAL for more than SNN_STATIC_MAX_NEURONS neurons, a missing or
+ * misaligned buffer, a negative t; SNN_ECUDA on a failed CUDA call.
+ */
+#define SNN_STATIC_MAX_NEURONS 131072
+typedef struct snn_static_io {
+    const int64_t *row_ptr;
+    const int32_t *syn_tgt;
+    const int32_t *syn_w;
+    const uint8_t *syn_delay;
+    float *U;
+    float *I;
+    uint8_t *R;
+    int32_t *ring;
+    int64_t ring_stride;
+    int32_t *spikes;
+    int32_t *n_spikes;
+} snn_static_io;
+
+int snn_step_static(const snn_net *net, const snn_static_io *io, uint64_t seed, int64_t t, void *cuda_stream);
+
 /* Static description of a status code. */
 const char *snn_strerror(int code);
 

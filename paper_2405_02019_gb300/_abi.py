@@ -84,6 +84,17 @@ class snn_info(C.Structure):
     ]
 
 
+STATIC_MAX_NEURONS = 131072
+
+
+class snn_static_io(C.Structure):
+    _fields_ = [
+        ("row_ptr", C.c_void_p), ("syn_tgt", C.c_void_p), ("syn_w", C.c_void_p), ("syn_delay", C.c_void_p),
+        ("U", C.c_void_p), ("I", C.c_void_p), ("R", C.c_void_p), ("ring", C.c_void_p),
+        ("ring_stride", C.c_int64), ("spikes", C.c_void_p), ("n_spikes", C.c_void_p),
+    ]
+
+
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsnn.so")
 
 # name -> (restype, argtypes)
@@ -99,6 +110,7 @@ PROTOTYPES = {
     "snn_profile_steps": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]),
     "snn_destroy": (None, [C.c_void_p]),
+    "snn_step_static": (C.c_int, [C.c_void_p, C.POINTER(snn_static_io), C.c_uint64, C.c_int64, C.c_void_p]),
     "snn_strerror": (C.c_char_p, [C.c_int]),
     "snn_last_error": (C.c_char_p, []),
 }

@@ -34,6 +34,11 @@ int fail(int code, const std::string &msg)
 
 }  // namespace
 
+namespace snn {
+// Lets other translation units report through snn_last_error.
+void set_last_error(const char *msg) { g_last_error = msg; }
+}  // namespace snn
+
 struct snn_net {
     snn_spec spec{};
     snn::Constants c{};
