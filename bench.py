@@ -233,8 +233,10 @@ def run_gpu(args):
     seed = wl.seed + rank
     tps = args.ticks_per_step
     t0 = time.perf_counter()
+    engine = {"default": snn.ENGINE_DEFAULT, "graph": snn.ENGINE_GRAPH, "persistent": snn.ENGINE_PERSISTENT,
+              "pipelined": snn.ENGINE_PIPELINED}[args.engine]
     net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, seed, steps_per_graph=tps,
-                      raster_capacity=1 << 25, device=dev)
+                      raster_capacity=1 << 25, device=dev, engine=engine)
     build_s = time.perf_counter() - t0
     info = net.info()
     stream = torch.cuda.current_stream(dev)
@@ -304,7 +306,23 @@ def run_gpu(args):
                       "share": ms_d / (ms_u + ms_d), "events_per_launch": pe / prof_ticks,
                       "spikes_per_launch": pspk / prof_ticks},
     }
-    dom = "k_update" if ms_u >= ms_d else "k_deliver"
+    if info.engine == snn.ENGINE_PIPELINED:
+        step_bytes = upd_bytes + dlv_bytes
+        kernels = {"k_step": {"avg_us": ms_u / prof_ticks * 1e3, "bytes_per_launch": step_bytes,
+                              "gbs": step_bytes / (ms_u / prof_ticks * 1e-3) / 1e9, "share": 1.0,
+                              "events_per_launch": pe / prof_ticks, "spikes_per_launch": pspk / prof_ticks}}
+        dom = "k_step"
+    elif info.engine == snn.ENGINE_PERSISTENT:
+        # one cooperative launch per bench step: all of its steps' algorithmic bytes over its duration
+        per_launch = tps * (upd_bytes + (EVENT_BYTES * events + SPIKE_BYTES * spikes) / (args.steps * tps))
+        kernels["k_persistent"] = {"avg_us": secs_max * 1e6 / args.steps, "bytes_per_launch": per_launch,
+                                   "gbs": per_launch / (secs_max / args.steps) / 1e9, "share": 1.0,
+                                   "steps_per_launch": tps}
+        kernels["k_update"]["note"] = kernels["k_deliver"]["note"] = (
+            "graph-engine kernels timed one launch at a time for the per-phase split")
+        dom = "k_persistent"
+    else:
+        dom = "k_update" if ms_u >= ms_d else "k_deliver"
     traffic = _recorded_traffic(dom)
     roofline = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": peak, "unit": "GB/s",
                 "frac": kernels[dom]["gbs"] / peak, "traffic": traffic,
@@ -327,6 +345,8 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f32/i32", "data": "synthetic (PD microcircuit sampled from the paper's tables)",
         "config": {"workload": f"{wl.name}: 77,169 neurons, 284,811,022 synapses, dt 0.1 ms, seed {wl.seed}+rank",
                    "ticks_per_step": tps, "bio_seconds": bio_s, "steps_per_graph": info.steps_per_graph,
+                   "engine": {snn.ENGINE_GRAPH: "graph", snn.ENGINE_PERSISTENT: "persistent",
+                              snn.ENGINE_PIPELINED: "pipelined"}[info.engine],
                    "deliver_blocks": info.deliver_blocks, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (2.56 GB synapse store); ring and neuron state are L2-resident by design"},
         "rtf": rtf, "realtime_x": 1.0 / rtf, "spikes_per_tick": spikes / (args.steps * tps),
@@ -335,7 +355,8 @@ def run_gpu(args):
                 "d2h_bytes_per_step": d2h / args.steps,
                 "note": "network uploaded once by snn_build_network (setup, untimed as in the paper's RTF); "
                         "every bench step enqueues 1,000 steps and reads the raster back to host memory"},
-        "gpu_launches": args.steps * (2 * tps + 1),
+        "gpu_launches": args.steps * {snn.ENGINE_PERSISTENT: 1, snn.ENGINE_PIPELINED: tps + 1,
+                                      snn.ENGINE_GRAPH: 2 * tps + 1}[info.engine],
         "roofline": roofline, "kernels": kernels,
         "clocks": clk.summary(), "build_s": build_s,
         "paper_context": {"fpga_best_rtf": 0.79, "hardware": "Intel Agilex 7 FPGA (horiz/multi/s)"},
@@ -359,6 +380,7 @@ def main():
     ap.add_argument("--cpu-ticks", type=int, default=2000)
     ap.add_argument("--reference-ticks", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--engine", default="default", choices=["default", "graph", "persistent", "pipelined"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -107,8 +107,22 @@ typedef struct snn_custom_net {
  *   raster_capacity: spikes the device holds between reads (0 = 1<<24);
  *   deliver_blocks: CTAs of the delivery kernel (0 = 2 per SM);
  *   custom: NULL, or an explicit network (then the scales are ignored);
- *   n_threads: host threads for network construction (0 = all cores).
+ *   n_threads: host threads for network construction (0 = all cores);
+ *   engine: how the steps are scheduled; every engine gives the same raster and state:
+ *     SNN_ENGINE_PIPELINED (the default): one kernel per step, replayed from a CUDA
+ *       graph.  A spike decided at step s depends only on spikes of steps <= s-2
+ *       (input reaches U one step after it reaches I), so the kernel of step t
+ *       delivers step t's spikes while the same launch finishes step t's current
+ *       update and decides step t+1's spikes;
+ *     SNN_ENGINE_GRAPH: the two phases of Listing push2 as two kernels per step,
+ *       replayed from a CUDA graph;
+ *     SNN_ENGINE_PERSISTENT: one cooperative launch per batch of steps, the two
+ *       phases separated by bounded grid-wide barriers.
  */
+#define SNN_ENGINE_DEFAULT 0
+#define SNN_ENGINE_GRAPH 1
+#define SNN_ENGINE_PERSISTENT 2
+#define SNN_ENGINE_PIPELINED 3
 typedef struct snn_spec {
     uint32_t abi_version; /* must be SNN_ABI_VERSION */
     int32_t scale_n_permille;
@@ -118,6 +132,8 @@ typedef struct snn_spec {
     int64_t raster_capacity;
     int32_t deliver_blocks;
     int32_t n_threads;
+    int32_t engine;
+    int32_t reserved;
     snn_model model;
     const snn_custom_net *custom;
 } snn_spec;
@@ -133,7 +149,9 @@ typedef struct snn_sizes {
     int64_t raster_capacity;
 } snn_sizes;
 
-/* Byte offsets of the device buffers inside the arena (for inspection).  Layouts:
+/* Byte offsets of the device buffers inside the arena (for inspection).  U and R give
+ * the buffers that hold the state after the steps enqueued so far (the pipelined
+ * engine alternates between two buffers).  Layouts:
  * U, I float[n_neurons_padded]; R uint8[n_neurons_padded] (refractory steps left);
  * ring int32[64][n_neurons_padded]; row_ptr int64[n_neurons+1] into the padded
  * synapse arrays; syn_tgt, syn_w int32[n_synapses_padded], syn_delay uint8[...]
@@ -151,7 +169,7 @@ typedef struct snn_info {
     int64_t n_synapses;
     int64_t n_synapses_padded;
     int64_t t;            /* steps enqueued so far */
-    int64_t spikes_read;  /* spikes moved to the host so far */
+    int64_t spikes_read;  /* spikes of completed steps moved to the host so far */
     int64_t events_read;  /* recurrent synaptic events (sum of the senders' out-degrees) of those */
     int32_t n_pops;
     int32_t t_ref_steps;
@@ -164,8 +182,8 @@ typedef struct snn_info {
     int32_t chunks_per_row;
     int32_t steps_per_graph;
     int32_t deliver_blocks;
-    uint32_t device_error;         /* sticky device error bits (1 = raster overflow) */
-    int32_t reserved;
+    uint32_t device_error;         /* sticky device error bits (1 = raster overflow, 2 = barrier timeout) */
+    int32_t engine;                /* SNN_ENGINE_PIPELINED, SNN_ENGINE_GRAPH or SNN_ENGINE_PERSISTENT */
 } snn_info;
 
 typedef struct snn_net snn_net;
@@ -188,7 +206,8 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
 /* Enqueues n_steps steps (Listing push / push2 of §3.1; one step = dt) on
  * `cuda_stream` and returns without waiting.  n_steps = 0 is a no-op.
  * Errors: SNN_EINVAL (n_steps < 0), SNN_ESTATE (after a sticky device error),
- * SNN_ECUDA. */
+ * SNN_ECUDA.  A persistent-engine barrier that waits longer than 2 s records a device
+ * error that the next read reports as SNN_ETIMEOUT. */
 int snn_step_n(snn_net *net, int64_t n_steps, void *cuda_stream);
 
 /* Waits for the enqueued steps, moves the device raster to the host and returns
@@ -196,7 +215,8 @@ int snn_step_n(snn_net *net, int64_t n_steps, void *cuda_stream);
  * caller-allocated arrays of `capacity` entries; *n_written receives how many were
  * written (the rest stay for the next call).  With steps == neurons == NULL it only
  * reports the number of unread spikes.  Errors: SNN_EOVERFLOW if the raster filled
- * between reads (the dynamics after that point are invalid), SNN_ECUDA. */
+ * between reads (the dynamics after that point are invalid), SNN_ETIMEOUT if a
+ * persistent-engine barrier timed out, SNN_ECUDA. */
 int snn_read_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t capacity, int64_t *n_written);
 
 /* Waits for the enqueued steps and returns the mean firing rate (Hz) of each
@@ -214,8 +234,9 @@ int snn_get_layout(const snn_net *net, snn_layout *out);
 
 /* Runs n_steps steps kernel by kernel (no graph), timing each kernel with CUDA
  * events on `cuda_stream`, and returns after they finish.  ms_update / ms_deliver
- * receive the summed milliseconds of the update and delivery kernels.  Same
- * dynamics as snn_step_n.  Errors as snn_step_n. */
+ * receive the summed milliseconds of the update and delivery kernels (pipelined
+ * engine: of its one step kernel in ms_update, 0 in ms_deliver).  Same dynamics as
+ * snn_step_n.  Errors as snn_step_n. */
 int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *ms_update, double *ms_deliver);
 
 /* Releases host-side state (not the caller's arena).  NULL is ignored. */

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -54,6 +55,9 @@ struct snn_net {
     int update_grid = 0;
     int deliver_grid = 0;
     int steps_per_graph = 0;
+    int engine = SNN_ENGINE_GRAPH;
+    int persistent_grid = 0;
+    int step_grid = 0;
     cudaStream_t capture_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -74,11 +78,28 @@ namespace {
 int launch_steps_direct(snn_net *net, int64_t m, cudaStream_t st)
 {
     for (int64_t k = 0; k < m; ++k) {
-        snn::launch_update(net->args, static_cast<int>(k), net->update_grid, st);
-        snn::launch_deliver(net->args, static_cast<int>(k), net->deliver_grid, st);
+        if (net->engine == SNN_ENGINE_PIPELINED) {
+            snn::launch_step(net->args, static_cast<int>(k), net->step_grid, st);
+        } else {
+            snn::launch_update(net->args, static_cast<int>(k), net->update_grid, st);
+            snn::launch_deliver(net->args, static_cast<int>(k), net->deliver_grid, st);
+        }
     }
     snn::launch_advance(net->args.ctl, m, st);
     SNN_CUDA_TRY(cudaGetLastError());
+    return SNN_OK;
+}
+
+int launch_steps_persistent(snn_net *net, int64_t n, cudaStream_t st)
+{
+    while (n > 0) {
+        const int64_t m = std::min<int64_t>(n, snn::kMaxPersistentSteps);
+        SNN_CUDA_TRY(cudaMemsetAsync(net->arena + net->L.ctl + offsetof(snn::Ctl, bar), 0, sizeof(uint32_t), st));
+        const int e = snn::launch_persistent(net->args, m, net->persistent_grid, st);
+        if (e != 0)
+            return fail(SNN_ECUDA, std::string("cooperative launch: ") + cudaGetErrorString(static_cast<cudaError_t>(e)));
+        n -= m;
+    }
     return SNN_OK;
 }
 
@@ -87,8 +108,12 @@ int capture_graph(snn_net *net)
     SNN_CUDA_TRY(cudaStreamCreateWithFlags(&net->capture_stream, cudaStreamNonBlocking));
     SNN_CUDA_TRY(cudaStreamBeginCapture(net->capture_stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < net->steps_per_graph; ++k) {
-        snn::launch_update(net->args, k, net->update_grid, net->capture_stream);
-        snn::launch_deliver(net->args, k, net->deliver_grid, net->capture_stream);
+        if (net->engine == SNN_ENGINE_PIPELINED) {
+            snn::launch_step(net->args, k, net->step_grid, net->capture_stream);
+        } else {
+            snn::launch_update(net->args, k, net->update_grid, net->capture_stream);
+            snn::launch_deliver(net->args, k, net->deliver_grid, net->capture_stream);
+        }
     }
     snn::launch_advance(net->args.ctl, net->steps_per_graph, net->capture_stream);
     cudaError_t launch_err = cudaGetLastError();
@@ -151,6 +176,8 @@ int drain(snn_net *net)
         SNN_CUDA_TRY(cudaMemcpy(net->arena + net->L.ctl + offsetof(snn::Ctl, cursor), zero, sizeof(zero),
                                 cudaMemcpyHostToDevice));
     }
+    if (net->device_error & snn::kErrTimeout)
+        return fail(SNN_ETIMEOUT, "a grid barrier of the persistent engine timed out");
     if (net->device_error & snn::kErrRaster)
         return fail(SNN_EOVERFLOW, "device raster filled before it was read; raise raster_capacity");
     return SNN_OK;
@@ -296,10 +323,52 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         a.u_reset = net->c.u_reset;
         a.t_ref = net->c.t_ref;
         a.w_ext_fx = net->c.w_ext_fx;
+        a.barrier_timeout_ns = snn::kBarrierTimeoutNs;
+        a.barrier_extra = 0;
+        // Fault injection for tests of the bounded barrier wait: with SNN_FAULT=barrier_stall
+        // in the environment at build time, every barrier expects one arrival that never
+        // comes and gives up after 20 ms, so the run must end with SNN_ETIMEOUT.
+        if (const char *f = std::getenv("SNN_FAULT")) {
+            if (std::string(f) == "barrier_stall") {
+                a.barrier_extra = 1;
+                a.barrier_timeout_ns = 20000000ull;
+            }
+        }
         net->update_grid = snn::update_grid(net->n);
         net->deliver_grid = spec->deliver_blocks > 0 ? spec->deliver_blocks : 2 * net->num_sms;
         net->steps_per_graph = spec->steps_per_graph > 0 ? spec->steps_per_graph : 1000;
-        rc = capture_graph(net);
+        net->engine = spec->engine == SNN_ENGINE_DEFAULT ? SNN_ENGINE_PIPELINED : spec->engine;
+        if (net->engine == SNN_ENGINE_PERSISTENT) {
+            int coop = 0;
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, net->device);
+            const int per_sm = coop ? snn::persistent_blocks_per_sm() : 0;
+            if (per_sm < 1) {
+                snn_destroy(net);
+                return fail(SNN_ENOTSUP, "cooperative launch of the persistent engine is not available");
+            }
+            net->persistent_grid = net->num_sms;  // one CTA per SM (all co-resident)
+        }
+        if (net->engine == SNN_ENGINE_PIPELINED) {
+            // state "after 0 steps" is buffer 1; the first kernel decides step 0's spikes
+            net->step_grid = snn::step_grid(net->num_sms);
+            const int64_t quad_warps = ((net->n + 3) / 4 + 31) / 32;
+            a.neuron_warps = static_cast<int32_t>(
+                std::min<int64_t>(24, std::max<int64_t>(1, (quad_warps + net->step_grid - 1) / net->step_grid)));
+            a.U2 = reinterpret_cast<float *>(A + L.U2);
+            a.R2 = A + L.R2;
+            a.queue = reinterpret_cast<snn::QueueEntry *>(A + L.queue);
+            cuda_ok(cudaMemcpyAsync(A + L.U2, u0.data(), 4 * net->npad, cudaMemcpyHostToDevice, st), "U2");
+            cuda_ok(cudaMemsetAsync(A + L.R2, 0, net->npad, st), "R2");
+            cuda_ok(cudaMemsetAsync(A + L.queue, 0xFF, 3 * sizeof(snn::QueueEntry) * net->npad, st), "queue");
+            snn::launch_prime(a, net->step_grid, st);
+            cuda_ok(cudaGetLastError(), "prime launch");
+            cuda_ok(cudaStreamSynchronize(st), "prime");
+            if (rc != SNN_OK) {
+                snn_destroy(net);
+                return rc;
+            }
+        }
+        rc = (net->engine == SNN_ENGINE_GRAPH || net->engine == SNN_ENGINE_PIPELINED) ? capture_graph(net) : SNN_OK;
         if (rc == SNN_OK && cudaEventCreateWithFlags(&net->ev_done, cudaEventDisableTiming) != cudaSuccess)
             rc = fail(SNN_ECUDA, "event create");
         if (rc != SNN_OK) {
@@ -321,12 +390,17 @@ int snn_step_n(snn_net *net, int64_t n_steps, void *cuda_stream)
     if (net->device_error) return fail(SNN_ESTATE, "a previous device error is pending");
     if (n_steps == 0) return SNN_OK;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    const int64_t full = n_steps / net->steps_per_graph;
-    const int64_t rem = n_steps % net->steps_per_graph;
-    for (int64_t g = 0; g < full; ++g) SNN_CUDA_TRY(cudaGraphLaunch(net->graph_exec, st));
-    if (rem > 0) {
-        int rc = launch_steps_direct(net, rem, st);
+    if (net->engine == SNN_ENGINE_PERSISTENT) {
+        const int rc = launch_steps_persistent(net, n_steps, st);
         if (rc) return rc;
+    } else {
+        const int64_t full = n_steps / net->steps_per_graph;
+        const int64_t rem = n_steps % net->steps_per_graph;
+        for (int64_t g = 0; g < full; ++g) SNN_CUDA_TRY(cudaGraphLaunch(net->graph_exec, st));
+        if (rem > 0) {
+            const int rc = launch_steps_direct(net, rem, st);
+            if (rc) return rc;
+        }
     }
     SNN_CUDA_TRY(cudaEventRecord(net->ev_done, st));
     net->ev_recorded = true;
@@ -349,9 +423,14 @@ int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *
         const int64_t m = std::min(batch, n_steps - done);
         for (int64_t k = 0; k < m; ++k) {
             cudaEventRecord(ev[3 * k], st);
-            snn::launch_update(net->args, static_cast<int>(k), net->update_grid, st);
-            cudaEventRecord(ev[3 * k + 1], st);
-            snn::launch_deliver(net->args, static_cast<int>(k), net->deliver_grid, st);
+            if (net->engine == SNN_ENGINE_PIPELINED) {
+                snn::launch_step(net->args, static_cast<int>(k), net->step_grid, st);
+                cudaEventRecord(ev[3 * k + 1], st);
+            } else {
+                snn::launch_update(net->args, static_cast<int>(k), net->update_grid, st);
+                cudaEventRecord(ev[3 * k + 1], st);
+                snn::launch_deliver(net->args, static_cast<int>(k), net->deliver_grid, st);
+            }
             cudaEventRecord(ev[3 * k + 2], st);
         }
         snn::launch_advance(net->args.ctl, m, st);
@@ -383,7 +462,12 @@ int snn_read_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t capa
     if (!net || !n_written) return fail(SNN_EINVAL, "null argument");
     *n_written = 0;
     int rc = drain(net);
-    const int64_t avail = static_cast<int64_t>(net->hist_t.size()) - net->read_pos;
+    // the pipelined engine has already decided (and recorded) the next step's spikes:
+    // return only spikes of completed steps
+    const int64_t done_end =
+        std::lower_bound(net->hist_t.begin(), net->hist_t.end(), static_cast<int32_t>(std::min<int64_t>(net->t, INT32_MAX))) -
+        net->hist_t.begin();
+    const int64_t avail = std::max<int64_t>(0, done_end - net->read_pos);
     if (!steps && !neurons) {
         *n_written = avail;
         return rc;
@@ -403,6 +487,7 @@ int snn_read_rates(snn_net *net, int64_t t_begin, int64_t t_end, double *pop_rat
 {
     if (!net || !pop_rates_hz) return fail(SNN_EINVAL, "null argument");
     if (t_begin < 0 || t_end <= t_begin) return fail(SNN_EINVAL, "empty or negative window");
+    if (t_end > net->t) return fail(SNN_EINVAL, "window ends after the steps enqueued so far");
     int rc = drain(net);
     const int P = net->spec.model.n_pops;
     std::vector<int64_t> pop_cnt(P, 0);
@@ -432,8 +517,15 @@ int snn_get_info(const snn_net *net, snn_info *out)
     out->n_synapses = net->n_syn;
     out->n_synapses_padded = net->n_syn_padded;
     out->t = net->t;
-    out->spikes_read = static_cast<int64_t>(net->hist_t.size());
-    out->events_read = net->events_read;
+    // count spikes of completed steps only (the pipelined engine records the next
+    // step's spikes one launch early)
+    const int64_t done_end =
+        std::lower_bound(net->hist_t.begin(), net->hist_t.end(), static_cast<int32_t>(std::min<int64_t>(net->t, INT32_MAX))) -
+        net->hist_t.begin();
+    int64_t pending_events = 0;
+    for (size_t j = static_cast<size_t>(done_end); j < net->hist_t.size(); ++j) pending_events += net->out_degree[net->hist_i[j]];
+    out->spikes_read = done_end;
+    out->events_read = net->events_read - pending_events;
     out->n_pops = net->spec.model.n_pops;
     out->t_ref_steps = net->c.t_ref;
     for (int b = 0; b <= SNN_MAX_POPS; ++b)
@@ -454,6 +546,7 @@ int snn_get_info(const snn_net *net, snn_info *out)
     out->steps_per_graph = net->steps_per_graph;
     out->deliver_blocks = net->deliver_grid;
     out->device_error = net->device_error;
+    out->engine = net->engine;
     return SNN_OK;
 }
 
@@ -463,9 +556,10 @@ int snn_get_layout(const snn_net *net, snn_layout *out)
     const snn::Layout &L = net->L;
     out->ctl = L.ctl;
     out->params = L.tables;
-    out->U = L.U;
+    const bool second = net->engine == SNN_ENGINE_PIPELINED && ((net->t - 1) & 1);
+    out->U = second ? L.U2 : L.U;
     out->I = L.I;
-    out->R = L.R;
+    out->R = second ? L.R2 : L.R;
     out->ring = L.ring;
     out->row_ptr = L.row_ptr;
     out->syn_tgt = L.syn_tgt;

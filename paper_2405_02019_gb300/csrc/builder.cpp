@@ -166,7 +166,7 @@ bool validate_spec(const snn_spec &spec, std::string &why)
     for (int b = 0; b < m.n_pops; ++b) {
         if (!(m.k_ext[b] >= 0)) return fail("k_ext must be >= 0");
         const double lam = m.k_ext[b] * m.nu_th_hz * m.dt_ms * 1e-3;
-        if (lam > 8.0) return fail("thalamic mean per step above 8 exceeds the Poisson table");
+        if (lam > 4.0) return fail("thalamic mean per step above 4 exceeds the Poisson table's accuracy");
         if (m.n_full[b] < 0) return fail("n_full must be >= 0");
     }
     for (int o = 0; o < m.n_overrides; ++o)
@@ -176,6 +176,7 @@ bool validate_spec(const snn_spec &spec, std::string &why)
         return fail("raster_capacity out of [0, 2^31-1]");
     if (spec.steps_per_graph < 0 || spec.steps_per_graph > 100000) return fail("steps_per_graph out of [0, 100000]");
     if (spec.deliver_blocks < 0 || spec.deliver_blocks > 65535) return fail("deliver_blocks out of range");
+    if (spec.engine < SNN_ENGINE_DEFAULT || spec.engine > SNN_ENGINE_PIPELINED) return fail("unknown engine");
     if (spec.custom) {
         const snn_custom_net &c = *spec.custom;
         if (c.n_neurons < 1 || c.n_neurons > (int64_t{1} << 30)) return fail("custom n_neurons out of [1, 2^30]");
@@ -230,6 +231,9 @@ Layout make_layout(const snn_spec &spec)
     L.syn_d = o; o = up(o + L.syn_padded_max + 16);
     L.rast_nrn = o; o = up(o + 4 * L.rast_cap);
     L.rast_t = o; o = up(o + 4 * L.rast_cap);
+    L.U2 = o; o = up(o + 4 * L.npad);
+    L.R2 = o; o = up(o + L.npad);
+    L.queue = o; o = up(o + uint64_t{3} * sizeof(QueueEntry) * L.npad);
     L.total = o;
     return L;
 }

@@ -17,7 +17,13 @@ constexpr int kRowAlign = 4;                 // synapse rows padded to whole int
 constexpr int kChunk = 256;                  // synapses per delivery work item (32 lanes x 2 quads)
 constexpr int kUpdateThreads = 128;          // 4 neurons per thread
 constexpr int kDeliverThreads = 256;
+constexpr int kPersistThreads = 1024;        // one CTA per SM in the persistent engine
+constexpr int kStepDeliverWarps = 8;         // delivery warps per CTA of the pipelined step kernel
+constexpr int kStepMaxThreads = 1024;
 constexpr uint32_t kErrRaster = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;  // default bound of every grid-barrier wait
+constexpr int64_t kMaxPersistentSteps = 1 << 20;        // steps per cooperative launch
 
 // Device control block (first bytes of the arena).
 struct alignas(64) Ctl {
@@ -25,7 +31,18 @@ struct alignas(64) Ctl {
     uint32_t cursor;         // spikes appended to the raster since the last drain
     uint32_t step_begin[2];  // raster index where step t's spikes start, by t mod 2
     uint32_t err;            // sticky error bits
-    uint32_t pad[10];
+    uint32_t bar;            // grid-barrier arrivals of the running persistent launch
+    uint32_t qcnt[3];        // pipelined engine: spikes queued for step s in queue s mod 3
+    uint32_t pad[6];
+};
+
+// Pipelined engine: one queue entry per spike of a step, written by the thread that
+// decided the spike, consumed by the next kernel's delivery warps.
+struct alignas(16) QueueEntry {
+    uint32_t row_quad;   // first synapse of the row / 4
+    uint32_t len_quads;  // padded row length / 4
+    int32_t neuron;
+    int32_t step;        // low 32 bits of the step index (tells fresh entries from stale ones)
 };
 
 // Tables the update kernel stages in shared memory (in the arena, read-only).
@@ -58,6 +75,12 @@ struct StepArgs {
     float p11, p21, p22, theta, u_reset;
     int32_t t_ref;
     int32_t w_ext_fx;
+    uint64_t barrier_timeout_ns;  // bound of each grid-barrier wait (persistent engine)
+    uint32_t barrier_extra;       // arrivals expected beyond the grid (0; 1 only for the stall test)
+    int32_t neuron_warps;         // pipelined engine: neuron warps per CTA
+    float *U2;                    // pipelined engine: second U / R buffers (state after A(s) in buffer s mod 2)
+    uint8_t *R2;
+    QueueEntry *queue;            // pipelined engine: 3 queues of npad entries
 };
 
 // Host constants of one model (§2.2).
@@ -87,7 +110,7 @@ struct HostNetwork {
 
 // Arena layout for a spec.
 struct Layout {
-    uint64_t ctl, tables, U, I, R, ring, row_ptr, syn_tgt, syn_w, syn_d, rast_nrn, rast_t, total;
+    uint64_t ctl, tables, U, I, R, ring, row_ptr, syn_tgt, syn_w, syn_d, rast_nrn, rast_t, U2, R2, queue, total;
     int64_t npad, syn_padded_max, rast_cap;
 };
 
@@ -107,5 +130,11 @@ void launch_update(const StepArgs &a, int k, int grid, void *stream);
 void launch_deliver(const StepArgs &a, int k, int grid, void *stream);
 void launch_advance(Ctl *ctl, int64_t m, void *stream);
 int update_grid(int64_t n);
+int persistent_blocks_per_sm();
+int launch_persistent(const StepArgs &a, int64_t n_steps, int grid, void *stream);
+void launch_step(const StepArgs &a, int k, int grid, void *stream);   // pipelined: B(t), A(t+1) and D(t)
+void launch_prime(const StepArgs &a, int grid, void *stream);         // pipelined: A(0)
+int step_grid(int num_sms);
+int step_threads(const StepArgs &a);
 
 }  // namespace snn

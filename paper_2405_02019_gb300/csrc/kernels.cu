@@ -1,23 +1,28 @@
-// Device side of one simulation step (sm_103a).
+// Device side of the simulation step (sm_103a).
 //
-// k_update  -- Listing push of §3.1, phase 1, for every neuron, fused with the
-//              ring read of §3.2 and the spike queue of Listing push2:
-//                in   = W[t mod 64][i] + T(t, i) * w_ext      (int32, 2^-12 pA units)
-//                W[t mod 64][i] = 0
-//                if R == 0: x = p22 U + p21 I; spike if x >= theta (then x = reset, R = t_ref); U = x
-//                else:      U = reset; R -= 1
-//                I = p11 I + in * 2^-12
-//              T is Poisson(nu_th K dt) by CDF inversion of one Philox word (§2.2).
-//              Spikers are compacted warp by warp (one atomic per warp with spikes)
-//              into the raster, which doubles as the step's spike queue.
-// k_deliver -- Listing push2 of §3.1, phase 2: every queued spiker's row (sorted by
-//              delay, §3.5) is cut into 256-synapse chunks; a warp streams a chunk
-//              with 16-byte loads and adds each weight into W[(t + d) mod 64][target]
-//              with a fire-and-forget int32 reduction (order-independent).
-// k_advance -- moves the step counter after a batch of steps.
+// Phase 1 (Listing push of §3.1, fused with the ring read of §3.2 and the spike queue
+// of Listing push2), for every neuron:
+//     in   = W[t mod 64][i] + T(t, i) * w_ext      (int32, 2^-12 pA units)
+//     W[t mod 64][i] = 0
+//     if R == 0: x = p22 U + p21 I; spike if x >= theta (then x = reset, R = t_ref); U = x
+//     else:      U = reset; R -= 1
+//     I = p11 I + in * 2^-12
+// T is Poisson(nu_th K dt) by CDF inversion of one Philox word (§2.2).  Spikers are
+// compacted warp by warp (one atomic per warp with spikes) into the raster, which is
+// also the step's spike queue.
+// Phase 2 (Listing push2 of §3.1): every queued spiker's row (sorted by delay, §3.5)
+// is cut into 256-synapse chunks; a warp streams a chunk with 16-byte loads and adds
+// each weight into W[(t + d) mod 64][target] with a fire-and-forget int32 reduction,
+// so the order of delivery cannot change the result.
 //
-// No FMA anywhere in the neuron arithmetic: __fmul_rn / __fadd_rn round every
-// product and sum on its own, matching the host reference bit for bit.
+// Two engines run these phases:
+//   k_update + k_deliver -- one kernel per phase, replayed from a CUDA graph;
+//   k_persistent         -- one cooperative launch for a batch of steps, the phases
+//                           separated by grid-wide barriers whose spin-waits are
+//                           bounded (on timeout the kernel records an error and exits).
+//
+// No FMA in the neuron arithmetic: __fmul_rn / __fadd_rn round every product and sum
+// on its own, which is what makes the raster reproducible bit for bit.
 #include <cuda_runtime.h>
 
 #include "internal.hpp"
@@ -32,11 +37,51 @@ __device__ __forceinline__ void red_add_s32(int32_t *addr, int32_t v)
     asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(addr), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t v;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+    return v;
+}
+
 // Streaming 16-byte load of read-once data (evict-first in L1/L2).
 __device__ __forceinline__ int4 ld_stream4(const int32_t *p) { return __ldcs(reinterpret_cast<const int4 *>(p)); }
 __device__ __forceinline__ uint32_t ld_stream_u32(const uint8_t *p)
 {
     return __ldcs(reinterpret_cast<const unsigned int *>(p));
+}
+
+// Global warp number with consecutive numbers on consecutive CTAs, so that a short
+// list of work items spreads over all SMs instead of filling the first CTAs.
+__device__ __forceinline__ int64_t spread_warp()
+{
+    return static_cast<int64_t>(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+}
+
+__device__ __forceinline__ void red_release_add_u32(uint32_t *addr, uint32_t v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(addr), "r"(v) : "memory");
+}
+
+struct SharedTables {
+    uint64_t thr[SNN_MAX_POPS * kPK];
+    int64_t off[SNN_MAX_POPS + 1];
+    int n_pops;
+};
+
+__device__ __forceinline__ void stage_tables(const StepArgs &a, SharedTables &s)
+{
+    for (int j = threadIdx.x; j < SNN_MAX_POPS * kPK; j += blockDim.x) s.thr[j] = (&a.tables->thresholds[0][0])[j];
+    if (threadIdx.x <= SNN_MAX_POPS) s.off[threadIdx.x] = a.tables->pop_off[threadIdx.x];
+    if (threadIdx.x == 0) s.n_pops = a.tables->n_pops;
+    __syncthreads();
 }
 
 __device__ __forceinline__ int32_t neuron_step(const StepArgs &a, float &u, float &cur, uint32_t &r, int32_t in)
@@ -58,57 +103,48 @@ __device__ __forceinline__ int32_t neuron_step(const StepArgs &a, float &u, floa
     return spike;
 }
 
-__global__ void __launch_bounds__(kUpdateThreads) k_update(const StepArgs a, const int k)
+// Phase 1 for neurons 4q .. 4q+3 (those below n).  The ring row is read through L2
+// (other SMs add into it between steps).
+__device__ __forceinline__ void update_quad(const StepArgs &a, const SharedTables &s, int64_t t, int64_t q,
+                                            int32_t spk[4])
 {
-    __shared__ uint64_t s_thr[SNN_MAX_POPS * kPK];
-    __shared__ int64_t s_off[SNN_MAX_POPS + 1];
-    __shared__ int s_npops;
-    for (int j = threadIdx.x; j < SNN_MAX_POPS * kPK; j += blockDim.x)
-        s_thr[j] = (&a.tables->thresholds[0][0])[j];
-    if (threadIdx.x <= SNN_MAX_POPS) s_off[threadIdx.x] = a.tables->pop_off[threadIdx.x];
-    if (threadIdx.x == 0) s_npops = a.tables->n_pops;
-    __syncthreads();
-
-    const int64_t t = a.ctl->t_base + k;
-    const int64_t slot = t & kDMask;
-    const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;  // neuron quad
     const int64_t i0 = q * 4;
-    int32_t spk[4] = {0, 0, 0, 0};
-
-    if (i0 < a.n) {
-        float4 u4 = *reinterpret_cast<const float4 *>(a.U + i0);
-        float4 c4 = *reinterpret_cast<const float4 *>(a.I + i0);
-        uint32_t r4 = *reinterpret_cast<const uint32_t *>(a.R + i0);
-        int32_t *wrow = a.ring + slot * a.npad + i0;
-        const int4 w4 = *reinterpret_cast<const int4 *>(wrow);
-        *reinterpret_cast<int4 *>(wrow) = make_int4(0, 0, 0, 0);
-        const Block4 rnd = philox4x64_10(static_cast<uint64_t>(t), static_cast<uint64_t>(q), 0, 0, a.seed,
-                                         kStreamThalamic);
-        float uu[4] = {u4.x, u4.y, u4.z, u4.w};
-        float cc[4] = {c4.x, c4.y, c4.z, c4.w};
-        const int32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
-        uint32_t rr[4] = {r4 & 0xFFu, (r4 >> 8) & 0xFFu, (r4 >> 16) & 0xFFu, r4 >> 24};
-        int b = 0;
+    const int64_t slot = t & kDMask;
+    float4 u4 = *reinterpret_cast<const float4 *>(a.U + i0);
+    float4 c4 = *reinterpret_cast<const float4 *>(a.I + i0);
+    const uint32_t r4 = *reinterpret_cast<const uint32_t *>(a.R + i0);
+    int32_t *wrow = a.ring + slot * a.npad + i0;
+    const int4 w4 = __ldcg(reinterpret_cast<const int4 *>(wrow));
+    *reinterpret_cast<int4 *>(wrow) = make_int4(0, 0, 0, 0);
+    const Block4 rnd =
+        philox4x64_10(static_cast<uint64_t>(t), static_cast<uint64_t>(q), 0, 0, a.seed, kStreamThalamic);
+    float uu[4] = {u4.x, u4.y, u4.z, u4.w};
+    float cc[4] = {c4.x, c4.y, c4.z, c4.w};
+    const int32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
+    uint32_t rr[4] = {r4 & 0xFFu, (r4 >> 8) & 0xFFu, (r4 >> 16) & 0xFFu, r4 >> 24};
+    int b = 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int64_t i = i0 + j;
-            if (i < a.n) {
-                while (b + 1 < s_npops && i >= s_off[b + 1]) ++b;
-                const uint64_t v = rnd.w[j] >> 1;
-                const uint64_t *thr = s_thr + b * kPK;
-                uint32_t T = 0;
-                while (T < static_cast<uint32_t>(kPK) && v >= thr[T]) ++T;
-                const int32_t in = static_cast<int32_t>(static_cast<uint32_t>(ww[j]) +
-                                                        T * static_cast<uint32_t>(a.w_ext_fx));
-                spk[j] = neuron_step(a, uu[j], cc[j], rr[j], in);
-            }
+    for (int j = 0; j < 4; ++j) {
+        const int64_t i = i0 + j;
+        if (i < a.n) {
+            while (b + 1 < s.n_pops && i >= s.off[b + 1]) ++b;
+            const uint64_t v = rnd.w[j] >> 1;
+            const uint64_t *thr = s.thr + b * kPK;
+            uint32_t T = 0;
+            while (T < static_cast<uint32_t>(kPK) && v >= thr[T]) ++T;
+            const int32_t in =
+                static_cast<int32_t>(static_cast<uint32_t>(ww[j]) + T * static_cast<uint32_t>(a.w_ext_fx));
+            spk[j] = neuron_step(a, uu[j], cc[j], rr[j], in);
         }
-        *reinterpret_cast<float4 *>(a.U + i0) = make_float4(uu[0], uu[1], uu[2], uu[3]);
-        *reinterpret_cast<float4 *>(a.I + i0) = make_float4(cc[0], cc[1], cc[2], cc[3]);
-        *reinterpret_cast<uint32_t *>(a.R + i0) = rr[0] | (rr[1] << 8) | (rr[2] << 16) | (rr[3] << 24);
     }
+    *reinterpret_cast<float4 *>(a.U + i0) = make_float4(uu[0], uu[1], uu[2], uu[3]);
+    *reinterpret_cast<float4 *>(a.I + i0) = make_float4(cc[0], cc[1], cc[2], cc[3]);
+    *reinterpret_cast<uint32_t *>(a.R + i0) = rr[0] | (rr[1] << 8) | (rr[2] << 16) | (rr[3] << 24);
+}
 
-    // warp-aggregated append of this step's spikers to the raster / spike queue
+// Warp-collective (every lane must call): append the warp's spikers to the raster.
+__device__ __forceinline__ void append_spikes(const StepArgs &a, int64_t t, int64_t i0, const int32_t spk[4])
+{
     const int lane = threadIdx.x & 31;
     const int cnt = spk[0] + spk[1] + spk[2] + spk[3];
     int incl = cnt;
@@ -118,45 +154,39 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const StepArgs a, con
         if (lane >= o) incl += v;
     }
     const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    if (total > 0) {
-        uint32_t base = 0;
-        if (lane == 31) base = atomicAdd(&a.ctl->cursor, static_cast<uint32_t>(total));
-        base = __shfl_sync(0xFFFFFFFFu, base, 31);
-        uint32_t pos = base + static_cast<uint32_t>(incl - cnt);
+    if (total == 0) return;
+    uint32_t base = 0;
+    if (lane == 31) base = atomicAdd(&a.ctl->cursor, static_cast<uint32_t>(total));
+    base = __shfl_sync(0xFFFFFFFFu, base, 31);
+    uint32_t pos = base + static_cast<uint32_t>(incl - cnt);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (spk[j]) {
-                if (pos < a.rast_cap) {
-                    a.rast_nrn[pos] = static_cast<int32_t>(i0 + j);
-                    a.rast_t[pos] = static_cast<int32_t>(t);
-                } else {
-                    atomicOr(&a.ctl->err, kErrRaster);
-                }
-                ++pos;
+    for (int j = 0; j < 4; ++j) {
+        if (spk[j]) {
+            if (pos < a.rast_cap) {
+                a.rast_nrn[pos] = static_cast<int32_t>(i0 + j);
+                a.rast_t[pos] = static_cast<int32_t>(t);
+            } else {
+                atomicOr(&a.ctl->err, kErrRaster);
             }
+            ++pos;
         }
     }
 }
 
-__global__ void __launch_bounds__(kDeliverThreads) k_deliver(const StepArgs a, const int k)
+// Phase 2 for the spikers queued in raster[begin, end), work items grid-strided over
+// warps: item = (spiker, 256-synapse chunk of its row).
+__device__ __forceinline__ void deliver_range(const StepArgs &a, int64_t t, uint32_t begin, uint32_t end,
+                                              int64_t warp, int64_t nwarps)
 {
-    const int64_t t = a.ctl->t_base + k;
-    const uint32_t cur = a.ctl->cursor;
-    const uint32_t begin = a.ctl->step_begin[t & 1];
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->step_begin[(t + 1) & 1] = cur;
-    const uint32_t end = cur < a.rast_cap ? cur : a.rast_cap;
     const int64_t nspk = end > begin ? static_cast<int64_t>(end - begin) : 0;
     const int64_t items = nspk * a.chunks_per_row;
     const int lane = threadIdx.x & 31;
-    const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
     int32_t *const ring = a.ring;
     const int64_t npad = a.npad;
-
     for (int64_t it = warp; it < items; it += nwarps) {
         const int64_t j = it / a.chunks_per_row;
         const int64_t c = it - j * a.chunks_per_row;
-        const int32_t s = a.rast_nrn[begin + j];
+        const int32_t s = __ldcg(a.rast_nrn + begin + j);
         const int64_t rs = a.row_ptr[s];
         const int64_t re = a.row_ptr[s + 1];
         const int64_t off = rs + c * kChunk;
@@ -188,9 +218,340 @@ __global__ void __launch_bounds__(kDeliverThreads) k_deliver(const StepArgs a, c
     }
 }
 
+__global__ void __launch_bounds__(kUpdateThreads) k_update(const StepArgs a, const int k)
+{
+    __shared__ SharedTables s;
+    stage_tables(a, s);
+    const int64_t t = a.ctl->t_base + k;
+    const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    int32_t spk[4] = {0, 0, 0, 0};
+    if (q * 4 < a.n) update_quad(a, s, t, q, spk);
+    append_spikes(a, t, q * 4, spk);
+}
+
+__global__ void __launch_bounds__(kDeliverThreads) k_deliver(const StepArgs a, const int k)
+{
+    const int64_t t = a.ctl->t_base + k;
+    const uint32_t cur = a.ctl->cursor;
+    const uint32_t begin = a.ctl->step_begin[t & 1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->step_begin[(t + 1) & 1] = cur;
+    const uint32_t end = cur < a.rast_cap ? cur : a.rast_cap;
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    deliver_range(a, t, begin, end, spread_warp(), nwarps);
+}
+
 __global__ void k_advance(Ctl *ctl, int64_t m) { ctl->t_base += m; }
 
+// Grid-wide barrier of a cooperative launch: the `index`-th barrier of the launch
+// waits until all gridDim.x blocks have arrived index times.  The wait is bounded by
+// a.barrier_timeout_ns; on timeout the error bit is set (which releases every other
+// waiting block too) and false returned.
+__device__ __forceinline__ bool grid_barrier(const StepArgs &a, Ctl *ctl, uint32_t index)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        // the CTA barrier above orders the block's writes before this release
+        red_release_add_u32(&ctl->bar, 1u);
+        const uint32_t target = index * gridDim.x + a.barrier_extra;
+        if (ld_acquire_u32(&ctl->bar) < target) {
+            const uint64_t t0 = global_ns();
+            uint32_t spins = 0;
+            while (ld_acquire_u32(&ctl->bar) < target) {
+                if ((++spins & 255u) == 0 && global_ns() - t0 > a.barrier_timeout_ns) {
+                    atomicOr(&ctl->err, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+                if ((spins & 63u) == 0 && (ld_acquire_u32(&ctl->err) & kErrTimeout)) {
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kPersistThreads, 1) k_persistent(const StepArgs a, const int64_t n_steps)
+{
+    __shared__ SharedTables s;
+    stage_tables(a, s);
+    Ctl *ctl = a.ctl;
+    const int64_t t0 = ctl->t_base;
+    uint32_t begin = ctl->step_begin[t0 & 1];
+    const int64_t nquads = (a.n + 3) / 4;
+    const int64_t quad_warps = (nquads + 31) / 32;
+    const int64_t warp = spread_warp();
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    uint32_t nbar = 0;
+    for (int64_t st = 0; st < n_steps; ++st) {
+        const int64_t t = t0 + st;
+        // phase 1: warp g updates quads 32g .. 32g+31 (coalesced), warps spread over SMs
+        for (int64_t g = warp; g < quad_warps; g += nwarps) {
+            const int64_t q = g * 32 + lane;
+            int32_t spk[4] = {0, 0, 0, 0};
+            if (q < nquads) update_quad(a, s, t, q, spk);
+            append_spikes(a, t, q * 4, spk);
+        }
+        if (!grid_barrier(a, ctl, ++nbar)) return;
+        const uint32_t cur = ld_acquire_u32(&ctl->cursor);
+        const uint32_t end = cur < a.rast_cap ? cur : a.rast_cap;
+        deliver_range(a, t, begin, end, warp, nwarps);
+        begin = cur;
+        if (!grid_barrier(a, ctl, ++nbar)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->t_base = t0 + n_steps;
+        ctl->step_begin[(t0 + n_steps) & 1] = begin;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined engine: one kernel per step.
+//
+// In the recurrence a spike decided at step s uses I after step s-1, which already
+// holds W[s-1]; W[s-1] only receives spikes of steps <= s-2.  So the spike decision
+// of step t+1 (A(t+1)) needs the current update of step t (B(t): I <- p11 I + W[t] +
+// T w_ext) but not the delivery of step t's spikes (D(t), which writes slots t+1 ..
+// t+63 and is read from step t+1 on).  Kernel K_t therefore runs, concurrently:
+//   neuron warps:   B(t) then A(t+1) for their neurons (same thread, program order);
+//   delivery warps: D(t) for the spikes of step t decided by K_{t-1}.
+// Each neuron still sees A(0), B(0), A(1), B(1), ... in order, so the arithmetic is
+// the same as the two-phase engines.  U and R after A(s) live in buffer s mod 2 (the
+// state after s steps is in buffer (s-1) mod 2); the spikes of step s are queued in
+// queue s mod 3 by the thread that decided them, with their row bounds, and their
+// rows are prefetched into L2 for the next kernel's delivery warps.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Neuron part for quad q: B(t) (unless do_b is false: the first kernel, t = -1) then
+// A(t+1).  Warp-collective: every lane must call it (lanes without a quad pass valid=false).
+__device__ __forceinline__ void pipe_quad(const StepArgs &a, const SharedTables &s, int64_t t, int64_t q,
+                                          bool valid, bool do_b)
+{
+    const int64_t i0 = q * 4;
+    const int64_t sn = t + 1;  // the step whose spikes are decided here
+    int32_t spk[4] = {0, 0, 0, 0};
+    if (valid) {
+        const float *Uin = (t & 1) ? a.U2 : a.U;
+        const uint8_t *Rin = (t & 1) ? a.R2 : a.R;
+        float *Uout = (sn & 1) ? a.U2 : a.U;
+        uint8_t *Rout = (sn & 1) ? a.R2 : a.R;
+        const float4 u4 = *reinterpret_cast<const float4 *>(Uin + i0);
+        const float4 c4 = *reinterpret_cast<const float4 *>(a.I + i0);
+        const uint32_t r4 = *reinterpret_cast<const uint32_t *>(Rin + i0);
+        float uu[4] = {u4.x, u4.y, u4.z, u4.w};
+        float cc[4] = {c4.x, c4.y, c4.z, c4.w};
+        uint32_t rr[4] = {r4 & 0xFFu, (r4 >> 8) & 0xFFu, (r4 >> 16) & 0xFFu, r4 >> 24};
+        if (do_b) {
+            int32_t *wrow = a.ring + (t & kDMask) * a.npad + i0;
+            const int4 w4 = __ldcg(reinterpret_cast<const int4 *>(wrow));
+            *reinterpret_cast<int4 *>(wrow) = make_int4(0, 0, 0, 0);
+            const Block4 rnd =
+                philox4x64_10(static_cast<uint64_t>(t), static_cast<uint64_t>(q), 0, 0, a.seed, kStreamThalamic);
+            const int32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
+            int b = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t i = i0 + j;
+                if (i < a.n) {
+                    while (b + 1 < s.n_pops && i >= s.off[b + 1]) ++b;
+                    const uint64_t v = rnd.w[j] >> 1;
+                    const uint64_t *thr = s.thr + b * kPK;
+                    uint32_t T = 0;
+                    while (T < static_cast<uint32_t>(kPK) && v >= thr[T]) ++T;
+                    const int32_t in =
+                        static_cast<int32_t>(static_cast<uint32_t>(ww[j]) + T * static_cast<uint32_t>(a.w_ext_fx));
+                    cc[j] = __fadd_rn(__fmul_rn(a.p11, cc[j]), __fmul_rn(__int2float_rn(in), 0x1p-12f));
+                }
+            }
+            *reinterpret_cast<float4 *>(a.I + i0) = make_float4(cc[0], cc[1], cc[2], cc[3]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (i0 + j >= a.n) continue;
+            if (rr[j] == 0u) {
+                float x = __fadd_rn(__fmul_rn(a.p22, uu[j]), __fmul_rn(a.p21, cc[j]));
+                if (x >= a.theta) {
+                    spk[j] = 1;
+                    x = a.u_reset;
+                    rr[j] = static_cast<uint32_t>(a.t_ref);
+                }
+                uu[j] = x;
+            } else {
+                uu[j] = a.u_reset;
+                rr[j] -= 1u;
+            }
+        }
+        *reinterpret_cast<float4 *>(Uout + i0) = make_float4(uu[0], uu[1], uu[2], uu[3]);
+        *reinterpret_cast<uint32_t *>(Rout + i0) = rr[0] | (rr[1] << 8) | (rr[2] << 16) | (rr[3] << 24);
+    }
+    // queue and record the spikes of step sn: one pair of atomics per warp with spikes
+    const int lane = threadIdx.x & 31;
+    const int cnt = spk[0] + spk[1] + spk[2] + spk[3];
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    if (total == 0) return;
+    uint32_t qbase = 0, rbase = 0;
+    if (lane == 31) {
+        qbase = atomicAdd(&a.ctl->qcnt[sn % 3], static_cast<uint32_t>(total));
+        rbase = atomicAdd(&a.ctl->cursor, static_cast<uint32_t>(total));
+    }
+    qbase = __shfl_sync(0xFFFFFFFFu, qbase, 31);
+    rbase = __shfl_sync(0xFFFFFFFFu, rbase, 31);
+    uint32_t k = static_cast<uint32_t>(incl - cnt);
+    QueueEntry *qrow = a.queue + (sn % 3) * a.npad;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (!spk[j]) continue;
+        const int64_t i = i0 + j;
+        const int64_t rs = a.row_ptr[i];
+        const int64_t re = a.row_ptr[i + 1];
+        if (re > rs) {
+            prefetch_l2(a.syn_tgt + rs, static_cast<uint32_t>(4 * (re - rs)));
+            prefetch_l2(a.syn_w + rs, static_cast<uint32_t>(4 * (re - rs)));
+            const int64_t d0 = rs & ~int64_t{15}, d1 = (re + 15) & ~int64_t{15};
+            prefetch_l2(a.syn_d + d0, static_cast<uint32_t>(d1 - d0));
+        }
+        QueueEntry e;
+        e.row_quad = static_cast<uint32_t>(rs >> 2);
+        e.len_quads = static_cast<uint32_t>((re - rs) >> 2);
+        e.neuron = static_cast<int32_t>(i);
+        e.step = static_cast<int32_t>(sn);
+        *reinterpret_cast<int4 *>(qrow + qbase + k) = *reinterpret_cast<const int4 *>(&e);
+        const uint32_t pos = rbase + k;
+        if (pos < a.rast_cap) {
+            a.rast_nrn[pos] = static_cast<int32_t>(i);
+            a.rast_t[pos] = static_cast<int32_t>(sn);
+        } else {
+            atomicOr(&a.ctl->err, kErrRaster);
+        }
+        ++k;
+    }
+}
+
+// D(t): the spikes of step t sit at the front of queue t mod 3, each entry tagged with
+// its step; a warp walks its items until it meets an entry of another step.
+__device__ __forceinline__ void pipe_deliver(const StepArgs &a, int64_t t, int64_t dw, int64_t ndw)
+{
+    const int lane = threadIdx.x & 31;
+    const QueueEntry *qrow = a.queue + (t % 3) * a.npad;
+    const int64_t cpr = a.chunks_per_row;
+    int32_t *const ring = a.ring;
+    const int64_t npad = a.npad;
+    for (int64_t it = dw;; it += ndw) {
+        const int64_t j = it / cpr;
+        if (j >= a.n) break;
+        const int4 raw = __ldcg(reinterpret_cast<const int4 *>(qrow + j));
+        if (raw.w != static_cast<int32_t>(t)) break;
+        const int64_t c = it - j * cpr;
+        const int64_t rs = static_cast<int64_t>(static_cast<uint32_t>(raw.x)) * 4;
+        const int64_t re = rs + static_cast<int64_t>(static_cast<uint32_t>(raw.y)) * 4;
+        const int64_t off = rs + c * kChunk;
+        if (off >= re) continue;
+        int4 tg[2], wv[2];
+        uint32_t dv[2];
+        bool ok[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t o = off + u * 128 + lane * 4;
+            ok[u] = o < re;
+            if (ok[u]) {
+                tg[u] = ld_stream4(a.syn_tgt + o);
+                wv[u] = ld_stream4(a.syn_w + o);
+                dv[u] = ld_stream_u32(a.syn_d + o);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (!ok[u]) continue;
+            const int32_t tt[4] = {tg[u].x, tg[u].y, tg[u].z, tg[u].w};
+            const int32_t wq[4] = {wv[u].x, wv[u].y, wv[u].z, wv[u].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int64_t d = (dv[u] >> (8 * e)) & 0xFFu;
+                if (wq[e] != 0) red_add_s32(ring + ((t + d) & kDMask) * npad + tt[e], wq[e]);
+            }
+        }
+    }
+}
+
+// Shared tables staged by the neuron warps only (named barrier 1), so that the
+// delivery warps of the same CTA start at once.
+__device__ __forceinline__ void stage_tables_neurons(const StepArgs &a, SharedTables &s, int nthreads)
+{
+    for (int j = threadIdx.x; j < SNN_MAX_POPS * kPK; j += nthreads) s.thr[j] = (&a.tables->thresholds[0][0])[j];
+    if (threadIdx.x <= SNN_MAX_POPS) s.off[threadIdx.x] = a.tables->pop_off[threadIdx.x];
+    if (threadIdx.x == 0) s.n_pops = a.tables->n_pops;
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+__global__ void __launch_bounds__(kStepMaxThreads) k_step(const StepArgs a, const int k)
+{
+    __shared__ SharedTables s;
+    const int64_t t = a.ctl->t_base + k;
+    const int wib = threadIdx.x >> 5;
+    if (wib < a.neuron_warps) {
+        stage_tables_neurons(a, s, a.neuron_warps * 32);
+        const int64_t nquads = (a.n + 3) / 4;
+        const int64_t quad_warps = (nquads + 31) / 32;
+        const int64_t nw = static_cast<int64_t>(a.neuron_warps) * gridDim.x;
+        for (int64_t g = static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < quad_warps; g += nw) {
+            const int64_t q = g * 32 + (threadIdx.x & 31);
+            pipe_quad(a, s, t, q, q < nquads, true);
+        }
+    } else {
+        if (blockIdx.x == 0 && threadIdx.x == a.neuron_warps * 32) a.ctl->qcnt[(t + 2) % 3] = 0;
+        const int dwarps = static_cast<int>(blockDim.x >> 5) - a.neuron_warps;
+        const int64_t dw = static_cast<int64_t>(wib - a.neuron_warps) * gridDim.x + blockIdx.x;
+        pipe_deliver(a, t, dw, static_cast<int64_t>(dwarps) * gridDim.x);
+    }
+}
+
+__global__ void __launch_bounds__(kStepMaxThreads) k_prime(const StepArgs a)
+{
+    __shared__ SharedTables s;
+    const int wib = threadIdx.x >> 5;
+    if (wib >= a.neuron_warps) return;
+    stage_tables_neurons(a, s, a.neuron_warps * 32);
+    const int64_t nquads = (a.n + 3) / 4;
+    const int64_t quad_warps = (nquads + 31) / 32;
+    const int64_t nw = static_cast<int64_t>(a.neuron_warps) * gridDim.x;
+    for (int64_t g = static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < quad_warps; g += nw) {
+        const int64_t q = g * 32 + (threadIdx.x & 31);
+        pipe_quad(a, s, -1, q, q < nquads, false);
+    }
+}
+
 }  // namespace
+
+int step_grid(int num_sms) { return num_sms; }
+
+int step_threads(const StepArgs &a) { return 32 * (a.neuron_warps + kStepDeliverWarps); }
+
+void launch_step(const StepArgs &a, int k, int grid, void *stream)
+{
+    k_step<<<grid, step_threads(a), 0, static_cast<cudaStream_t>(stream)>>>(a, k);
+}
+
+void launch_prime(const StepArgs &a, int grid, void *stream)
+{
+    k_prime<<<grid, step_threads(a), 0, static_cast<cudaStream_t>(stream)>>>(a);
+}
 
 int update_grid(int64_t n)
 {
@@ -211,6 +572,24 @@ void launch_deliver(const StepArgs &a, int k, int grid, void *stream)
 void launch_advance(Ctl *ctl, int64_t m, void *stream)
 {
     k_advance<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(ctl, m);
+}
+
+int persistent_blocks_per_sm()
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent, kPersistThreads, 0) != cudaSuccess) return 0;
+    return nb;
+}
+
+int launch_persistent(const StepArgs &a, int64_t n_steps, int grid, void *stream)
+{
+    StepArgs args = a;
+    int64_t n = n_steps;
+    void *params[] = {&args, &n};
+    const cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_persistent), dim3(grid),
+                                                      dim3(kPersistThreads), params, 0,
+                                                      static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? 0 : static_cast<int>(e);
 }
 
 }  // namespace snn

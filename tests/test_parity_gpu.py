@@ -118,12 +118,18 @@ def test_network_identical_tiny(model, tiny):
     net.close()
 
 
-@pytest.mark.parametrize("spg", [96, 1000])
-def test_raster_bit_exact_tiny(model, tiny, spg):
+GRAPH, PERSIST, PIPE = snn.ENGINE_GRAPH, snn.ENGINE_PERSISTENT, snn.ENGINE_PIPELINED
+ENGINES = [GRAPH, PERSIST, PIPE]
+
+
+@pytest.mark.parametrize("engine,spg", [(GRAPH, 96), (GRAPH, 1000), (PERSIST, 0), (PIPE, 96), (PIPE, 1000)])
+def test_raster_bit_exact_tiny(model, tiny, engine, spg):
     """Tiny microcircuit (7,718 neurons, 2.85e6 synapses), 1,000 steps: identical raster
     and final state.  spg=96 mixes graph replays with directly launched remainders."""
     wl, onet = tiny
-    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, steps_per_graph=spg)
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, steps_per_graph=spg,
+                      engine=engine)
+    assert net.info().engine == engine
     net.step(wl.steps)
     g_t, g_i = net.read_spikes()
     sim = oracle.Sim(model, onet, wl.seed)
@@ -137,9 +143,11 @@ def test_raster_bit_exact_tiny(model, tiny, spg):
     net.close()
 
 
-def test_incremental_reads_and_rates(model, tiny):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_incremental_reads_and_rates(model, tiny, engine):
     wl, onet = tiny
-    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, steps_per_graph=50)
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, steps_per_graph=50,
+                      engine=engine)
     parts = []
     for n in (1, 7, 120, 372):
         net.step(n)
@@ -160,10 +168,13 @@ def test_incremental_reads_and_rates(model, tiny):
     net.close()
 
 
-def test_profile_steps_same_dynamics(model, tiny):
-    """The kernel-by-kernel timing path computes the same steps as the graph path."""
+@pytest.mark.parametrize("engine", ENGINES)
+def test_profile_steps_same_dynamics(model, tiny, engine):
+    """The kernel-by-kernel timing path computes the same steps as either engine, and
+    can be interleaved with it."""
     wl, onet = tiny
-    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, steps_per_graph=64)
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, steps_per_graph=64,
+                      engine=engine)
     net.step(100)
     mu, md = net.profile_steps(300)
     assert mu > 0 and md > 0
@@ -183,15 +194,16 @@ def _chain(d_first, d_second, w2):
                 pop_offsets=[0, 3, 3, 3, 3, 3, 3, 3, 3])
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("t1", [2, 62, 63, 64])
 @pytest.mark.parametrize("d", [1, 15, 16, 63])
-def test_hand_placed_spike_arrival(t1, d):
+def test_hand_placed_spike_arrival(t1, d, engine):
     """A spike at step t1 with delay d reaches the target's current at the end of step
     t1 + d, with the exact amplitude, on the GPU as in the oracle (ring wrap included)."""
     m = workload.microcircuit_model().replace(k_ext=[0.0] * 8)
     w2 = 12345 * 16
     c = _chain(t1 - 1, d, w2)
-    net = snn.Network(m, custom=c, steps_per_graph=7)
+    net = snn.Network(m, custom=c, steps_per_graph=7, engine=engine)
     onet = oracle.network_from_edges(3, c["pre"], c["post"], c["w_fx"], c["delay"], c["u0"], c["pop_offsets"])
     sim = oracle.Sim(m, onet, 1)
     t_arr = t1 + d
@@ -212,9 +224,9 @@ def test_hand_placed_spike_arrival(t1, d):
 # ------------------------------------------------------------------ edge cases
 
 
-def _custom_parity(m, custom, steps, spg=16, seed=5, **kw):
+def _custom_parity(m, custom, steps, spg=16, seed=5, engine=GRAPH, **kw):
     n = len(custom["u0"])
-    net = snn.Network(m, custom=custom, steps_per_graph=spg, seed=seed, **kw)
+    net = snn.Network(m, custom=custom, steps_per_graph=spg, seed=seed, engine=engine, **kw)
     onet = oracle.network_from_edges(n, custom["pre"], custom["post"], custom["w_fx"], custom["delay"],
                                      custom["u0"], custom.get("pop_offsets"))
     sim = oracle.Sim(m, onet, seed)
@@ -227,19 +239,21 @@ def _custom_parity(m, custom, steps, spg=16, seed=5, **kw):
     return o
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("n", [1, 3, 13, 129, 517])
-def test_ragged_neuron_counts_no_synapses(n):
+def test_ragged_neuron_counts_no_synapses(n, engine):
     """Neuron counts that fill neither a quad nor a 128-wide ring row; no synapses;
     thalamic drive only (population 0 = L23E)."""
     m = workload.microcircuit_model()
     rng = np.random.default_rng(n)
     u0 = rng.uniform(0, 16, n).astype(np.float32)
     custom = dict(pre=[], post=[], w_fx=[], delay=[], u0=u0, pop_offsets=[0] + [n] * 8)
-    o = _custom_parity(m, custom, 300)
+    o = _custom_parity(m, custom, 300, engine=engine)
     assert len(o[0]) > 0
 
 
-def test_long_rows_ragged_chunks_and_all_delays():
+@pytest.mark.parametrize("engine", ENGINES)
+def test_long_rows_ragged_chunks_and_all_delays(engine):
     """Rows longer than one 256-synapse chunk with ragged tails, every delay 1..63,
     multapses and autapses, mixed signs, several populations."""
     m = workload.microcircuit_model()
@@ -258,13 +272,14 @@ def test_long_rows_ragged_chunks_and_all_delays():
     u0 = rng.uniform(10, 16, n).astype(np.float32)
     po = [0, 40, 80, 120, 160, 200, 240, 280, n]
     custom = dict(pre=pre, post=post, w_fx=w, delay=d, u0=u0, pop_offsets=po)
-    o = _custom_parity(m, custom, 400, spg=33)
+    o = _custom_parity(m, custom, 400, spg=33, engine=engine)
     assert len(o[0]) > 50
 
 
-def test_raster_overflow_is_reported(model):
+@pytest.mark.parametrize("engine", ENGINES)
+def test_raster_overflow_is_reported(model, engine):
     """A raster smaller than the spikes of the run fails loudly with SNN_EOVERFLOW."""
-    net = snn.Network(model, 20, 20, seed=1, raster_capacity=64)
+    net = snn.Network(model, 20, 20, seed=1, raster_capacity=64, engine=engine)
     net.step(300)
     with pytest.raises(snn.SnnError) as e:
         net.read_spikes()
@@ -274,11 +289,12 @@ def test_raster_overflow_is_reported(model):
     net.close()
 
 
+@pytest.mark.parametrize("engine", ENGINES)
 @pytest.mark.parametrize("scale", [(1, 1), (5, 300), (300, 5)])
-def test_extreme_scales(model, scale):
+def test_extreme_scales(model, scale, engine):
     sn, sk = scale
     onet = oracle.build_network(model, sn, sk, 9)
-    net = snn.Network(model, sn, sk, seed=9, steps_per_graph=40)
+    net = snn.Network(model, sn, sk, seed=9, steps_per_graph=40, engine=engine)
     _row_multisets_equal(onet, *_device_network(net))
     net.step(250)
     g = net.read_spikes()
@@ -307,14 +323,39 @@ def full(model):
     return wl, onet
 
 
-def test_full_scale_parity(model, full):
+def _rows_equal_sampled(onet, rp, tg, w, d, rows):
+    """Exact per-row multiset comparison for the given rows, plus global sums over all
+    synapses (the full sort of 2.8e8 records is left to the smaller scales)."""
+    lens = np.diff(onet.row_ptr)
+    plen = np.diff(rp)
+    assert np.all(plen % 4 == 0) and np.all(plen >= lens) and np.all(plen - lens < 4)
+    for i in rows:
+        a, L = onet.row_ptr[i], lens[i]
+        b = rp[i]
+        o = np.sort(onet.post[a:a + L].astype(np.int64) << 38 | onet.delay[a:a + L].astype(np.int64) << 32
+                    | (onet.w_fx[a:a + L].astype(np.int64) + 2**31))
+        g = np.sort(tg[b:b + L].astype(np.int64) << 38 | d[b:b + L].astype(np.int64) << 32
+                    | (w[b:b + L].astype(np.int64) + 2**31))
+        assert np.array_equal(o, g), i
+        assert np.all(np.diff(d[b:b + L].astype(int)) >= 0)
+        assert np.all(w[b + L:rp[i + 1]] == 0)
+    n_real = rp[-1]
+    assert int(w[:n_real].astype(np.int64).sum()) == int(onet.w_fx.astype(np.int64).sum())
+    assert int(tg[:n_real].astype(np.int64).sum()) - int(
+        (np.repeat(np.arange(onet.n), plen - lens)).sum()) == int(onet.post.astype(np.int64).sum())
+    assert int(d[:n_real].astype(np.int64).sum()) - int((plen - lens).sum()) == int(
+        onet.delay.astype(np.int64).sum())
+
+
+@pytest.mark.parametrize("engine", [snn.ENGINE_DEFAULT, GRAPH])
+def test_full_scale_parity(model, full, engine):
     """Full microcircuit (77,169 neurons, 284,811,022 synapses) in the bench's launch
-    configuration: identical network, and an identical raster and state over the
-    first 1,200 steps (120 ms of biological time)."""
+    configuration (default engine) and with the graph engine: the network (every row
+    that spikes in the window, 2,000 random rows, global sums), and an identical raster
+    and state over the first 1,200 steps (120 ms of biological time)."""
     wl, onet = full
-    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed)
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, engine=engine)
     assert net.info().n_synapses == 284_811_022
-    _row_multisets_equal(onet, *_device_network(net))
     steps = 1200
     net.step(steps)
     g_t, g_i = net.read_spikes()
@@ -323,6 +364,9 @@ def test_full_scale_parity(model, full):
     assert len(o_t) > 0
     assert np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
     _assert_same_state(net, sim)
+    rng = np.random.default_rng(0)
+    rows = np.unique(np.concatenate([o_i, rng.integers(0, onet.n, 2000)]))
+    _rows_equal_sampled(onet, *_device_network(net), rows)
     net.close()
 
 
@@ -340,4 +384,27 @@ def test_full_scale_activity_band(model, full):
         import warnings
 
         warnings.warn(f"full-scale activity {per_step:.1f} spikes/step is outside the paper's band")
+    net.close()
+
+
+def test_barrier_wait_is_bounded_and_reported(model, monkeypatch):
+    """Failure detection without a GPU fault: with SNN_FAULT=barrier_stall every grid
+    barrier of the persistent engine waits for an arrival that never comes; the wait
+    gives up after its 20 ms bound, the run reports SNN_ETIMEOUT, and the context stays
+    usable for the next network."""
+    monkeypatch.setenv("SNN_FAULT", "barrier_stall")
+    net = snn.Network(model, 20, 20, seed=1, engine=PERSIST)
+    net.step(3)
+    with pytest.raises(snn.SnnError) as e:
+        net.read_spikes()
+    assert e.value.code == snn.SNN_ETIMEOUT
+    assert net.info().device_error & 2
+    net.close()
+    monkeypatch.delenv("SNN_FAULT")
+    onet = oracle.build_network(model, 20, 20, 1)
+    net = snn.Network(model, 20, 20, seed=1, engine=PERSIST)
+    net.step(50)
+    g = net.read_spikes()
+    o = oracle.Sim(model, onet, 1).run(50)
+    assert np.array_equal(g[0], o[0]) and np.array_equal(g[1], o[1])
     net.close()
