@@ -1,8 +1,9 @@
 """Benchmark of the full-scale Potjans-Diesmann microcircuit step loop on GB300.
 
-One bench step = 1,000 simulation steps of 0.1 ms (100 ms of biological time) of the
-full microcircuit (77,169 neurons, 284,811,022 synapses, seed 1 + rank), so the
-default --steps 100 covers the paper's 10 s runs (§4).  Prints one JSON line.
+One bench step = 1,024 simulation steps of 0.1 ms (102.4 ms of biological time, one
+CUDA-graph replay) of the full microcircuit (77,169 neurons, 284,811,022 synapses,
+seed 1 + rank), so the default --steps 100 covers the paper's 10 s runs (§4).  Prints
+one JSON line.
 
   value     recurrent synaptic events/s (sum of the spikers' out-degrees / seconds),
             device-timed with CUDA events around snn_step_n graph replays
@@ -35,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 import workload  # noqa: E402
 
-TICKS_PER_STEP = 1000
+TICKS_PER_STEP = 1024
 UPDATE_BYTES_PER_NEURON = 26   # U r/w 8 + I r/w 8 + R r/w 2 + ring slot read + clear 8
 EVENT_BYTES = 13               # tgt 4 + w 4 + delay 1 read + 4-byte ring reduction
 SPIKE_BYTES = 20               # row_ptr pair 16 + queue entry 4
@@ -354,7 +355,7 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": "synaptic events/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": d2h / args.steps,
                 "note": "network uploaded once by snn_build_network (setup, untimed as in the paper's RTF); "
-                        "every bench step enqueues 1,000 steps and reads the raster back to host memory"},
+                        "every bench step enqueues 1,024 steps and reads the raster back to host memory"},
         "gpu_launches": args.steps * {snn.ENGINE_PERSISTENT: 1, snn.ENGINE_PIPELINED: tps + 1,
                                       snn.ENGINE_GRAPH: 2 * tps + 1}[info.engine],
         "roofline": roofline, "kernels": kernels,

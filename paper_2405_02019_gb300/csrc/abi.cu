@@ -75,11 +75,13 @@ struct snn_net {
 
 namespace {
 
-int launch_steps_direct(snn_net *net, int64_t m, cudaStream_t st)
+// m steps launched one by one, starting at step t0 (the device counter t_base equals t0).
+int launch_steps_direct(snn_net *net, int64_t m, cudaStream_t st, int64_t t0)
 {
     for (int64_t k = 0; k < m; ++k) {
         if (net->engine == SNN_ENGINE_PIPELINED) {
-            snn::launch_step(net->args, static_cast<int>(k), net->step_grid, st);
+            const int ph = static_cast<int>((t0 + k) % snn::kPhasePeriod);
+            snn::launch_step(net->args, static_cast<int>(k), ph, net->step_grid, st);
         } else {
             snn::launch_update(net->args, static_cast<int>(k), net->update_grid, st);
             snn::launch_deliver(net->args, static_cast<int>(k), net->deliver_grid, st);
@@ -109,7 +111,8 @@ int capture_graph(snn_net *net)
     SNN_CUDA_TRY(cudaStreamBeginCapture(net->capture_stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < net->steps_per_graph; ++k) {
         if (net->engine == SNN_ENGINE_PIPELINED) {
-            snn::launch_step(net->args, k, net->step_grid, net->capture_stream);
+            // replays start on a multiple of the phase period (see snn_step_n)
+            snn::launch_step(net->args, k, k % snn::kPhasePeriod, net->step_grid, net->capture_stream);
         } else {
             snn::launch_update(net->args, k, net->update_grid, net->capture_stream);
             snn::launch_deliver(net->args, k, net->deliver_grid, net->capture_stream);
@@ -323,6 +326,8 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         a.u_reset = net->c.u_reset;
         a.t_ref = net->c.t_ref;
         a.w_ext_fx = net->c.w_ext_fx;
+        for (int b = 0; b <= SNN_MAX_POPS; ++b) a.pop_off[b] = tabs.pop_off[b];
+        a.n_pops = spec->model.n_pops;
         a.barrier_timeout_ns = snn::kBarrierTimeoutNs;
         a.barrier_extra = 0;
         // Fault injection for tests of the bounded barrier wait: with SNN_FAULT=barrier_stall
@@ -353,13 +358,24 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
             net->step_grid = snn::step_grid(net->num_sms);
             const int64_t quad_warps = ((net->n + 3) / 4 + 31) / 32;
             a.neuron_warps = static_cast<int32_t>(
-                std::min<int64_t>(24, std::max<int64_t>(1, (quad_warps + net->step_grid - 1) / net->step_grid)));
+                std::min<int64_t>(8, std::max<int64_t>(1, (quad_warps + net->step_grid - 1) / net->step_grid)));
             a.U2 = reinterpret_cast<float *>(A + L.U2);
             a.R2 = A + L.R2;
             a.queue = reinterpret_cast<snn::QueueEntry *>(A + L.queue);
+            a.quad_warps = static_cast<int32_t>(quad_warps);
+            a.qcount = reinterpret_cast<uint32_t *>(A + L.qcount);
+            if (snn::prepare_step_kernel(a) != 0) {
+                snn_destroy(net);
+                return fail(SNN_ENOTSUP, "network too large for the pipelined engine's shared memory");
+            }
+            cuda_ok(cudaMemsetAsync(A + L.qcount, 0, 4 * 4 * (net->npad / 128 + 1), st), "qcount");
             cuda_ok(cudaMemcpyAsync(A + L.U2, u0.data(), 4 * net->npad, cudaMemcpyHostToDevice, st), "U2");
             cuda_ok(cudaMemsetAsync(A + L.R2, 0, net->npad, st), "R2");
-            cuda_ok(cudaMemsetAsync(A + L.queue, 0xFF, 3 * sizeof(snn::QueueEntry) * net->npad, st), "queue");
+            cuda_ok(cudaMemsetAsync(A + L.queue, 0xFF, 4 * sizeof(snn::QueueEntry) * net->npad, st), "queue");
+            // a graph holds a whole number of phase periods
+            net->steps_per_graph = std::max(snn::kPhasePeriod,
+                                            (spec->steps_per_graph > 0 ? spec->steps_per_graph : 1024) /
+                                                snn::kPhasePeriod * snn::kPhasePeriod);
             snn::launch_prime(a, net->step_grid, st);
             cuda_ok(cudaGetLastError(), "prime launch");
             cuda_ok(cudaStreamSynchronize(st), "prime");
@@ -394,11 +410,21 @@ int snn_step_n(snn_net *net, int64_t n_steps, void *cuda_stream)
         const int rc = launch_steps_persistent(net, n_steps, st);
         if (rc) return rc;
     } else {
-        const int64_t full = n_steps / net->steps_per_graph;
-        const int64_t rem = n_steps % net->steps_per_graph;
-        for (int64_t g = 0; g < full; ++g) SNN_CUDA_TRY(cudaGraphLaunch(net->graph_exec, st));
-        if (rem > 0) {
-            const int rc = launch_steps_direct(net, rem, st);
+        int64_t t = net->t, n = n_steps;
+        if (net->engine == SNN_ENGINE_PIPELINED) {
+            // single steps up to the next multiple of the phase period, where graphs start
+            const int64_t head = std::min<int64_t>(n, (snn::kPhasePeriod - t % snn::kPhasePeriod) % snn::kPhasePeriod);
+            if (head > 0) {
+                const int rc = launch_steps_direct(net, head, st, t);
+                if (rc) return rc;
+                t += head;
+                n -= head;
+            }
+        }
+        for (; n >= net->steps_per_graph; n -= net->steps_per_graph, t += net->steps_per_graph)
+            SNN_CUDA_TRY(cudaGraphLaunch(net->graph_exec, st));
+        if (n > 0) {
+            const int rc = launch_steps_direct(net, n, st, t);
             if (rc) return rc;
         }
     }
@@ -424,7 +450,8 @@ int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *
         for (int64_t k = 0; k < m; ++k) {
             cudaEventRecord(ev[3 * k], st);
             if (net->engine == SNN_ENGINE_PIPELINED) {
-                snn::launch_step(net->args, static_cast<int>(k), net->step_grid, st);
+                const int ph = static_cast<int>((net->t + done + k) % snn::kPhasePeriod);
+                snn::launch_step(net->args, static_cast<int>(k), ph, net->step_grid, st);
                 cudaEventRecord(ev[3 * k + 1], st);
             } else {
                 snn::launch_update(net->args, static_cast<int>(k), net->update_grid, st);

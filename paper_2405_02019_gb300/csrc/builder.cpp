@@ -225,7 +225,7 @@ Layout make_layout(const snn_spec &spec)
     L.I = o; o = up(o + 4 * L.npad);
     L.R = o; o = up(o + L.npad);
     L.ring = o; o = up(o + uint64_t{4} * kDMax * L.npad);
-    L.row_ptr = o; o = up(o + 8 * (n + 1));
+    L.row_ptr = o; o = up(o + 8 * (n + 5));  // 4 spare entries: quads read row_ptr[i0 .. i0+4]
     L.syn_tgt = o; o = up(o + 4 * L.syn_padded_max);
     L.syn_w = o; o = up(o + 4 * L.syn_padded_max);
     L.syn_d = o; o = up(o + L.syn_padded_max + 16);
@@ -233,7 +233,8 @@ Layout make_layout(const snn_spec &spec)
     L.rast_t = o; o = up(o + 4 * L.rast_cap);
     L.U2 = o; o = up(o + 4 * L.npad);
     L.R2 = o; o = up(o + L.npad);
-    L.queue = o; o = up(o + uint64_t{3} * sizeof(QueueEntry) * L.npad);
+    L.queue = o; o = up(o + uint64_t{4} * sizeof(QueueEntry) * L.npad);
+    L.qcount = o; o = up(o + uint64_t{4} * 4 * (L.npad / 128 + 1));
     L.total = o;
     return L;
 }

@@ -19,7 +19,8 @@ constexpr int kUpdateThreads = 128;          // 4 neurons per thread
 constexpr int kDeliverThreads = 256;
 constexpr int kPersistThreads = 1024;        // one CTA per SM in the persistent engine
 constexpr int kStepDeliverWarps = 8;         // delivery warps per CTA of the pipelined step kernel
-constexpr int kStepMaxThreads = 1024;
+constexpr int kStepMaxThreads = 512;            // neuron warps (<= 8) + delivery warps per CTA
+constexpr int kPhasePeriod = 64;             // pipelined engine: buffers repeat with t mod 64
 constexpr uint32_t kErrRaster = 1u;
 constexpr uint32_t kErrTimeout = 2u;
 constexpr uint64_t kBarrierTimeoutNs = 2000000000ull;  // default bound of every grid-barrier wait
@@ -32,8 +33,8 @@ struct alignas(64) Ctl {
     uint32_t step_begin[2];  // raster index where step t's spikes start, by t mod 2
     uint32_t err;            // sticky error bits
     uint32_t bar;            // grid-barrier arrivals of the running persistent launch
-    uint32_t qcnt[3];        // pipelined engine: spikes queued for step s in queue s mod 3
-    uint32_t pad[6];
+    uint32_t qcnt[4];        // pipelined engine: spikes queued for step s in queue s mod 4
+    uint32_t pad[5];
 };
 
 // Pipelined engine: one queue entry per spike of a step, written by the thread that
@@ -80,7 +81,11 @@ struct StepArgs {
     int32_t neuron_warps;         // pipelined engine: neuron warps per CTA
     float *U2;                    // pipelined engine: second U / R buffers (state after A(s) in buffer s mod 2)
     uint8_t *R2;
-    QueueEntry *queue;            // pipelined engine: 3 queues of npad entries
+    QueueEntry *queue;            // pipelined engine: 4 queues of npad entries
+    int64_t pop_off[SNN_MAX_POPS + 1];  // population offsets (read from the launch arguments)
+    int32_t n_pops;
+    int32_t quad_warps;           // pipelined engine: groups of 128 neurons (one queue region each)
+    uint32_t *qcount;             // pipelined engine: spikes per group, [4][quad_warps]
 };
 
 // Host constants of one model (§2.2).
@@ -110,7 +115,7 @@ struct HostNetwork {
 
 // Arena layout for a spec.
 struct Layout {
-    uint64_t ctl, tables, U, I, R, ring, row_ptr, syn_tgt, syn_w, syn_d, rast_nrn, rast_t, U2, R2, queue, total;
+    uint64_t ctl, tables, U, I, R, ring, row_ptr, syn_tgt, syn_w, syn_d, rast_nrn, rast_t, U2, R2, queue, qcount, total;
     int64_t npad, syn_padded_max, rast_cap;
 };
 
@@ -132,8 +137,9 @@ void launch_advance(Ctl *ctl, int64_t m, void *stream);
 int update_grid(int64_t n);
 int persistent_blocks_per_sm();
 int launch_persistent(const StepArgs &a, int64_t n_steps, int grid, void *stream);
-void launch_step(const StepArgs &a, int k, int grid, void *stream);   // pipelined: B(t), A(t+1) and D(t)
+void launch_step(const StepArgs &a, int k, int ph, int grid, void *stream);  // pipelined: B(t), A(t+1), D(t); ph = t mod 64
 void launch_prime(const StepArgs &a, int grid, void *stream);         // pipelined: A(0)
+int prepare_step_kernel(const StepArgs &a);                           // dynamic shared memory opt-in
 int step_grid(int num_sms);
 int step_threads(const StepArgs &a);
 

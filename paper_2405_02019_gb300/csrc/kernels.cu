@@ -323,9 +323,17 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_persistent(const StepArg
 //   delivery warps: D(t) for the spikes of step t decided by K_{t-1}.
 // Each neuron still sees A(0), B(0), A(1), B(1), ... in order, so the arithmetic is
 // the same as the two-phase engines.  U and R after A(s) live in buffer s mod 2 (the
-// state after s steps is in buffer (s-1) mod 2); the spikes of step s are queued in
-// queue s mod 3 by the thread that decided them, with their row bounds, and their
-// rows are prefetched into L2 for the next kernel's delivery warps.
+// state after s steps is in buffer (s-1) mod 2).
+//
+// Spike queue of step s (buffers s mod 4): every group of 128 neurons (one warp's 32
+// quads) owns a 128-entry region; the warp writes its spikers' entries (with their
+// row bounds, loaded with the neuron state) there and its spike count into qcount,
+// with plain stores -- no atomic and no dependent load stands after the spike
+// decision.  The rows are prefetched into L2 for the next kernel.  The delivery warps
+// of every CTA prefix-sum the counts in shared memory to number the spikes, and the
+// warp delivering chunk 0 of spike j records it at raster position base + j; the
+// raster base advances once per step (Ctl::step_begin[t mod 2]).  Every buffer choice
+// depends on t mod 64 only, which the launch passes in (`ph`).
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
@@ -333,42 +341,88 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Neuron part for quad q: B(t) (unless do_b is false: the first kernel, t = -1) then
-// A(t+1).  Warp-collective: every lane must call it (lanes without a quad pass valid=false).
-__device__ __forceinline__ void pipe_quad(const StepArgs &a, const SharedTables &s, int64_t t, int64_t q,
-                                          bool valid, bool do_b)
+// Population of neuron i from the offsets in the launch arguments.
+__device__ __forceinline__ int pop_of(const StepArgs &a, int64_t i)
 {
+    int b = 0;
+    while (b + 1 < a.n_pops && i >= a.pop_off[b + 1]) ++b;
+    return b;
+}
+
+// Poisson count T = #{k : v >= thr[k]} (thresholds nondecreasing): the first eight
+// thresholds of the quad's population come in registers, the rest from memory.
+__device__ __forceinline__ uint32_t poisson_count(uint64_t v, const uint64_t (&r)[8], const uint64_t *thr_row)
+{
+    uint32_t T = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) T += (v >= r[k]) ? 1u : 0u;
+    if (T == 8u)
+        while (T < static_cast<uint32_t>(kPK) && v >= __ldg(thr_row + T)) ++T;
+    return T;
+}
+
+// Neuron part for quad q = 32 g + lane: B(t) (unless do_b is false: the first kernel,
+// t = -1) then A(t+1).  Warp-collective: every lane of group g must call it (lanes
+// without a quad pass valid = false).
+__device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, int ph, int64_t g, bool valid,
+                                          bool do_b)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t q = g * 32 + lane;
     const int64_t i0 = q * 4;
-    const int64_t sn = t + 1;  // the step whose spikes are decided here
+    const int phn = ph + 1;  // phase of the step whose spikes are decided here
     int32_t spk[4] = {0, 0, 0, 0};
+    int64_t rp[5] = {0, 0, 0, 0, 0};
     if (valid) {
-        const float *Uin = (t & 1) ? a.U2 : a.U;
-        const uint8_t *Rin = (t & 1) ? a.R2 : a.R;
-        float *Uout = (sn & 1) ? a.U2 : a.U;
-        uint8_t *Rout = (sn & 1) ? a.R2 : a.R;
+        const float *Uin = (ph & 1) ? a.U2 : a.U;
+        const uint8_t *Rin = (ph & 1) ? a.R2 : a.R;
+        float *Uout = (phn & 1) ? a.U2 : a.U;
+        uint8_t *Rout = (phn & 1) ? a.R2 : a.R;
+        // every load of the quad is issued here, in one round trip (row bounds too,
+        // whether or not the neurons spike)
         const float4 u4 = *reinterpret_cast<const float4 *>(Uin + i0);
         const float4 c4 = *reinterpret_cast<const float4 *>(a.I + i0);
         const uint32_t r4 = *reinterpret_cast<const uint32_t *>(Rin + i0);
+        const longlong2 rpa = __ldg(reinterpret_cast<const longlong2 *>(a.row_ptr + i0));
+        const longlong2 rpb = __ldg(reinterpret_cast<const longlong2 *>(a.row_ptr + i0 + 2));
+        const int64_t rpc = __ldg(a.row_ptr + i0 + 4);
+        rp[0] = rpa.x; rp[1] = rpa.y; rp[2] = rpb.x; rp[3] = rpb.y; rp[4] = rpc;
+        int32_t *wrow = a.ring + (ph & kDMask) * a.npad + i0;
+        int4 w4 = make_int4(0, 0, 0, 0);
+        const int b0 = pop_of(a, i0);
+        const uint64_t *thr0 = &a.tables->thresholds[b0][0];
+        uint64_t tr[8];
+        if (do_b) {
+            w4 = __ldcg(reinterpret_cast<const int4 *>(wrow));
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) {
+                const ulonglong2 v2 = __ldg(reinterpret_cast<const ulonglong2 *>(thr0 + k));
+                tr[k] = v2.x;
+                tr[k + 1] = v2.y;
+            }
+        }
         float uu[4] = {u4.x, u4.y, u4.z, u4.w};
         float cc[4] = {c4.x, c4.y, c4.z, c4.w};
         uint32_t rr[4] = {r4 & 0xFFu, (r4 >> 8) & 0xFFu, (r4 >> 16) & 0xFFu, r4 >> 24};
         if (do_b) {
-            int32_t *wrow = a.ring + (t & kDMask) * a.npad + i0;
-            const int4 w4 = __ldcg(reinterpret_cast<const int4 *>(wrow));
             *reinterpret_cast<int4 *>(wrow) = make_int4(0, 0, 0, 0);
             const Block4 rnd =
                 philox4x64_10(static_cast<uint64_t>(t), static_cast<uint64_t>(q), 0, 0, a.seed, kStreamThalamic);
             const int32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
-            int b = 0;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int64_t i = i0 + j;
                 if (i < a.n) {
-                    while (b + 1 < s.n_pops && i >= s.off[b + 1]) ++b;
+                    const int b = pop_of(a, i);
                     const uint64_t v = rnd.w[j] >> 1;
-                    const uint64_t *thr = s.thr + b * kPK;
-                    uint32_t T = 0;
-                    while (T < static_cast<uint32_t>(kPK) && v >= thr[T]) ++T;
+                    uint32_t T;
+                    if (b == b0) {
+                        T = poisson_count(v, tr, thr0);
+                    } else {  // a population boundary inside the quad: read that row from memory
+                        const uint64_t *thr = &a.tables->thresholds[b][0];
+                        T = 0;
+                        while (T < static_cast<uint32_t>(kPK) && v >= __ldg(thr + T)) ++T;
+                    }
                     const int32_t in =
                         static_cast<int32_t>(static_cast<uint32_t>(ww[j]) + T * static_cast<uint32_t>(a.w_ext_fx));
                     cc[j] = __fadd_rn(__fmul_rn(a.p11, cc[j]), __fmul_rn(__int2float_rn(in), 0x1p-12f));
@@ -395,8 +449,7 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const SharedTables 
         *reinterpret_cast<float4 *>(Uout + i0) = make_float4(uu[0], uu[1], uu[2], uu[3]);
         *reinterpret_cast<uint32_t *>(Rout + i0) = rr[0] | (rr[1] << 8) | (rr[2] << 16) | (rr[3] << 24);
     }
-    // queue and record the spikes of step sn: one pair of atomics per warp with spikes
-    const int lane = threadIdx.x & 31;
+    // the group's spikes of step t+1: count and entries, plain stores in its own region
     const int cnt = spk[0] + spk[1] + spk[2] + spk[3];
     int incl = cnt;
 #pragma unroll
@@ -405,22 +458,16 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const SharedTables 
         if (lane >= o) incl += v;
     }
     const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    if (total == 0) return;
-    uint32_t qbase = 0, rbase = 0;
-    if (lane == 31) {
-        qbase = atomicAdd(&a.ctl->qcnt[sn % 3], static_cast<uint32_t>(total));
-        rbase = atomicAdd(&a.ctl->cursor, static_cast<uint32_t>(total));
-    }
-    qbase = __shfl_sync(0xFFFFFFFFu, qbase, 31);
-    rbase = __shfl_sync(0xFFFFFFFFu, rbase, 31);
-    uint32_t k = static_cast<uint32_t>(incl - cnt);
-    QueueEntry *qrow = a.queue + (sn % 3) * a.npad;
+    if (lane == 0) a.qcount[(phn & 3) * a.quad_warps + g] = static_cast<uint32_t>(total);
+    if (cnt == 0) return;
+    QueueEntry *region = a.queue + (phn & 3) * a.npad + g * 128;
+    int k = incl - cnt;
+    const int64_t sn = t + 1;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         if (!spk[j]) continue;
-        const int64_t i = i0 + j;
-        const int64_t rs = a.row_ptr[i];
-        const int64_t re = a.row_ptr[i + 1];
+        const int64_t rs = rp[j];
+        const int64_t re = rp[j + 1];
         if (re > rs) {
             prefetch_l2(a.syn_tgt + rs, static_cast<uint32_t>(4 * (re - rs)));
             prefetch_l2(a.syn_w + rs, static_cast<uint32_t>(4 * (re - rs)));
@@ -430,35 +477,83 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const SharedTables 
         QueueEntry e;
         e.row_quad = static_cast<uint32_t>(rs >> 2);
         e.len_quads = static_cast<uint32_t>((re - rs) >> 2);
-        e.neuron = static_cast<int32_t>(i);
+        e.neuron = static_cast<int32_t>(i0 + j);
         e.step = static_cast<int32_t>(sn);
-        *reinterpret_cast<int4 *>(qrow + qbase + k) = *reinterpret_cast<const int4 *>(&e);
-        const uint32_t pos = rbase + k;
-        if (pos < a.rast_cap) {
-            a.rast_nrn[pos] = static_cast<int32_t>(i);
-            a.rast_t[pos] = static_cast<int32_t>(sn);
-        } else {
-            atomicOr(&a.ctl->err, kErrRaster);
-        }
+        *reinterpret_cast<int4 *>(region + k) = *reinterpret_cast<const int4 *>(&e);
         ++k;
     }
 }
 
-// D(t): the spikes of step t sit at the front of queue t mod 3, each entry tagged with
-// its step; a warp walks its items until it meets an entry of another step.
-__device__ __forceinline__ void pipe_deliver(const StepArgs &a, int64_t t, int64_t dw, int64_t ndw)
+// D(t), run by the delivery warps of every CTA (dthreads threads, named barrier 2):
+// number the spikes of step t by a prefix sum of the per-group counts (shared
+// memory s_pref[quad_warps + 1]), then grid-stride over (spike, 256-synapse chunk)
+// items.  The warp taking chunk 0 of spike j also records it in the raster.
+__device__ __forceinline__ void pipe_deliver(const StepArgs &a, const int64_t &t, int ph, int dt, int dthreads,
+                                             int64_t dw, int64_t ndw, uint32_t *s_pref)
 {
+    __shared__ uint32_t s_wsum[32];
     const int lane = threadIdx.x & 31;
-    const QueueEntry *qrow = a.queue + (t % 3) * a.npad;
+    const int QW = a.quad_warps;
+    const uint32_t *cnts = a.qcount + (ph & 3) * QW;
+    const uint32_t rbase = __ldcg(&a.ctl->step_begin[t & 1]);
+    // block scan of the counts
+    const int per = (QW + dthreads - 1) / dthreads;
+    const int lo = dt * per, hi = min(lo + per, QW);
+    uint32_t local = 0;
+    for (int g = lo; g < hi; ++g) {
+        const uint32_t c = __ldcg(cnts + g);
+        s_pref[g] = c;
+        local += c;
+    }
+    uint32_t incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int dwarp = dt >> 5;
+    if (lane == 31) s_wsum[dwarp] = incl;
+    asm volatile("bar.sync 2, %0;" ::"r"(dthreads) : "memory");
+    uint32_t before = 0;
+    for (int w = 0; w < dwarp; ++w) before += s_wsum[w];
+    uint32_t run = before + incl - local;
+    for (int g = lo; g < hi; ++g) {
+        const uint32_t c = s_pref[g];
+        s_pref[g] = run;
+        run += c;
+    }
+    if (dt == dthreads - 1) s_pref[QW] = run;
+    asm volatile("bar.sync 2, %0;" ::"r"(dthreads) : "memory");
+    const uint32_t n = s_pref[QW];
+    if (blockIdx.x == 0 && dt == 0) {
+        a.ctl->step_begin[(t + 1) & 1] = rbase + n;
+        a.ctl->cursor = rbase + n;
+        if (static_cast<uint64_t>(rbase) + n > a.rast_cap) atomicOr(&a.ctl->err, kErrRaster);
+    }
+    const QueueEntry *qbuf = a.queue + (ph & 3) * a.npad;
     const int64_t cpr = a.chunks_per_row;
+    const int64_t items = static_cast<int64_t>(n) * cpr;
     int32_t *const ring = a.ring;
     const int64_t npad = a.npad;
-    for (int64_t it = dw;; it += ndw) {
+    for (int64_t it = dw; it < items; it += ndw) {
         const int64_t j = it / cpr;
-        if (j >= a.n) break;
-        const int4 raw = __ldcg(reinterpret_cast<const int4 *>(qrow + j));
-        if (raw.w != static_cast<int32_t>(t)) break;
         const int64_t c = it - j * cpr;
+        // group holding spike j: the last g with s_pref[g] <= j
+        int glo = 0, ghi = QW - 1;
+        while (glo < ghi) {
+            const int mid = (glo + ghi + 1) >> 1;
+            if (s_pref[mid] <= static_cast<uint32_t>(j)) glo = mid;
+            else ghi = mid - 1;
+        }
+        const int4 raw = __ldcg(reinterpret_cast<const int4 *>(qbuf + static_cast<int64_t>(glo) * 128 +
+                                                               (j - s_pref[glo])));
+        if (c == 0 && lane == 0) {
+            const uint64_t pos = static_cast<uint64_t>(rbase) + static_cast<uint64_t>(j);
+            if (pos < a.rast_cap) {
+                a.rast_nrn[pos] = raw.z;
+                a.rast_t[pos] = static_cast<int32_t>(t);
+            }
+        }
         const int64_t rs = static_cast<int64_t>(static_cast<uint32_t>(raw.x)) * 4;
         const int64_t re = rs + static_cast<int64_t>(static_cast<uint32_t>(raw.y)) * 4;
         const int64_t off = rs + c * kChunk;
@@ -484,57 +579,39 @@ __device__ __forceinline__ void pipe_deliver(const StepArgs &a, int64_t t, int64
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int64_t d = (dv[u] >> (8 * e)) & 0xFFu;
-                if (wq[e] != 0) red_add_s32(ring + ((t + d) & kDMask) * npad + tt[e], wq[e]);
+                if (wq[e] != 0) red_add_s32(ring + ((ph + d) & kDMask) * npad + tt[e], wq[e]);
             }
         }
     }
 }
 
-// Shared tables staged by the neuron warps only (named barrier 1), so that the
-// delivery warps of the same CTA start at once.
-__device__ __forceinline__ void stage_tables_neurons(const StepArgs &a, SharedTables &s, int nthreads)
+__global__ void __launch_bounds__(kStepMaxThreads, 1) k_step(const StepArgs a, const int k, const int ph)
 {
-    for (int j = threadIdx.x; j < SNN_MAX_POPS * kPK; j += nthreads) s.thr[j] = (&a.tables->thresholds[0][0])[j];
-    if (threadIdx.x <= SNN_MAX_POPS) s.off[threadIdx.x] = a.tables->pop_off[threadIdx.x];
-    if (threadIdx.x == 0) s.n_pops = a.tables->n_pops;
-    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
-}
-
-__global__ void __launch_bounds__(kStepMaxThreads) k_step(const StepArgs a, const int k)
-{
-    __shared__ SharedTables s;
-    const int64_t t = a.ctl->t_base + k;
+    extern __shared__ uint32_t s_pref[];
+    const int64_t t = a.ctl->t_base + k;  // used for Philox counters and step tags only
     const int wib = threadIdx.x >> 5;
     if (wib < a.neuron_warps) {
-        stage_tables_neurons(a, s, a.neuron_warps * 32);
         const int64_t nquads = (a.n + 3) / 4;
-        const int64_t quad_warps = (nquads + 31) / 32;
         const int64_t nw = static_cast<int64_t>(a.neuron_warps) * gridDim.x;
-        for (int64_t g = static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < quad_warps; g += nw) {
-            const int64_t q = g * 32 + (threadIdx.x & 31);
-            pipe_quad(a, s, t, q, q < nquads, true);
-        }
+        for (int64_t g = static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < a.quad_warps; g += nw)
+            pipe_quad(a, t, ph, g, g * 32 + (threadIdx.x & 31) < nquads, true);
     } else {
-        if (blockIdx.x == 0 && threadIdx.x == a.neuron_warps * 32) a.ctl->qcnt[(t + 2) % 3] = 0;
-        const int dwarps = static_cast<int>(blockDim.x >> 5) - a.neuron_warps;
+        const int dthreads = static_cast<int>(blockDim.x) - 32 * a.neuron_warps;
+        const int dt = static_cast<int>(threadIdx.x) - 32 * a.neuron_warps;
         const int64_t dw = static_cast<int64_t>(wib - a.neuron_warps) * gridDim.x + blockIdx.x;
-        pipe_deliver(a, t, dw, static_cast<int64_t>(dwarps) * gridDim.x);
+        pipe_deliver(a, t, ph, dt, dthreads, dw, static_cast<int64_t>(dthreads >> 5) * gridDim.x, s_pref);
     }
 }
 
-__global__ void __launch_bounds__(kStepMaxThreads) k_prime(const StepArgs a)
+__global__ void __launch_bounds__(kStepMaxThreads, 1) k_prime(const StepArgs a)
 {
-    __shared__ SharedTables s;
     const int wib = threadIdx.x >> 5;
     if (wib >= a.neuron_warps) return;
-    stage_tables_neurons(a, s, a.neuron_warps * 32);
     const int64_t nquads = (a.n + 3) / 4;
-    const int64_t quad_warps = (nquads + 31) / 32;
     const int64_t nw = static_cast<int64_t>(a.neuron_warps) * gridDim.x;
-    for (int64_t g = static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < quad_warps; g += nw) {
-        const int64_t q = g * 32 + (threadIdx.x & 31);
-        pipe_quad(a, s, -1, q, q < nquads, false);
-    }
+    const int64_t t = -1;
+    for (int64_t g = static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < a.quad_warps; g += nw)
+        pipe_quad(a, t, -1, g, g * 32 + (threadIdx.x & 31) < nquads, false);
 }
 
 }  // namespace
@@ -543,9 +620,19 @@ int step_grid(int num_sms) { return num_sms; }
 
 int step_threads(const StepArgs &a) { return 32 * (a.neuron_warps + kStepDeliverWarps); }
 
-void launch_step(const StepArgs &a, int k, int grid, void *stream)
+static size_t step_smem(const StepArgs &a) { return sizeof(uint32_t) * (static_cast<size_t>(a.quad_warps) + 1); }
+
+int prepare_step_kernel(const StepArgs &a)
 {
-    k_step<<<grid, step_threads(a), 0, static_cast<cudaStream_t>(stream)>>>(a, k);
+    const size_t smem = step_smem(a);
+    if (smem <= 48 * 1024) return 0;
+    return static_cast<int>(cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(smem)));
+}
+
+void launch_step(const StepArgs &a, int k, int ph, int grid, void *stream)
+{
+    k_step<<<grid, step_threads(a), step_smem(a), static_cast<cudaStream_t>(stream)>>>(a, k, ph);
 }
 
 void launch_prime(const StepArgs &a, int grid, void *stream)
