@@ -111,8 +111,16 @@ int capture_graph(snn_net *net)
     SNN_CUDA_TRY(cudaStreamBeginCapture(net->capture_stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < net->steps_per_graph; ++k) {
         if (net->engine == SNN_ENGINE_PIPELINED) {
-            // replays start on a multiple of the phase period (see snn_step_n)
-            snn::launch_step(net->args, k, k % snn::kPhasePeriod, net->step_grid, net->capture_stream);
+            // replays start on a multiple of the phase period (see snn_step_n); consecutive
+            // step kernels overlap their launch with the previous one (programmatic edges)
+            const int e = snn::launch_step(net->args, k, k % snn::kPhasePeriod, net->step_grid, net->capture_stream,
+                                           /*programmatic=*/k > 0);
+            if (e != 0) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(net->capture_stream, &g);
+                if (g) cudaGraphDestroy(g);
+                return fail(SNN_ECUDA, std::string("capture: ") + cudaGetErrorString(static_cast<cudaError_t>(e)));
+            }
         } else {
             snn::launch_update(net->args, k, net->update_grid, net->capture_stream);
             snn::launch_deliver(net->args, k, net->deliver_grid, net->capture_stream);
@@ -358,7 +366,8 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
             net->step_grid = snn::step_grid(net->num_sms);
             const int64_t quad_warps = ((net->n + 3) / 4 + 31) / 32;
             a.neuron_warps = static_cast<int32_t>(
-                std::min<int64_t>(8, std::max<int64_t>(1, (quad_warps + net->step_grid - 1) / net->step_grid)));
+                std::min<int64_t>(snn::kStepMaxNeuronWarps,
+                                  std::max<int64_t>(1, (quad_warps + net->step_grid - 1) / net->step_grid)));
             a.U2 = reinterpret_cast<float *>(A + L.U2);
             a.R2 = A + L.R2;
             a.queue = reinterpret_cast<snn::QueueEntry *>(A + L.queue);

@@ -19,7 +19,8 @@ constexpr int kUpdateThreads = 128;          // 4 neurons per thread
 constexpr int kDeliverThreads = 256;
 constexpr int kPersistThreads = 1024;        // one CTA per SM in the persistent engine
 constexpr int kStepDeliverWarps = 8;         // delivery warps per CTA of the pipelined step kernel
-constexpr int kStepMaxThreads = 512;            // neuron warps (<= 8) + delivery warps per CTA
+constexpr int kStepMaxThreads = 384;            // neuron warps (<= 4) + delivery warps per CTA
+constexpr int kStepMaxNeuronWarps = 4;
 constexpr int kPhasePeriod = 64;             // pipelined engine: buffers repeat with t mod 64
 constexpr uint32_t kErrRaster = 1u;
 constexpr uint32_t kErrTimeout = 2u;
@@ -137,7 +138,9 @@ void launch_advance(Ctl *ctl, int64_t m, void *stream);
 int update_grid(int64_t n);
 int persistent_blocks_per_sm();
 int launch_persistent(const StepArgs &a, int64_t n_steps, int grid, void *stream);
-void launch_step(const StepArgs &a, int k, int ph, int grid, void *stream);  // pipelined: B(t), A(t+1), D(t); ph = t mod 64
+// pipelined: B(t), A(t+1), D(t); ph = t mod 64.  With `programmatic`, the launch may
+// begin while the previous kernel in the stream still runs (it waits inside).
+int launch_step(const StepArgs &a, int k, int ph, int grid, void *stream, bool programmatic = false);
 void launch_prime(const StepArgs &a, int grid, void *stream);         // pipelined: A(0)
 int prepare_step_kernel(const StepArgs &a);                           // dynamic shared memory opt-in
 int step_grid(int num_sms);

@@ -361,11 +361,18 @@ __device__ __forceinline__ uint32_t poisson_count(uint64_t v, const uint64_t (&r
     return T;
 }
 
+// Waits until the previous kernel of the stream has completed and its writes are
+// visible (a no-op unless this launch was made programmatic).
+__device__ __forceinline__ void wait_previous_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Neuron part for quad q = 32 g + lane: B(t) (unless do_b is false: the first kernel,
 // t = -1) then A(t+1).  Warp-collective: every lane of group g must call it (lanes
-// without a quad pass valid = false).
+// without a quad pass valid = false).  Everything that does not depend on the
+// previous step (row bounds, Poisson thresholds, the Philox block) is done before
+// `wait_first` (if set) waits for the previous kernel.
 __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, int ph, int64_t g, bool valid,
-                                          bool do_b)
+                                          bool do_b, bool wait_first)
 {
     const int lane = threadIdx.x & 31;
     const int64_t q = g * 32 + lane;
@@ -373,41 +380,46 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, i
     const int phn = ph + 1;  // phase of the step whose spikes are decided here
     int32_t spk[4] = {0, 0, 0, 0};
     int64_t rp[5] = {0, 0, 0, 0, 0};
+    // independent of the previous step: network, tables, random numbers
+    uint64_t tr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    Block4 rnd = {{0, 0, 0, 0}};
+    int b0 = 0;
+    const uint64_t *thr0 = a.tables->thresholds[0];
     if (valid) {
-        const float *Uin = (ph & 1) ? a.U2 : a.U;
-        const uint8_t *Rin = (ph & 1) ? a.R2 : a.R;
-        float *Uout = (phn & 1) ? a.U2 : a.U;
-        uint8_t *Rout = (phn & 1) ? a.R2 : a.R;
-        // every load of the quad is issued here, in one round trip (row bounds too,
-        // whether or not the neurons spike)
-        const float4 u4 = *reinterpret_cast<const float4 *>(Uin + i0);
-        const float4 c4 = *reinterpret_cast<const float4 *>(a.I + i0);
-        const uint32_t r4 = *reinterpret_cast<const uint32_t *>(Rin + i0);
         const longlong2 rpa = __ldg(reinterpret_cast<const longlong2 *>(a.row_ptr + i0));
         const longlong2 rpb = __ldg(reinterpret_cast<const longlong2 *>(a.row_ptr + i0 + 2));
         const int64_t rpc = __ldg(a.row_ptr + i0 + 4);
         rp[0] = rpa.x; rp[1] = rpa.y; rp[2] = rpb.x; rp[3] = rpb.y; rp[4] = rpc;
-        int32_t *wrow = a.ring + (ph & kDMask) * a.npad + i0;
-        int4 w4 = make_int4(0, 0, 0, 0);
-        const int b0 = pop_of(a, i0);
-        const uint64_t *thr0 = &a.tables->thresholds[b0][0];
-        uint64_t tr[8];
+        b0 = pop_of(a, i0);
+        thr0 = &a.tables->thresholds[b0][0];
         if (do_b) {
-            w4 = __ldcg(reinterpret_cast<const int4 *>(wrow));
 #pragma unroll
             for (int k = 0; k < 8; k += 2) {
                 const ulonglong2 v2 = __ldg(reinterpret_cast<const ulonglong2 *>(thr0 + k));
                 tr[k] = v2.x;
                 tr[k + 1] = v2.y;
             }
+            rnd = philox4x64_10(static_cast<uint64_t>(t), static_cast<uint64_t>(q), 0, 0, a.seed, kStreamThalamic);
         }
+    }
+    if (wait_first) wait_previous_grid();
+    if (valid) {
+        const float *Uin = (ph & 1) ? a.U2 : a.U;
+        const uint8_t *Rin = (ph & 1) ? a.R2 : a.R;
+        float *Uout = (phn & 1) ? a.U2 : a.U;
+        uint8_t *Rout = (phn & 1) ? a.R2 : a.R;
+        // the state of the quad, in one round trip
+        const float4 u4 = *reinterpret_cast<const float4 *>(Uin + i0);
+        const float4 c4 = *reinterpret_cast<const float4 *>(a.I + i0);
+        const uint32_t r4 = *reinterpret_cast<const uint32_t *>(Rin + i0);
+        int32_t *wrow = a.ring + (ph & kDMask) * a.npad + i0;
+        int4 w4 = make_int4(0, 0, 0, 0);
+        if (do_b) w4 = __ldcg(reinterpret_cast<const int4 *>(wrow));
         float uu[4] = {u4.x, u4.y, u4.z, u4.w};
         float cc[4] = {c4.x, c4.y, c4.z, c4.w};
         uint32_t rr[4] = {r4 & 0xFFu, (r4 >> 8) & 0xFFu, (r4 >> 16) & 0xFFu, r4 >> 24};
         if (do_b) {
             *reinterpret_cast<int4 *>(wrow) = make_int4(0, 0, 0, 0);
-            const Block4 rnd =
-                philox4x64_10(static_cast<uint64_t>(t), static_cast<uint64_t>(q), 0, 0, a.seed, kStreamThalamic);
             const int32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -489,12 +501,13 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, i
 // memory s_pref[quad_warps + 1]), then grid-stride over (spike, 256-synapse chunk)
 // items.  The warp taking chunk 0 of spike j also records it in the raster.
 __device__ __forceinline__ void pipe_deliver(const StepArgs &a, const int64_t &t, int ph, int dt, int dthreads,
-                                             int64_t dw, int64_t ndw, uint32_t *s_pref)
+                                             int64_t dw, int64_t ndw, uint32_t *s_pref, bool wait_first)
 {
     __shared__ uint32_t s_wsum[32];
     const int lane = threadIdx.x & 31;
     const int QW = a.quad_warps;
     const uint32_t *cnts = a.qcount + (ph & 3) * QW;
+    if (wait_first) wait_previous_grid();
     const uint32_t rbase = __ldcg(&a.ctl->step_begin[t & 1]);
     // block scan of the counts
     const int per = (QW + dthreads - 1) / dthreads;
@@ -585,25 +598,32 @@ __device__ __forceinline__ void pipe_deliver(const StepArgs &a, const int64_t &t
     }
 }
 
-__global__ void __launch_bounds__(kStepMaxThreads, 1) k_step(const StepArgs a, const int k, const int ph)
+// t_base is read before waiting on the previous kernel: within a graph replay it only
+// changes in the replay's last node, and direct launches are not programmatic.
+__global__ void __launch_bounds__(kStepMaxThreads, 2) k_step(const StepArgs a, const int k, const int ph)
 {
     extern __shared__ uint32_t s_pref[];
+    allow_next_grid();
     const int64_t t = a.ctl->t_base + k;  // used for Philox counters and step tags only
     const int wib = threadIdx.x >> 5;
     if (wib < a.neuron_warps) {
         const int64_t nquads = (a.n + 3) / 4;
         const int64_t nw = static_cast<int64_t>(a.neuron_warps) * gridDim.x;
-        for (int64_t g = static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < a.quad_warps; g += nw)
-            pipe_quad(a, t, ph, g, g * 32 + (threadIdx.x & 31) < nquads, true);
+        bool first = true;
+        for (int64_t g = static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < a.quad_warps; g += nw) {
+            pipe_quad(a, t, ph, g, g * 32 + (threadIdx.x & 31) < nquads, true, first);
+            first = false;
+        }
+        if (first) wait_previous_grid();
     } else {
         const int dthreads = static_cast<int>(blockDim.x) - 32 * a.neuron_warps;
         const int dt = static_cast<int>(threadIdx.x) - 32 * a.neuron_warps;
         const int64_t dw = static_cast<int64_t>(wib - a.neuron_warps) * gridDim.x + blockIdx.x;
-        pipe_deliver(a, t, ph, dt, dthreads, dw, static_cast<int64_t>(dthreads >> 5) * gridDim.x, s_pref);
+        pipe_deliver(a, t, ph, dt, dthreads, dw, static_cast<int64_t>(dthreads >> 5) * gridDim.x, s_pref, true);
     }
 }
 
-__global__ void __launch_bounds__(kStepMaxThreads, 1) k_prime(const StepArgs a)
+__global__ void __launch_bounds__(kStepMaxThreads, 2) k_prime(const StepArgs a)
 {
     const int wib = threadIdx.x >> 5;
     if (wib >= a.neuron_warps) return;
@@ -611,7 +631,7 @@ __global__ void __launch_bounds__(kStepMaxThreads, 1) k_prime(const StepArgs a)
     const int64_t nw = static_cast<int64_t>(a.neuron_warps) * gridDim.x;
     const int64_t t = -1;
     for (int64_t g = static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < a.quad_warps; g += nw)
-        pipe_quad(a, t, -1, g, g * 32 + (threadIdx.x & 31) < nquads, false);
+        pipe_quad(a, t, -1, g, g * 32 + (threadIdx.x & 31) < nquads, false, false);
 }
 
 }  // namespace
@@ -630,9 +650,19 @@ int prepare_step_kernel(const StepArgs &a)
                                                  static_cast<int>(smem)));
 }
 
-void launch_step(const StepArgs &a, int k, int ph, int grid, void *stream)
+int launch_step(const StepArgs &a, int k, int ph, int grid, void *stream, bool programmatic)
 {
-    k_step<<<grid, step_threads(a), step_smem(a), static_cast<cudaStream_t>(stream)>>>(a, k, ph);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(step_threads(a));
+    cfg.dynamicSmemBytes = step_smem(a);
+    cfg.stream = static_cast<cudaStream_t>(stream);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = programmatic ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return static_cast<int>(cudaLaunchKernelEx(&cfg, k_step, a, k, ph));
 }
 
 void launch_prime(const StepArgs &a, int grid, void *stream)
