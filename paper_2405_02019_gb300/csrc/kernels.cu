@@ -325,15 +325,14 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_persistent(const StepArg
 // the same as the two-phase engines.  U and R after A(s) live in buffer s mod 2 (the
 // state after s steps is in buffer (s-1) mod 2).
 //
-// Spike queue of step s (buffers s mod 4): every group of 128 neurons (one warp's 32
-// quads) owns a 128-entry region; the warp writes its spikers' entries (with their
-// row bounds, loaded with the neuron state) there and its spike count into qcount,
-// with plain stores -- no atomic and no dependent load stands after the spike
-// decision.  The rows are prefetched into L2 for the next kernel.  The delivery warps
-// of every CTA prefix-sum the counts in shared memory to number the spikes, and the
-// warp delivering chunk 0 of spike j records it at raster position base + j; the
-// raster base advances once per step (Ctl::step_begin[t mod 2]).  Every buffer choice
-// depends on t mod 64 only, which the launch passes in (`ph`).
+// Spike queue of step s (buffer s mod 4, count Ctl::qcnt[s mod 4]): a warp with
+// spikers reserves room with one atomic and writes their entries (row bounds were
+// loaded with the neuron state).  The rows are prefetched into L2 for the next
+// kernel.  A delivery warp loads the step's spike count and the entry of its first
+// item in the same round trip, then the synapses; the warp delivering chunk 0 of spike
+// j records it at raster position base + j, the raster base advancing once per step
+// (Ctl::step_begin[t mod 2]).  Every buffer choice depends on t mod 64 only, which the
+// launch passes in (`ph`).
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
@@ -470,9 +469,12 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, i
         if (lane >= o) incl += v;
     }
     const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    if (lane == 0) a.qcount[(phn & 3) * a.quad_warps + g] = static_cast<uint32_t>(total);
+    if (total == 0) return;
+    uint32_t base = 0;
+    if (lane == 31) base = atomicAdd(&a.ctl->qcnt[phn & 3], static_cast<uint32_t>(total));
+    base = __shfl_sync(0xFFFFFFFFu, base, 31);
     if (cnt == 0) return;
-    QueueEntry *region = a.queue + (phn & 3) * a.npad + g * 128;
+    QueueEntry *region = a.queue + (phn & 3) * a.npad + base;
     int k = incl - cnt;
     const int64_t sn = t + 1;
 #pragma unroll
@@ -496,70 +498,32 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, i
     }
 }
 
-// D(t), run by the delivery warps of every CTA (dthreads threads, named barrier 2):
-// number the spikes of step t by a prefix sum of the per-group counts (shared
-// memory s_pref[quad_warps + 1]), then grid-stride over (spike, 256-synapse chunk)
-// items.  The warp taking chunk 0 of spike j also records it in the raster.
-__device__ __forceinline__ void pipe_deliver(const StepArgs &a, const int64_t &t, int ph, int dt, int dthreads,
-                                             int64_t dw, int64_t ndw, uint32_t *s_pref, bool wait_first)
+// D(t), run by the delivery warps: grid-stride over (spike, 256-synapse chunk) items
+// of queue t mod 4.  The count, the raster base and the first item's entry are loaded
+// in one round trip.  The warp taking chunk 0 of spike j records it in the raster.
+__device__ __forceinline__ void pipe_deliver(const StepArgs &a, const int64_t &t, int ph, bool leader, int64_t dw,
+                                             int64_t ndw, bool wait_first)
 {
-    __shared__ uint32_t s_wsum[32];
     const int lane = threadIdx.x & 31;
-    const int QW = a.quad_warps;
-    const uint32_t *cnts = a.qcount + (ph & 3) * QW;
-    if (wait_first) wait_previous_grid();
-    const uint32_t rbase = __ldcg(&a.ctl->step_begin[t & 1]);
-    // block scan of the counts
-    const int per = (QW + dthreads - 1) / dthreads;
-    const int lo = dt * per, hi = min(lo + per, QW);
-    uint32_t local = 0;
-    for (int g = lo; g < hi; ++g) {
-        const uint32_t c = __ldcg(cnts + g);
-        s_pref[g] = c;
-        local += c;
-    }
-    uint32_t incl = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    const int dwarp = dt >> 5;
-    if (lane == 31) s_wsum[dwarp] = incl;
-    asm volatile("bar.sync 2, %0;" ::"r"(dthreads) : "memory");
-    uint32_t before = 0;
-    for (int w = 0; w < dwarp; ++w) before += s_wsum[w];
-    uint32_t run = before + incl - local;
-    for (int g = lo; g < hi; ++g) {
-        const uint32_t c = s_pref[g];
-        s_pref[g] = run;
-        run += c;
-    }
-    if (dt == dthreads - 1) s_pref[QW] = run;
-    asm volatile("bar.sync 2, %0;" ::"r"(dthreads) : "memory");
-    const uint32_t n = s_pref[QW];
-    if (blockIdx.x == 0 && dt == 0) {
-        a.ctl->step_begin[(t + 1) & 1] = rbase + n;
-        a.ctl->cursor = rbase + n;
-        if (static_cast<uint64_t>(rbase) + n > a.rast_cap) atomicOr(&a.ctl->err, kErrRaster);
-    }
     const QueueEntry *qbuf = a.queue + (ph & 3) * a.npad;
     const int64_t cpr = a.chunks_per_row;
-    const int64_t items = static_cast<int64_t>(n) * cpr;
     int32_t *const ring = a.ring;
     const int64_t npad = a.npad;
-    for (int64_t it = dw; it < items; it += ndw) {
+    if (wait_first) wait_previous_grid();
+    const uint32_t n = __ldcg(&a.ctl->qcnt[ph & 3]);
+    const uint32_t rbase = __ldcg(&a.ctl->step_begin[t & 1]);
+    if (leader) {
+        a.ctl->step_begin[(t + 1) & 1] = rbase + n;
+        a.ctl->cursor = rbase + n;
+        a.ctl->qcnt[(ph + 2) & 3] = 0;  // the queue the next kernel fills after this one
+        if (static_cast<uint64_t>(rbase) + n > a.rast_cap) atomicOr(&a.ctl->err, kErrRaster);
+    }
+    for (int64_t it = dw;; it += ndw) {
         const int64_t j = it / cpr;
+        if (j >= npad) break;
+        const int4 raw = __ldcg(reinterpret_cast<const int4 *>(qbuf + j));  // issued before n is known
+        if (j >= n) break;
         const int64_t c = it - j * cpr;
-        // group holding spike j: the last g with s_pref[g] <= j
-        int glo = 0, ghi = QW - 1;
-        while (glo < ghi) {
-            const int mid = (glo + ghi + 1) >> 1;
-            if (s_pref[mid] <= static_cast<uint32_t>(j)) glo = mid;
-            else ghi = mid - 1;
-        }
-        const int4 raw = __ldcg(reinterpret_cast<const int4 *>(qbuf + static_cast<int64_t>(glo) * 128 +
-                                                               (j - s_pref[glo])));
         if (c == 0 && lane == 0) {
             const uint64_t pos = static_cast<uint64_t>(rbase) + static_cast<uint64_t>(j);
             if (pos < a.rast_cap) {
@@ -602,7 +566,6 @@ __device__ __forceinline__ void pipe_deliver(const StepArgs &a, const int64_t &t
 // changes in the replay's last node, and direct launches are not programmatic.
 __global__ void __launch_bounds__(kStepMaxThreads, 2) k_step(const StepArgs a, const int k, const int ph)
 {
-    extern __shared__ uint32_t s_pref[];
     allow_next_grid();
     const int64_t t = a.ctl->t_base + k;  // used for Philox counters and step tags only
     const int wib = threadIdx.x >> 5;
@@ -616,10 +579,10 @@ __global__ void __launch_bounds__(kStepMaxThreads, 2) k_step(const StepArgs a, c
         }
         if (first) wait_previous_grid();
     } else {
-        const int dthreads = static_cast<int>(blockDim.x) - 32 * a.neuron_warps;
-        const int dt = static_cast<int>(threadIdx.x) - 32 * a.neuron_warps;
+        const int dwarps = static_cast<int>(blockDim.x >> 5) - a.neuron_warps;
+        const bool leader = blockIdx.x == 0 && threadIdx.x == 32 * a.neuron_warps;
         const int64_t dw = static_cast<int64_t>(wib - a.neuron_warps) * gridDim.x + blockIdx.x;
-        pipe_deliver(a, t, ph, dt, dthreads, dw, static_cast<int64_t>(dthreads >> 5) * gridDim.x, s_pref, true);
+        pipe_deliver(a, t, ph, leader, dw, static_cast<int64_t>(dwarps) * gridDim.x, true);
     }
 }
 
@@ -640,15 +603,9 @@ int step_grid(int num_sms) { return num_sms; }
 
 int step_threads(const StepArgs &a) { return 32 * (a.neuron_warps + kStepDeliverWarps); }
 
-static size_t step_smem(const StepArgs &a) { return sizeof(uint32_t) * (static_cast<size_t>(a.quad_warps) + 1); }
+static size_t step_smem(const StepArgs &) { return 0; }
 
-int prepare_step_kernel(const StepArgs &a)
-{
-    const size_t smem = step_smem(a);
-    if (smem <= 48 * 1024) return 0;
-    return static_cast<int>(cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(smem)));
-}
+int prepare_step_kernel(const StepArgs &) { return 0; }
 
 int launch_step(const StepArgs &a, int k, int ph, int grid, void *stream, bool programmatic)
 {
