@@ -329,6 +329,34 @@ def run_gpu(args):
                 "frac": kernels[dom]["gbs"] / peak, "traffic": traffic,
                 "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth, burst)"}
 
+    # delivery alone at saturating load: random senders of the same network, fresh list
+    # per launch (rows >> L2 for the larger lists); the ring is left modified, so this
+    # runs after every other measurement
+    sat = []
+    outdeg = net.out_degrees()
+    rng = np.random.default_rng(1234 + rank)
+    for nsp in args.saturating:
+        ms_list, ev_list = [], []
+        for r in range(args.saturating_reps + 2):
+            spk = rng.integers(0, n, nsp).astype(np.int32)
+            dev_spk = torch.from_numpy(spk).to(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            net.deliver_spikes(dev_spk, 0)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if r >= 2:
+                ms_list.append(e0.elapsed_time(e1))
+                ev_list.append(int(outdeg[spk].sum()))
+        ms_avg = float(np.mean(ms_list))
+        ev_avg = float(np.mean(ev_list))
+        nbytes = EVENT_BYTES * ev_avg + SPIKE_BYTES * nsp
+        sat.append({"spikers": nsp, "events": ev_avg, "ms": ms_avg, "bytes": nbytes,
+                    "gbs": nbytes / (ms_avg * 1e-3) / 1e9, "frac": nbytes / (ms_avg * 1e-3) / 1e9 / peak,
+                    "reductions_per_s": ev_avg / (ms_avg * 1e-3)})
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu, _, _ = cpu_oracle_sample(model, wl, args.cpu_ticks)
@@ -359,6 +387,10 @@ def run_gpu(args):
         "gpu_launches": args.steps * {snn.ENGINE_PERSISTENT: 1, snn.ENGINE_PIPELINED: tps + 1,
                                       snn.ENGINE_GRAPH: 2 * tps + 1}[info.engine],
         "roofline": roofline, "kernels": kernels,
+        "delivery_saturating": {"kernel": "k_deliver_list", "bound": "hbm", "peak": peak, "unit": "GB/s",
+                                "note": "phase 2 alone over random senders of the same network "
+                                        "(13 B per event + 20 B per sender); int32 red.add into the ring",
+                                "points": sat},
         "clocks": clk.summary(), "build_s": build_s,
         "paper_context": {"fpga_best_rtf": 0.79, "hardware": "Intel Agilex 7 FPGA (horiz/multi/s)"},
     }
@@ -381,6 +413,8 @@ def main():
     ap.add_argument("--cpu-ticks", type=int, default=2000)
     ap.add_argument("--reference-ticks", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--saturating", type=int, nargs="*", default=[2048, 8192, 20480])
+    ap.add_argument("--saturating-reps", type=int, default=5)
     ap.add_argument("--engine", default="default", choices=["default", "graph", "persistent", "pipelined"])
     args = ap.parse_args()
     if args.warmup < 3:

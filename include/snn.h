@@ -229,6 +229,10 @@ int snn_read_rates(snn_net *net, int64_t t_begin, int64_t t_end, double *pop_rat
 /* Fills `out` with the network's constants and counters (host only, no wait). */
 int snn_get_info(const snn_net *net, snn_info *out);
 
+/* Copies every neuron's out-degree (synapses in its row, padding excluded) into the
+ * host array out[n_neurons] (host only). */
+int snn_get_out_degrees(const snn_net *net, int32_t *out);
+
 /* Fills `out` with the arena layout (host only). */
 int snn_get_layout(const snn_net *net, snn_layout *out);
 
@@ -238,6 +242,16 @@ int snn_get_layout(const snn_net *net, snn_layout *out);
  * engine: of its one step kernel in ms_update, 0 in ms_deliver).  Same dynamics as
  * snn_step_n.  Errors as snn_step_n. */
 int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *ms_update, double *ms_deliver);
+
+/* Phase 2 of Listing push2 (§3.1) alone, for measurement and tests: adds every
+ * synapse of the senders spikers[0 .. n_spikers) (device int32 neuron ids, each
+ * below n_neurons; repeats allowed) into the ring as spikes of step t, i.e.
+ * W[(t + d) mod 64][target] += w, in one launch of `blocks` CTAs (0 = full
+ * occupancy) on `cuda_stream`; returns without waiting.  The ring keeps the added
+ * input, so the simulated dynamics change accordingly.
+ * Errors: SNN_EINVAL (null or negative arguments), SNN_ECUDA. */
+int snn_deliver_spikes(snn_net *net, const int32_t *spikers, int64_t n_spikers, int64_t t, int32_t blocks,
+                       void *cuda_stream);
 
 /* Releases host-side state (not the caller's arena).  NULL is ignored. */
 void snn_destroy(snn_net *net);

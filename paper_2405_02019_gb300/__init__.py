@@ -167,6 +167,11 @@ def snn_profile_steps(handle: int, n_steps: int, stream: int):
     return a.value, b.value
 
 
+def snn_deliver_spikes(handle: int, spikers_ptr: int, n: int, t: int, blocks: int, stream: int) -> None:
+    _check(load().snn_deliver_spikes(C.c_void_p(handle), C.c_void_p(spikers_ptr), int(n), int(t), int(blocks),
+                                     C.c_void_p(stream)), "snn_deliver_spikes")
+
+
 def snn_destroy(handle: int) -> None:
     if handle:
         load().snn_destroy(C.c_void_p(handle))
@@ -221,11 +226,23 @@ class Network:
     def info(self) -> snn_info:
         return snn_get_info(self._handle)
 
+    def out_degrees(self) -> np.ndarray:
+        out = np.zeros(self.n_neurons, np.int32)
+        _check(load().snn_get_out_degrees(C.c_void_p(self._handle), C.c_void_p(_ptr(out))), "snn_get_out_degrees")
+        return out
+
     def layout(self) -> snn_layout:
         return snn_get_layout(self._handle)
 
     def profile_steps(self, n_steps: int, stream=None):
         return snn_profile_steps(self._handle, n_steps, self._stream(stream))
+
+    def deliver_spikes(self, spikers, t: int, blocks: int = 0, stream=None) -> None:
+        """Phase 2 alone for a device int32 tensor of senders (see snn_deliver_spikes)."""
+        import torch
+
+        assert spikers.dtype == torch.int32 and spikers.is_cuda and spikers.is_contiguous()
+        snn_deliver_spikes(self._handle, spikers.data_ptr(), spikers.numel(), t, blocks, self._stream(stream))
 
     def device_view(self, field: str, dtype, count: int, offset_elems: int = 0):
         """A torch view of one device buffer of the arena (inspection and tests)."""

@@ -608,6 +608,25 @@ int snn_get_layout(const snn_net *net, snn_layout *out)
     return SNN_OK;
 }
 
+int snn_get_out_degrees(const snn_net *net, int32_t *out)
+{
+    if (!net || !out) return fail(SNN_EINVAL, "null argument");
+    std::copy(net->out_degree.begin(), net->out_degree.end(), out);
+    return SNN_OK;
+}
+
+int snn_deliver_spikes(snn_net *net, const int32_t *spikers, int64_t n_spikers, int64_t t, int32_t blocks,
+                       void *cuda_stream)
+{
+    if (!net || (n_spikers > 0 && !spikers)) return fail(SNN_EINVAL, "null argument");
+    if (n_spikers < 0 || t < 0 || blocks < 0) return fail(SNN_EINVAL, "negative argument");
+    if (n_spikers == 0) return SNN_OK;
+    const int grid = blocks > 0 ? blocks : net->num_sms * snn::deliver_list_blocks_per_sm();
+    snn::launch_deliver_list(net->args, spikers, n_spikers, t, grid, cuda_stream);
+    SNN_CUDA_TRY(cudaGetLastError());
+    return SNN_OK;
+}
+
 void snn_destroy(snn_net *net)
 {
     if (!net) return;

@@ -135,6 +135,8 @@ int resolve_threads(int32_t requested);
 void launch_update(const StepArgs &a, int k, int grid, void *stream);
 void launch_deliver(const StepArgs &a, int k, int grid, void *stream);
 void launch_advance(Ctl *ctl, int64_t m, void *stream);
+void launch_deliver_list(const StepArgs &a, const int32_t *list, int64_t n, int64_t t, int grid, void *stream);
+int deliver_list_blocks_per_sm();
 int update_grid(int64_t n);
 int persistent_blocks_per_sm();
 int launch_persistent(const StepArgs &a, int64_t n_steps, int grid, void *stream);

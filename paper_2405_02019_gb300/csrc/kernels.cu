@@ -173,12 +173,11 @@ __device__ __forceinline__ void append_spikes(const StepArgs &a, int64_t t, int6
     }
 }
 
-// Phase 2 for the spikers queued in raster[begin, end), work items grid-strided over
-// warps: item = (spiker, 256-synapse chunk of its row).
-__device__ __forceinline__ void deliver_range(const StepArgs &a, int64_t t, uint32_t begin, uint32_t end,
-                                              int64_t warp, int64_t nwarps)
+// Phase 2 for the spikers list[0 .. nspk), work items grid-strided over warps:
+// item = (spiker, 256-synapse chunk of its row).
+__device__ __forceinline__ void deliver_list(const StepArgs &a, int64_t t, const int32_t *list, int64_t nspk,
+                                             int64_t warp, int64_t nwarps)
 {
-    const int64_t nspk = end > begin ? static_cast<int64_t>(end - begin) : 0;
     const int64_t items = nspk * a.chunks_per_row;
     const int lane = threadIdx.x & 31;
     int32_t *const ring = a.ring;
@@ -186,7 +185,7 @@ __device__ __forceinline__ void deliver_range(const StepArgs &a, int64_t t, uint
     for (int64_t it = warp; it < items; it += nwarps) {
         const int64_t j = it / a.chunks_per_row;
         const int64_t c = it - j * a.chunks_per_row;
-        const int32_t s = __ldcg(a.rast_nrn + begin + j);
+        const int32_t s = __ldcg(list + j);
         const int64_t rs = a.row_ptr[s];
         const int64_t re = a.row_ptr[s + 1];
         const int64_t off = rs + c * kChunk;
@@ -237,7 +236,16 @@ __global__ void __launch_bounds__(kDeliverThreads) k_deliver(const StepArgs a, c
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->step_begin[(t + 1) & 1] = cur;
     const uint32_t end = cur < a.rast_cap ? cur : a.rast_cap;
     const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-    deliver_range(a, t, begin, end, spread_warp(), nwarps);
+    const int64_t nspk = end > begin ? static_cast<int64_t>(end - begin) : 0;
+    deliver_list(a, t, a.rast_nrn + begin, nspk, spread_warp(), nwarps);
+}
+
+// Phase 2 alone for a caller-given list of senders (measurement and tests).
+__global__ void __launch_bounds__(kDeliverThreads) k_deliver_list(const StepArgs a, const int32_t *list,
+                                                                  const int64_t n, const int64_t t)
+{
+    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    deliver_list(a, t, list, n, spread_warp(), nwarps);
 }
 
 __global__ void k_advance(Ctl *ctl, int64_t m) { ctl->t_base += m; }
@@ -301,7 +309,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_persistent(const StepArg
         if (!grid_barrier(a, ctl, ++nbar)) return;
         const uint32_t cur = ld_acquire_u32(&ctl->cursor);
         const uint32_t end = cur < a.rast_cap ? cur : a.rast_cap;
-        deliver_range(a, t, begin, end, warp, nwarps);
+        deliver_list(a, t, a.rast_nrn + begin, end > begin ? static_cast<int64_t>(end - begin) : 0, warp, nwarps);
         begin = cur;
         if (!grid_barrier(a, ctl, ++nbar)) return;
     }
@@ -641,6 +649,18 @@ void launch_update(const StepArgs &a, int k, int grid, void *stream)
 void launch_deliver(const StepArgs &a, int k, int grid, void *stream)
 {
     k_deliver<<<grid, kDeliverThreads, 0, static_cast<cudaStream_t>(stream)>>>(a, k);
+}
+
+void launch_deliver_list(const StepArgs &a, const int32_t *list, int64_t n, int64_t t, int grid, void *stream)
+{
+    k_deliver_list<<<grid, kDeliverThreads, 0, static_cast<cudaStream_t>(stream)>>>(a, list, n, t);
+}
+
+int deliver_list_blocks_per_sm()
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_deliver_list, kDeliverThreads, 0) != cudaSuccess) return 1;
+    return nb > 0 ? nb : 1;
 }
 
 void launch_advance(Ctl *ctl, int64_t m, void *stream)

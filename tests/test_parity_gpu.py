@@ -185,6 +185,28 @@ def test_profile_steps_same_dynamics(model, tiny, engine):
     net.close()
 
 
+@pytest.mark.parametrize("nspk", [1, 37, 700])
+def test_deliver_spikes_matches_oracle_network(model, tiny, nspk):
+    """Phase 2 alone (snn_deliver_spikes) on a zero ring: every cell equals the sum of
+    w over the senders' synapses with (t + d) mod 64 and that target (repeats kept)."""
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed)
+    assert np.array_equal(net.out_degrees(), np.diff(onet.row_ptr))
+    rng = np.random.default_rng(nspk)
+    spikers = rng.integers(0, onet.n, nspk).astype(np.int32)
+    t = 61
+    net.deliver_spikes(torch.from_numpy(spikers).cuda(), t)
+    torch.cuda.synchronize()
+    npad = int(net.layout().n_neurons_padded)
+    ring = net.device_view("ring", torch.int32, 64 * npad).cpu().numpy().reshape(64, npad).astype(np.int64)
+    exp = np.zeros((64, npad), np.int64)
+    for s_ in spikers:
+        a, b = onet.row_ptr[s_], onet.row_ptr[s_ + 1]
+        np.add.at(exp, ((t + onet.delay[a:b].astype(np.int64)) % 64, onet.post[a:b]), onet.w_fx[a:b])
+    assert np.array_equal(ring, exp)
+    net.close()
+
+
 # ------------------------------------------------------------ hand-placed spikes
 
 
