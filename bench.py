@@ -308,10 +308,17 @@ def run_gpu(args):
                       "spikes_per_launch": pspk / prof_ticks},
     }
     if info.engine == snn.ENGINE_PIPELINED:
-        step_bytes = upd_bytes + dlv_bytes
-        kernels = {"k_step": {"avg_us": ms_u / prof_ticks * 1e3, "bytes_per_launch": step_bytes,
-                              "gbs": step_bytes / (ms_u / prof_ticks * 1e-3) / 1e9, "share": 1.0,
-                              "events_per_launch": pe / prof_ticks, "spikes_per_launch": pspk / prof_ticks}}
+        # the timed region is k_step launches only (plus one k_advance per graph): its
+        # average launch duration there is the region's time per step
+        step_bytes = UPDATE_BYTES_PER_NEURON * n + (EVENT_BYTES * events + SPIKE_BYTES * spikes) / (args.steps * tps)
+        avg_s = secs_max / (args.steps * tps)
+        kernels = {"k_step": {"avg_us": avg_s * 1e6, "bytes_per_launch": step_bytes,
+                              "gbs": step_bytes / avg_s / 1e9, "share": 1.0,
+                              "events_per_launch": events / (args.steps * tps),
+                              "spikes_per_launch": spikes / (args.steps * tps),
+                              "isolated_avg_us": ms_u / prof_ticks * 1e3,
+                              "note": "avg_us over the timed graph replays; isolated_avg_us brackets single "
+                                      "launches with CUDA events (launch latency included)"}}
         dom = "k_step"
     elif info.engine == snn.ENGINE_PERSISTENT:
         # one cooperative launch per bench step: all of its steps' algorithmic bytes over its duration
@@ -388,6 +395,7 @@ def run_gpu(args):
                                       snn.ENGINE_GRAPH: 2 * tps + 1}[info.engine],
         "roofline": roofline, "kernels": kernels,
         "delivery_saturating": {"kernel": "k_deliver_list", "bound": "hbm", "peak": peak, "unit": "GB/s",
+                                "traffic_20480": _recorded_traffic("k_deliver_list"),
                                 "note": "phase 2 alone over random senders of the same network "
                                         "(13 B per event + 20 B per sender); int32 red.add into the ring",
                                 "points": sat},
