@@ -243,6 +243,21 @@ int snn_get_layout(const snn_net *net, snn_layout *out);
  * snn_step_n.  Errors as snn_step_n. */
 int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *ms_update, double *ms_deliver);
 
+/* Checkpoint of the dynamic state after the steps enqueued so far (waits for them):
+ * neuron state, ring, control block and (pipelined engine) the next step's queued
+ * spikes, as one host byte blob.  With host_buf == NULL only *written (the size) is
+ * set.  Spikes recorded so far are first moved to the host history (read them with
+ * snn_read_spikes as usual).  The network itself and the seed are not saved: resume
+ * on a handle built from the same spec.  Because every random draw is counter-based
+ * on (seed, step, neuron), a resumed run reproduces the uninterrupted one bit for bit.
+ * Errors: SNN_ENOMEM (capacity < size), SNN_ECUDA, plus pending device errors. */
+int snn_save_state(snn_net *net, void *host_buf, uint64_t capacity, uint64_t *written);
+
+/* Restores a blob from snn_save_state into `net` (same spec; checked by shape and
+ * engine), including the step counter; the host spike history starts empty.
+ * Errors: SNN_EINVAL (not a state blob, or another shape/engine), SNN_ECUDA. */
+int snn_load_state(snn_net *net, const void *host_buf, uint64_t bytes);
+
 /* Phase 2 of Listing push2 (§3.1) alone, for measurement and tests: adds every
  * synapse of the senders spikers[0 .. n_spikers) (device int32 neuron ids, each
  * below n_neurons; repeats allowed) into the ring as spikes of step t, i.e.

@@ -114,6 +114,10 @@ def lib():
         L.or_run.argtypes = [P(OrModel), C.c_uint64, C.c_int64, vp, vp, vp, vp, vp, vp, vp, vp,
                              vp, C.c_int64, C.c_int64, vp, vp, C.c_int64, P(C.c_int64)]
         L.or_run.restype = C.c_int
+        L.or_quantize_i8.argtypes = [C.c_int32, vp, C.c_int64, vp, vp, vp, vp, vp, vp]
+        L.or_quantize_bf16.argtypes = [C.c_int64, vp, vp]
+        L.or_run_f64.argtypes = L.or_run.argtypes
+        L.or_run_f64.restype = C.c_int
         _lib = L
     return _lib
 
@@ -240,15 +244,42 @@ def network_from_edges(n: int, pre, post, w_fx, delay, u0, pop_off=None) -> Netw
                    np.ascontiguousarray(np.asarray(u0, np.float32)))
 
 
+def quantize_i8(net: "Network", n_pops: int = 8):
+    """Read-back weights of the int8 per-population-pair store, plus its tables."""
+    out = np.zeros(max(1, len(net.w_fx)), np.int32)
+    base = np.zeros(64, np.int32)
+    step = np.zeros(64, np.int32)
+    post = net.post if len(net.post) else np.zeros(1, np.int32)
+    w = net.w_fx if len(net.w_fx) else np.zeros(1, np.int32)
+    lib().or_quantize_i8(n_pops, _p(net.pop_off), net.n, _p(net.row_ptr), _p(post), _p(w), _p(out), _p(base),
+                         _p(step))
+    return out[: len(net.w_fx)], base.reshape(8, 8), step.reshape(8, 8)
+
+
+def quantize_bf16(w_fx: np.ndarray) -> np.ndarray:
+    w_fx = np.ascontiguousarray(w_fx, np.int32)
+    out = np.zeros(max(1, len(w_fx)), np.int32)
+    lib().or_quantize_bf16(len(w_fx), _p(w_fx if len(w_fx) else np.zeros(1, np.int32)), _p(out))
+    return out[: len(w_fx)]
+
+
+def with_weights(net: "Network", w_fx: np.ndarray) -> "Network":
+    return Network(net.n, net.pop_off, net.row_ptr, net.post, np.ascontiguousarray(w_fx, np.int32), net.delay,
+                   net.u0)
+
+
 class Sim:
     """State of one circuit under the oracle: U, I (FP32), R (steps), exact ring."""
 
-    def __init__(self, m, net: Network, seed: int):
+    def __init__(self, m, net: Network, seed: int, fp64: bool = False):
+        """fp64=True runs the same loop with FP64 neuron state and propagators."""
         self.m, self.net, self.seed = m, net, int(seed)
         self._cm = _model(m)
+        self.fp64 = fp64
         n = net.n
-        self.U = net.u0.copy()
-        self.I = np.zeros(n, np.float32)
+        dt = np.float64 if fp64 else np.float32
+        self.U = net.u0.astype(dt)
+        self.I = np.zeros(n, dt)
         self.R = np.zeros(n, np.int32)
         self.W = np.zeros(D_MAX * n, np.int64)
         self.t = 0
@@ -265,7 +296,8 @@ class Sim:
         post = net.post if len(net.post) else np.zeros(1, np.int32)
         w = net.w_fx if len(net.w_fx) else np.zeros(1, np.int32)
         d = net.delay if len(net.delay) else np.zeros(1, np.uint8)
-        rc = lib().or_run(C.byref(self._cm), self.seed, net.n, _p(net.pop_off), _p(net.row_ptr),
+        run = lib().or_run_f64 if self.fp64 else lib().or_run
+        rc = run(C.byref(self._cm), self.seed, net.n, _p(net.pop_off), _p(net.row_ptr),
                           _p(post), _p(w), _p(d), _p(self.U), _p(self.I), _p(self.R), _p(self.W),
                           self.t, n_steps, _p(rt), _p(ri), cap, C.byref(nr))
         if rc < 0:

@@ -489,3 +489,144 @@ int or_run(const or_model *m, uint64_t seed, int64_t N, const int64_t *pop_off,
     free(queue);
     return status;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Compressed synapse records (reduced-precision weights, §5.3): the weights a  */
+/* compressed store reproduces, computed here from their definitions.           */
+/* ------------------------------------------------------------------------ */
+
+static int or_pop_of(int32_t n_pops, const int64_t *pop_off, int64_t i)
+{
+    int b = 0;
+    while (b + 1 < n_pops && i >= pop_off[b + 1]) ++b;
+    return b;
+}
+
+/* int8 codes with one affine scale per (source population, target population)
+ * pair, fitted to the pair's weights ("deviation from the mean" storage): with lo,
+ * hi the pair's smallest and largest weight, base = lo + (hi - lo) div 2 and step =
+ * max(1, ceil((hi - lo) / 254)); a weight w becomes q = clamp(round((w - base) /
+ * step), -127, 127) and reads back as base + q step.  Rows are given as the CSR of
+ * the network (row i = source neuron i).  Writes the read-back weights to w_out and
+ * the [8][8] tables to base_out / step_out. */
+void or_quantize_i8(int32_t n_pops, const int64_t *pop_off, int64_t N, const int64_t *row_ptr, const int32_t *post,
+                    const int32_t *w_fx, int32_t *w_out, int32_t *base_out, int32_t *step_out)
+{
+    int64_t lo[OR_MAX_POPS][OR_MAX_POPS], hi[OR_MAX_POPS][OR_MAX_POPS];
+    int seen[OR_MAX_POPS][OR_MAX_POPS];
+    memset(seen, 0, sizeof(seen));
+    for (int64_t i = 0; i < N; ++i) {
+        const int a = or_pop_of(n_pops, pop_off, i);
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int b = or_pop_of(n_pops, pop_off, post[e]);
+            if (!seen[a][b] || w_fx[e] < lo[a][b]) lo[a][b] = w_fx[e];
+            if (!seen[a][b] || w_fx[e] > hi[a][b]) hi[a][b] = w_fx[e];
+            seen[a][b] = 1;
+        }
+    }
+    for (int a = 0; a < OR_MAX_POPS; ++a)
+        for (int b = 0; b < OR_MAX_POPS; ++b) {
+            int64_t base = 0, step = 1;
+            if (a < n_pops && b < n_pops && seen[a][b]) {
+                base = lo[a][b] + (hi[a][b] - lo[a][b]) / 2;
+                step = (hi[a][b] - lo[a][b] + 253) / 254;
+                if (step < 1) step = 1;
+            }
+            base_out[a * OR_MAX_POPS + b] = (int32_t)base;
+            step_out[a * OR_MAX_POPS + b] = (int32_t)step;
+        }
+    for (int64_t i = 0; i < N; ++i) {
+        const int a = or_pop_of(n_pops, pop_off, i);
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            const int b = or_pop_of(n_pops, pop_off, post[e]);
+            const int64_t base = base_out[a * OR_MAX_POPS + b], step = step_out[a * OR_MAX_POPS + b];
+            long long q = llround((double)(w_fx[e] - base) / (double)step);
+            if (q > 127) q = 127;
+            if (q < -127) q = -127;
+            w_out[e] = (int32_t)(base + q * step);
+        }
+    }
+}
+
+/* bfloat16 currents: the weight in pA (w_fx 2^-12) as a float, rounded to 8
+ * significand bits with ties to even, read back in 2^-12 pA units (exact). */
+void or_quantize_bf16(int64_t S, const int32_t *w_fx, int32_t *w_out)
+{
+    for (int64_t e = 0; e < S; ++e) {
+        float f = (float)w_fx[e] * (1.0f / 4096.0f);
+        uint32_t u;
+        memcpy(&u, &f, 4);
+        const uint32_t lsb = (u >> 16) & 1u;
+        u = (u + 0x7FFFu + lsb) & 0xFFFF0000u;
+        float g;
+        memcpy(&g, &u, 4);
+        w_out[e] = (int32_t)(g * 4096.0f);
+    }
+}
+
+/* The step loop of or_run with FP64 neuron state and FP64 propagators (the
+ * reference for the accuracy of the FP32 and compressed forms).  Synaptic and
+ * thalamic input are the same exact integers (2^-12 pA) as in or_run. */
+int or_run_f64(const or_model *m, uint64_t seed, int64_t N, const int64_t *pop_off, const int64_t *row_ptr,
+               const int32_t *post, const int32_t *w_fx, const uint8_t *dly, double *U, double *I, int32_t *R,
+               int64_t *W, int64_t t0, int64_t n_steps, int32_t *rast_t, int32_t *rast_i, int64_t rast_cap,
+               int64_t *n_rast)
+{
+    double c[6];
+    or_constants(m, c);
+    const double p11 = c[1], p22 = c[2], p21 = c[5];
+    const double theta = m->u_thr_mV - m->u_rest_mV, u_reset = m->u_reset_mV - m->u_rest_mV;
+    float f[5];
+    int32_t k2[2];
+    or_step_constants(m, f, k2);
+    const int32_t t_ref = k2[0];
+    const int64_t w_ext = k2[1];
+    uint64_t C[OR_MAX_POPS][OR_PKMAX];
+    for (int b = 0; b < m->n_pops; ++b) or_poisson_table(m, b, C[b]);
+    int32_t *queue = (int32_t *)malloc((size_t)(N > 0 ? N : 1) * sizeof(int32_t));
+    if (!queue) return -1;
+    int status = 0;
+    int64_t nr = *n_rast;
+    for (int64_t t = t0; t < t0 + n_steps; ++t) {
+        const int64_t slot = t % OR_DMAX;
+        int64_t nq = 0;
+        int b = 0;
+        for (int64_t i = 0; i < N; ++i) {
+            while (i >= pop_off[b + 1]) ++b;
+            const int32_t T = or_poisson_count(or_poisson_uniform(seed, t, i), C[b]);
+            const int64_t in = W[slot * N + i] + (int64_t)T * w_ext;
+            W[slot * N + i] = 0;
+            int spike = 0;
+            if (R[i] == 0) {
+                double x = p22 * U[i] + p21 * I[i];
+                if (x >= theta) {
+                    spike = 1;
+                    x = u_reset;
+                    R[i] = t_ref;
+                }
+                U[i] = x;
+            } else {
+                U[i] = u_reset;
+                R[i] -= 1;
+            }
+            I[i] = p11 * I[i] + (double)in / 4096.0;
+            if (spike) {
+                queue[nq++] = (int32_t)i;
+                if (nr < rast_cap) {
+                    rast_t[nr] = (int32_t)t;
+                    rast_i[nr] = (int32_t)i;
+                } else if (status == 0) {
+                    status = 1;
+                }
+                ++nr;
+            }
+        }
+        for (int64_t q = 0; q < nq; ++q) {
+            const int64_t s = queue[q];
+            for (int64_t e = row_ptr[s]; e < row_ptr[s + 1]; ++e) W[((t + dly[e]) % OR_DMAX) * N + post[e]] += w_fx[e];
+        }
+    }
+    *n_rast = nr;
+    free(queue);
+    return status;
+}

@@ -226,6 +226,20 @@ class Network:
     def info(self) -> snn_info:
         return snn_get_info(self._handle)
 
+    def save_state(self) -> bytes:
+        """Checkpoint of the dynamic state (see snn_save_state)."""
+        lib = load()
+        n = C.c_uint64()
+        _check(lib.snn_save_state(C.c_void_p(self._handle), None, 0, C.byref(n)), "snn_save_state")
+        buf = np.zeros(n.value, np.uint8)
+        _check(lib.snn_save_state(C.c_void_p(self._handle), C.c_void_p(_ptr(buf)), n.value, C.byref(n)),
+               "snn_save_state")
+        return buf.tobytes()
+
+    def load_state(self, blob: bytes) -> None:
+        buf = np.frombuffer(blob, np.uint8).copy()
+        _check(load().snn_load_state(C.c_void_p(self._handle), C.c_void_p(_ptr(buf)), len(buf)), "snn_load_state")
+
     def out_degrees(self) -> np.ndarray:
         out = np.zeros(self.n_neurons, np.int32)
         _check(load().snn_get_out_degrees(C.c_void_p(self._handle), C.c_void_p(_ptr(out))), "snn_get_out_degrees")

@@ -112,6 +112,8 @@ PROTOTYPES = {
     "snn_profile_steps": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]),
     "snn_get_out_degrees": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "snn_save_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.POINTER(C.c_uint64)]),
+    "snn_load_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64]),
     "snn_deliver_spikes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p]),
     "snn_destroy": (None, [C.c_void_p]),
     "snn_step_static": (C.c_int, [C.c_void_p, C.POINTER(snn_static_io), C.c_uint64, C.c_int64, C.c_void_p]),

@@ -608,6 +608,86 @@ int snn_get_layout(const snn_net *net, snn_layout *out)
     return SNN_OK;
 }
 
+namespace {
+
+constexpr uint64_t kStateMagic = 0x534E4E5354415431ull;  // "SNNSTAT1"
+
+struct StateHeader {
+    uint64_t magic;
+    uint64_t bytes;
+    int64_t n, npad, t;
+    int32_t engine, n_segments;
+};
+
+// Device segments that make up the dynamic state, as (arena offset, bytes).
+std::vector<std::pair<uint64_t, uint64_t>> state_segments(const snn_net *net)
+{
+    const snn::Layout &L = net->L;
+    std::vector<std::pair<uint64_t, uint64_t>> seg = {
+        {L.ctl, sizeof(snn::Ctl)}, {L.U, 4 * uint64_t(net->npad)}, {L.I, 4 * uint64_t(net->npad)},
+        {L.R, uint64_t(net->npad)}, {L.ring, 4 * uint64_t(snn::kDMax) * net->npad}};
+    if (net->engine == SNN_ENGINE_PIPELINED) {
+        seg.push_back({L.U2, 4 * uint64_t(net->npad)});
+        seg.push_back({L.R2, uint64_t(net->npad)});
+        seg.push_back({L.queue, 4 * sizeof(snn::QueueEntry) * net->npad});
+    }
+    return seg;
+}
+
+}  // namespace
+
+int snn_save_state(snn_net *net, void *host_buf, uint64_t capacity, uint64_t *written)
+{
+    if (!net || !written) return fail(SNN_EINVAL, "null argument");
+    const auto seg = state_segments(net);
+    uint64_t total = sizeof(StateHeader);
+    for (const auto &sg : seg) total += sg.second;
+    *written = total;
+    if (!host_buf) return SNN_OK;
+    if (capacity < total) return fail(SNN_ENOMEM, "state buffer too small");
+    int rc = drain(net);  // spikes so far go to the host history; the device raster restarts at 0
+    if (rc) return rc;
+    StateHeader h{kStateMagic, total, net->n, net->npad, net->t, net->engine, static_cast<int32_t>(seg.size())};
+    uint8_t *out = static_cast<uint8_t *>(host_buf);
+    std::memcpy(out, &h, sizeof(h));
+    uint64_t off = sizeof(h);
+    for (const auto &sg : seg) {
+        SNN_CUDA_TRY(cudaMemcpy(out + off, net->arena + sg.first, sg.second, cudaMemcpyDeviceToHost));
+        off += sg.second;
+    }
+    return SNN_OK;
+}
+
+int snn_load_state(snn_net *net, const void *host_buf, uint64_t bytes)
+{
+    if (!net || !host_buf) return fail(SNN_EINVAL, "null argument");
+    if (bytes < sizeof(StateHeader)) return fail(SNN_EINVAL, "state buffer too small");
+    StateHeader h;
+    std::memcpy(&h, host_buf, sizeof(h));
+    const auto seg = state_segments(net);
+    uint64_t total = sizeof(StateHeader);
+    for (const auto &sg : seg) total += sg.second;
+    if (h.magic != kStateMagic || h.bytes != total || bytes < total)
+        return fail(SNN_EINVAL, "not a state saved by snn_save_state");
+    if (h.n != net->n || h.npad != net->npad || h.engine != net->engine || h.n_segments != static_cast<int32_t>(seg.size()))
+        return fail(SNN_EINVAL, "state was saved from a network of another shape or engine");
+    int rc = wait_done(net);
+    if (rc) return rc;
+    const uint8_t *in = static_cast<const uint8_t *>(host_buf);
+    uint64_t off = sizeof(h);
+    for (const auto &sg : seg) {
+        SNN_CUDA_TRY(cudaMemcpy(net->arena + sg.first, in + off, sg.second, cudaMemcpyHostToDevice));
+        off += sg.second;
+    }
+    net->t = h.t;
+    net->hist_t.clear();
+    net->hist_i.clear();
+    net->read_pos = 0;
+    net->events_read = 0;
+    net->device_error = 0;
+    return SNN_OK;
+}
+
 int snn_get_out_degrees(const snn_net *net, int32_t *out)
 {
     if (!net || !out) return fail(SNN_EINVAL, "null argument");

@@ -451,3 +451,61 @@ def test_sender_order_is_irrelevant(model, tiny_net):
     r1 = oracle.Sim(model, net, 1).run(200)
     r2 = oracle.Sim(model, net2, 1).run(200)
     assert np.array_equal(r1[0], r2[0]) and np.array_equal(r1[1], r2[1])
+
+
+# ------------------------------------------------ compressed records and FP64 loop
+
+
+def test_int8_pair_quantizer_bounds(model, tiny_net):
+    """Per (source, target) population pair: the read-back weight is within half a step
+    of the true weight, every code fits int8, and the pair's extremes set base/step."""
+    q, base, step = oracle.quantize_i8(tiny_net)
+    pre, pp, qp = _pre_post_pops(tiny_net)
+    w = tiny_net.w_fx.astype(np.int64)
+    for a in range(8):
+        for b in range(8):
+            sel = (pp == a) & (qp == b)
+            if not sel.any():
+                assert base[a, b] == 0 and step[a, b] == 1
+                continue
+            lo, hi = w[sel].min(), w[sel].max()
+            assert base[a, b] == lo + (hi - lo) // 2
+            assert step[a, b] == max(1, -(-(hi - lo) // 254))
+            code = (q[sel].astype(np.int64) - base[a, b]) / step[a, b]
+            assert np.all(code == np.round(code)) and np.all(np.abs(code) <= 127)
+            assert np.all(np.abs(q[sel] - w[sel]) <= step[a, b] / 2 + 0.5)
+
+
+def test_bf16_quantizer_matches_torch():
+    """The bf16 read-back equals torch's float32 -> bfloat16 conversion (ties to even)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    w = np.concatenate([rng.integers(-6_000_000, 6_000_000, 20000), [0, 1, -1, 255, 256, 257, 4095, 2**24 - 1],
+                        [0x7F8080, 0x7F8180]]).astype(np.int32)
+    got = oracle.quantize_bf16(w)
+    f = torch.from_numpy((w.astype(np.float32) / np.float32(4096.0)))
+    ref = (f.to(torch.bfloat16).to(torch.float32) * 4096.0).numpy().astype(np.int64)
+    assert np.array_equal(got.astype(np.int64), ref)
+    nz = w != 0
+    assert np.all(np.abs(got[nz] - w[nz]) / np.abs(w[nz]) <= 2.0**-8 + 1e-12)
+
+
+def test_fp64_loop_psc_and_psp():
+    """FP64 loop: one spike of weight w arrives after its delay as exactly w * 2^-12 pA,
+    and the target's potential then follows the exact PSP gamma I (p22^n - p11^n) to
+    FP64 rounding."""
+    m = workload.microcircuit_model().replace(k_ext=[0.0] * 8)
+    c = oracle.constants(m)
+    w = 359_664
+    net = oracle.network_from_edges(2, pre=[0], post=[1], w_fx=[w], delay=[3], u0=[20.0, 0.0])
+    sim = oracle.Sim(m, net, seed=1, fp64=True)
+    sim.run(3)
+    assert sim.I[1] == 0.0
+    sim.run(1)
+    assert sim.I[1] == w / 4096.0
+    U = []
+    for _ in range(60):
+        sim.run(1)
+        U.append(sim.U[1])
+    k = np.arange(1, 61)
+    np.testing.assert_allclose(U, c["gamma"] * (w / 4096.0) * (c["p22"] ** k - c["p11"] ** k), rtol=1e-12)

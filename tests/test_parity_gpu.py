@@ -430,3 +430,45 @@ def test_barrier_wait_is_bounded_and_reported(model, monkeypatch):
     o = oracle.Sim(model, onet, 1).run(50)
     assert np.array_equal(g[0], o[0]) and np.array_equal(g[1], o[1])
     net.close()
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_checkpoint_resume_is_bit_exact(model, tiny, engine):
+    """2,000 steps straight equal 1,000 steps, save, restore into a fresh handle, 1,000
+    more steps (counter-based random numbers make the resumed run identical)."""
+    wl, onet = tiny
+    a = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, steps_per_graph=128, engine=engine)
+    a.step(2000)
+    full_t, full_i = a.read_spikes()
+    U_a, I_a, R_a = _state(a)
+    b = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, steps_per_graph=128, engine=engine)
+    b.step(1000)
+    first = b.read_spikes()
+    blob = b.save_state()
+    b.close()
+    c = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, steps_per_graph=128, engine=engine)
+    c.load_state(blob)
+    assert c.info().t == 1000
+    c.step(1000)
+    second = c.read_spikes()
+    assert np.array_equal(np.concatenate([first[0], second[0]]), full_t)
+    assert np.array_equal(np.concatenate([first[1], second[1]]), full_i)
+    U_c, I_c, R_c = _state(c)
+    assert np.array_equal(U_a.view(np.uint32), U_c.view(np.uint32))
+    assert np.array_equal(I_a.view(np.uint32), I_c.view(np.uint32)) and np.array_equal(R_a, R_c)
+    o = oracle.Sim(model, onet, wl.seed).run(2000)
+    assert np.array_equal(o[0], full_t) and np.array_equal(o[1], full_i)
+    a.close()
+    c.close()
+
+
+def test_load_state_rejects_other_shapes(model):
+    a = snn.Network(model, 20, 20, seed=1)
+    blob = a.save_state()
+    b = snn.Network(model, 30, 20, seed=1)
+    with pytest.raises(snn.SnnError):
+        b.load_state(blob)
+    with pytest.raises(snn.SnnError):
+        a.load_state(b"not a state")
+    a.close()
+    b.close()
