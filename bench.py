@@ -364,6 +364,54 @@ def run_gpu(args):
                     "gbs": nbytes / (ms_avg * 1e-3) / 1e9, "frac": nbytes / (ms_avg * 1e-3) / 1e9 / peak,
                     "reductions_per_s": ev_avg / (ms_avg * 1e-3)})
 
+    net.close()
+
+    # compressed synapse records on the same workload: step time and saturating delivery
+    forms = {}
+    for fname, fmt in (("int8_pair", snn.RECORD_PACKED_I8), ("bf16", snn.RECORD_PACKED_BF16)):
+        if fname not in args.forms:
+            continue
+        fnet = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, seed, steps_per_graph=tps,
+                           raster_capacity=1 << 25, device=dev, engine=engine, record_format=fmt)
+        fnet.step(args.warmup * tps)
+        fnet.read_spikes()
+        fe0 = fnet.info().events_read
+        torch.cuda.synchronize(dev)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.form_steps):
+            fnet.step(tps)
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        fsecs = a0.elapsed_time(a1) * 1e-3
+        fnet.read_spikes()
+        fev = fnet.info().events_read - fe0
+        fsat = []
+        for nsp in args.saturating[-1:]:
+            ms_l = []
+            for r in range(args.saturating_reps + 2):
+                spk = torch.from_numpy(rng.integers(0, n, nsp).astype(np.int32)).to(dev)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(dev)
+                e0.record(stream)
+                fnet.deliver_spikes(spk, 0)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                if r >= 2:
+                    ms_l.append(e0.elapsed_time(e1))
+            fsat.append({"spikers": nsp, "ms": float(np.mean(ms_l)),
+                         "speedup_vs_plain": float([p_["ms"] for p_ in sat if p_["spikers"] == nsp][0] /
+                                                   np.mean(ms_l))})
+        finfo = fnet.info()
+        forms[fname] = {"bytes_per_synapse": finfo.bytes_per_synapse, "value": fev / fsecs,
+                        "unit": "synaptic events/s", "rtf": fsecs / (args.form_steps * tps * model.dt_ms * 1e-3),
+                        "steps": args.form_steps * tps, "delivery_saturating": fsat,
+                        "note": "raster bit-exact with the oracle on the read-back weights; statistics vs FP64 "
+                                "in tests/test_precision_accuracy.py"}
+        fnet.close()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu, _, _ = cpu_oracle_sample(model, wl, args.cpu_ticks)
@@ -394,6 +442,7 @@ def run_gpu(args):
         "gpu_launches": args.steps * {snn.ENGINE_PERSISTENT: 1, snn.ENGINE_PIPELINED: tps + 1,
                                       snn.ENGINE_GRAPH: 2 * tps + 1}[info.engine],
         "roofline": roofline, "kernels": kernels,
+        "compressed_records": forms,
         "delivery_saturating": {"kernel": "k_deliver_list", "bound": "hbm", "peak": peak, "unit": "GB/s",
                                 "traffic_20480": _recorded_traffic("k_deliver_list"),
                                 "note": "phase 2 alone over random senders of the same network "
@@ -406,7 +455,6 @@ def run_gpu(args):
         line["cpu_baseline"] = cpu
     if rank == 0:
         print(json.dumps(line), flush=True)
-    net.close()
     return 0
 
 
@@ -423,6 +471,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--saturating", type=int, nargs="*", default=[2048, 8192, 20480])
     ap.add_argument("--saturating-reps", type=int, default=5)
+    ap.add_argument("--forms", nargs="*", default=["int8_pair", "bf16"])
+    ap.add_argument("--form-steps", type=int, default=20)
     ap.add_argument("--engine", default="default", choices=["default", "graph", "persistent", "pipelined"])
     args = ap.parse_args()
     if args.warmup < 3:

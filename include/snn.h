@@ -123,6 +123,25 @@ typedef struct snn_custom_net {
 #define SNN_ENGINE_GRAPH 1
 #define SNN_ENGINE_PERSISTENT 2
 #define SNN_ENGINE_PIPELINED 3
+/*
+ * record_format: how synapses are stored on the device (§3.5 stores a target, a
+ * delay and an FP32 weight; §5.3 proposes fewer bits per weight):
+ *   SNN_RECORD_PLAIN9:      int32 target, int32 weight (2^-12 pA), uint8 delay: 9 bytes;
+ *   SNN_RECORD_PACKED_I8:   uint32 word (target:20 | delay:6 | target population:3 |
+ *                           padding flag:1) and an int8 code read back as
+ *                           base[a][b] + code * step[a][b] for source population a and
+ *                           target population b; per pair, lo/hi = the pair's extreme
+ *                           weights, base = lo + (hi - lo) div 2, step = max(1,
+ *                           ceil((hi - lo) / 254)), code = clamp(round((w - base) /
+ *                           step), -127, 127): 5 bytes;
+ *   SNN_RECORD_PACKED_BF16: the same word and the current in pA as bfloat16 (round to
+ *                           nearest even): 6 bytes.
+ * Packed formats hold up to 2^20 neurons.  The dynamics are the plain ones applied to
+ * the read-back weights; accumulation stays int32.
+ */
+#define SNN_RECORD_PLAIN9 0
+#define SNN_RECORD_PACKED_I8 1
+#define SNN_RECORD_PACKED_BF16 2
 typedef struct snn_spec {
     uint32_t abi_version; /* must be SNN_ABI_VERSION */
     int32_t scale_n_permille;
@@ -133,7 +152,7 @@ typedef struct snn_spec {
     int32_t deliver_blocks;
     int32_t n_threads;
     int32_t engine;
-    int32_t reserved;
+    int32_t record_format;
     snn_model model;
     const snn_custom_net *custom;
 } snn_spec;
@@ -154,8 +173,10 @@ typedef struct snn_sizes {
  * engine alternates between two buffers).  Layouts:
  * U, I float[n_neurons_padded]; R uint8[n_neurons_padded] (refractory steps left);
  * ring int32[64][n_neurons_padded]; row_ptr int64[n_neurons+1] into the padded
- * synapse arrays; syn_tgt, syn_w int32[n_synapses_padded], syn_delay uint8[...]
- * (rows sorted by delay, each padded to a multiple of 4 with zero-weight entries);
+ * synapse arrays (rows sorted by delay, each padded to a multiple of 4 with entries
+ * that deliver nothing); plain records: syn_tgt, syn_w int32[n_synapses_padded],
+ * syn_delay uint8[...]; packed records: syn_tgt holds the uint32 words, syn_w the
+ * int8 codes or bfloat16 currents, syn_delay is unused;
  * rast_neuron, rast_step int32[raster_capacity]. */
 typedef struct snn_layout {
     uint64_t ctl, U, I, R, ring, row_ptr, syn_tgt, syn_w, syn_delay, rast_neuron, rast_step, params;
@@ -184,6 +205,10 @@ typedef struct snn_info {
     int32_t deliver_blocks;
     uint32_t device_error;         /* sticky device error bits (1 = raster overflow, 2 = barrier timeout) */
     int32_t engine;                /* SNN_ENGINE_PIPELINED, SNN_ENGINE_GRAPH or SNN_ENGINE_PERSISTENT */
+    int32_t record_format;         /* SNN_RECORD_* */
+    int32_t bytes_per_synapse;     /* device bytes of one synapse record */
+    int32_t i8_base[SNN_MAX_POPS][SNN_MAX_POPS];  /* SNN_RECORD_PACKED_I8 read-back tables [source][target] */
+    int32_t i8_step[SNN_MAX_POPS][SNN_MAX_POPS];
 } snn_info;
 
 typedef struct snn_net snn_net;
@@ -302,7 +327,8 @@ void snn_destroy(snn_net *net);
  * calls whose work overlaps on the GPU (different streams, or different handles at
  * the same time) race and give wrong results: serialise them.
  * Errors: SNN_EINVAL for more than SNN_STATIC_MAX_NEURONS neurons, a missing or
- * misaligned buffer, a negative t; SNN_ECUDA on a failed CUDA call.
+ * misaligned buffer, a negative t; SNN_ENOTSUP for a network with packed synapse
+ * records (this step reads plain records); SNN_ECUDA on a failed CUDA call.
  */
 #define SNN_STATIC_MAX_NEURONS 131072
 typedef struct snn_static_io {

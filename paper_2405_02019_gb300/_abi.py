@@ -12,6 +12,7 @@ FX_SHIFT = 12
 POISSON_KMAX = 24
 ABI_VERSION = 1
 ENGINE_DEFAULT, ENGINE_GRAPH, ENGINE_PERSISTENT, ENGINE_PIPELINED = 0, 1, 2, 3
+RECORD_PLAIN9, RECORD_PACKED_I8, RECORD_PACKED_BF16 = 0, 1, 2
 
 STATUS = {0: "SNN_OK", 1: "SNN_EINVAL", 2: "SNN_ENOMEM", 3: "SNN_ECUDA", 4: "SNN_EOVERFLOW",
           5: "SNN_ETIMEOUT", 6: "SNN_ESTATE", 7: "SNN_ENOTSUP"}
@@ -50,7 +51,7 @@ class snn_spec(C.Structure):
         ("abi_version", C.c_uint32), ("scale_n_permille", C.c_int32), ("scale_k_permille", C.c_int32),
         ("steps_per_graph", C.c_int32), ("seed", C.c_uint64), ("raster_capacity", C.c_int64),
         ("deliver_blocks", C.c_int32), ("n_threads", C.c_int32),
-        ("engine", C.c_int32), ("reserved", C.c_int32),
+        ("engine", C.c_int32), ("record_format", C.c_int32),
         ("model", snn_model),
         ("custom", C.POINTER(snn_custom_net)),
     ]
@@ -83,6 +84,8 @@ class snn_info(C.Structure):
         ("max_row_length", C.c_int32), ("chunks_per_row", C.c_int32),
         ("steps_per_graph", C.c_int32), ("deliver_blocks", C.c_int32),
         ("device_error", C.c_uint32), ("engine", C.c_int32),
+        ("record_format", C.c_int32), ("bytes_per_synapse", C.c_int32),
+        ("i8_base", (C.c_int32 * MAX_POPS) * MAX_POPS), ("i8_step", (C.c_int32 * MAX_POPS) * MAX_POPS),
     ]
 
 

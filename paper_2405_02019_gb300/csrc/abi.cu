@@ -49,6 +49,9 @@ struct snn_net {
     int32_t max_row = 0, chunks_per_row = 1;
     std::vector<int64_t> pop_off;
     std::vector<int32_t> out_degree;
+    int format = SNN_RECORD_PLAIN9;
+    int32_t i8_base[SNN_MAX_POPS][SNN_MAX_POPS] = {};
+    int32_t i8_step[SNN_MAX_POPS][SNN_MAX_POPS] = {};
     uint8_t *arena = nullptr;
     int device = 0;
     int num_sms = 0;
@@ -273,6 +276,9 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         net->chunks_per_row = std::max(1, (hn.max_row + snn::kChunk - 1) / snn::kChunk);
         net->pop_off = hn.pop_off;
         net->out_degree = std::move(hn.out_degree);
+        net->format = hn.format;
+        std::memcpy(net->i8_base, hn.i8_base, sizeof(net->i8_base));
+        std::memcpy(net->i8_step, hn.i8_step, sizeof(net->i8_step));
 
         int rc = SNN_OK;
         auto cuda_ok = [&](cudaError_t e, const char *what) {
@@ -287,6 +293,8 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         std::memcpy(tabs.thresholds, net->c.thresholds, sizeof(tabs.thresholds));
         for (int b = 0; b <= SNN_MAX_POPS; ++b) tabs.pop_off[b] = b < (int)hn.pop_off.size() ? hn.pop_off[b] : hn.n;
         tabs.n_pops = spec->model.n_pops;
+        for (int sa = 0; sa < SNN_MAX_POPS; ++sa)
+            for (int tb = 0; tb < SNN_MAX_POPS; ++tb) tabs.i8_pair[sa][tb] = {hn.i8_base[sa][tb], hn.i8_step[sa][tb]};
         std::vector<float> u0(net->npad, 0.0f);
         std::copy(hn.u0.begin(), hn.u0.end(), u0.begin());
         cuda_ok(cudaMemsetAsync(A + L.ctl, 0, sizeof(snn::Ctl), st), "memset ctl");
@@ -297,11 +305,16 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         cuda_ok(cudaMemsetAsync(A + L.ring, 0, uint64_t{4} * snn::kDMax * net->npad, st), "ring");
         cuda_ok(cudaMemcpyAsync(A + L.row_ptr, hn.row_ptr.data(), 8 * (net->n + 1), cudaMemcpyHostToDevice, st),
                 "row_ptr");
-        if (net->n_syn_padded > 0) {
+        if (net->n_syn_padded > 0 && hn.format == SNN_RECORD_PLAIN9) {
             cuda_ok(cudaMemcpyAsync(A + L.syn_tgt, hn.tgt.data(), 4 * net->n_syn_padded, cudaMemcpyHostToDevice, st),
                     "tgt");
             cuda_ok(cudaMemcpyAsync(A + L.syn_w, hn.w.data(), 4 * net->n_syn_padded, cudaMemcpyHostToDevice, st), "w");
             cuda_ok(cudaMemcpyAsync(A + L.syn_d, hn.d.data(), net->n_syn_padded, cudaMemcpyHostToDevice, st), "d");
+        } else if (net->n_syn_padded > 0) {
+            cuda_ok(cudaMemcpyAsync(A + L.syn_tgt, hn.word.data(), 4 * net->n_syn_padded, cudaMemcpyHostToDevice, st),
+                    "words");
+            cuda_ok(cudaMemcpyAsync(A + L.syn_w, hn.wbytes.data(), hn.wbytes.size(), cudaMemcpyHostToDevice, st),
+                    "weights");
         }
         cuda_ok(cudaStreamSynchronize(st), "upload sync");
         if (rc != SNN_OK) {
@@ -327,6 +340,7 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         a.seed = spec->seed;
         a.rast_cap = static_cast<uint32_t>(L.rast_cap);
         a.chunks_per_row = net->chunks_per_row;
+        a.format = net->format;
         a.p11 = net->c.p11f;
         a.p21 = net->c.p21f;
         a.p22 = net->c.p22f;
@@ -583,6 +597,10 @@ int snn_get_info(const snn_net *net, snn_info *out)
     out->deliver_blocks = net->deliver_grid;
     out->device_error = net->device_error;
     out->engine = net->engine;
+    out->record_format = net->format;
+    out->bytes_per_synapse = snn::record_bytes(net->format);
+    std::memcpy(out->i8_base, net->i8_base, sizeof(out->i8_base));
+    std::memcpy(out->i8_step, net->i8_step, sizeof(out->i8_step));
     return SNN_OK;
 }
 

@@ -177,6 +177,10 @@ bool validate_spec(const snn_spec &spec, std::string &why)
     if (spec.steps_per_graph < 0 || spec.steps_per_graph > 100000) return fail("steps_per_graph out of [0, 100000]");
     if (spec.deliver_blocks < 0 || spec.deliver_blocks > 65535) return fail("deliver_blocks out of range");
     if (spec.engine < SNN_ENGINE_DEFAULT || spec.engine > SNN_ENGINE_PIPELINED) return fail("unknown engine");
+    if (spec.record_format < SNN_RECORD_PLAIN9 || spec.record_format > SNN_RECORD_PACKED_BF16)
+        return fail("unknown record_format");
+    if (spec.record_format != SNN_RECORD_PLAIN9 && count_neurons(spec) > kPackedMaxNeurons)
+        return fail("packed records hold at most 2^20 neurons");
     if (spec.custom) {
         const snn_custom_net &c = *spec.custom;
         if (c.n_neurons < 1 || c.n_neurons > (int64_t{1} << 30)) return fail("custom n_neurons out of [1, 2^30]");
@@ -226,9 +230,11 @@ Layout make_layout(const snn_spec &spec)
     L.R = o; o = up(o + L.npad);
     L.ring = o; o = up(o + uint64_t{4} * kDMax * L.npad);
     L.row_ptr = o; o = up(o + 8 * (n + 5));  // 4 spare entries: quads read row_ptr[i0 .. i0+4]
+    const int fmt = spec.record_format;
+    const uint64_t wbytes = fmt == SNN_RECORD_PACKED_I8 ? 1 : fmt == SNN_RECORD_PACKED_BF16 ? 2 : 4;
     L.syn_tgt = o; o = up(o + 4 * L.syn_padded_max);
-    L.syn_w = o; o = up(o + 4 * L.syn_padded_max);
-    L.syn_d = o; o = up(o + L.syn_padded_max + 16);
+    L.syn_w = o; o = up(o + wbytes * L.syn_padded_max + 16);
+    L.syn_d = o; o = up(o + (fmt == SNN_RECORD_PLAIN9 ? L.syn_padded_max : 0) + 16);
     L.rast_nrn = o; o = up(o + 4 * L.rast_cap);
     L.rast_t = o; o = up(o + 4 * L.rast_cap);
     L.U2 = o; o = up(o + 4 * L.npad);
@@ -304,6 +310,95 @@ void sample_edges(const snn_spec &spec, const Constants &c, EdgeList &e, int nth
             e.d[s] = static_cast<uint8_t>(steps);
         }
     });
+}
+
+inline int pop_index(const std::vector<int64_t> &off, int n_pops, int64_t i)
+{
+    int b = 0;
+    while (b + 1 < n_pops && i >= off[b + 1]) ++b;
+    return b;
+}
+
+uint16_t to_bf16_even(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return static_cast<uint16_t>(u >> 16);
+}
+
+// Compressed records (§5.3): packed words, and int8 codes fitted per population pair or
+// bfloat16 currents; the plain arrays are released afterwards.
+void pack_records(HostNetwork &net, int n_pops, int nthreads)
+{
+    const int64_t n = net.n;
+    const int64_t S = net.n_syn_padded;
+    net.word.assign(S, 0);
+    std::vector<uint8_t> tpop(S, 0);
+    // extremes of each (source, target) pair, per thread then merged
+    const int T = std::max(1, nthreads);
+    std::vector<std::vector<int64_t>> lo(T, std::vector<int64_t>(64, INT64_MAX)), hi(T, std::vector<int64_t>(64, INT64_MIN));
+    parallel_for(T, n, [&](int th, int64_t r0, int64_t r1) {
+        for (int64_t i = r0; i < r1; ++i) {
+            const int a = pop_index(net.pop_off, n_pops, i);
+            const int64_t real_end = net.row_ptr[i] + net.out_degree[i];
+            for (int64_t s = net.row_ptr[i]; s < net.row_ptr[i + 1]; ++s) {
+                const int b = pop_index(net.pop_off, n_pops, net.tgt[s]);
+                tpop[s] = static_cast<uint8_t>(b);
+                uint32_t w = static_cast<uint32_t>(net.tgt[s]) | (static_cast<uint32_t>(net.d[s]) << kWordDelayShift) |
+                             (static_cast<uint32_t>(b) << kWordPopShift);
+                if (s >= real_end) {
+                    w |= kWordPad;
+                } else {
+                    lo[th][a * 8 + b] = std::min<int64_t>(lo[th][a * 8 + b], net.w[s]);
+                    hi[th][a * 8 + b] = std::max<int64_t>(hi[th][a * 8 + b], net.w[s]);
+                }
+                net.word[s] = w;
+            }
+        }
+    });
+    for (int a = 0; a < SNN_MAX_POPS; ++a)
+        for (int b = 0; b < SNN_MAX_POPS; ++b) {
+            int64_t l = INT64_MAX, h = INT64_MIN;
+            for (int th = 0; th < T; ++th) {
+                l = std::min(l, lo[th][a * 8 + b]);
+                h = std::max(h, hi[th][a * 8 + b]);
+            }
+            int64_t base = 0, step = 1;
+            if (l <= h) {
+                base = l + (h - l) / 2;
+                step = std::max<int64_t>(1, (h - l + 253) / 254);
+            }
+            net.i8_base[a][b] = static_cast<int32_t>(base);
+            net.i8_step[a][b] = static_cast<int32_t>(step);
+        }
+    if (net.format == SNN_RECORD_PACKED_I8) {
+        net.wbytes.assign(S, 0);
+        parallel_for(T, n, [&](int, int64_t r0, int64_t r1) {
+            for (int64_t i = r0; i < r1; ++i) {
+                const int a = pop_index(net.pop_off, n_pops, i);
+                const int64_t real_end = net.row_ptr[i] + net.out_degree[i];
+                for (int64_t s = net.row_ptr[i]; s < real_end; ++s) {
+                    const int b = tpop[s];
+                    const int64_t base = net.i8_base[a][b], step = net.i8_step[a][b];
+                    long long q = std::llround(static_cast<double>(net.w[s] - base) / static_cast<double>(step));
+                    q = std::min<long long>(127, std::max<long long>(-127, q));
+                    net.wbytes[s] = static_cast<uint8_t>(static_cast<int8_t>(q));
+                }
+            }
+        });
+    } else {
+        net.wbytes.assign(2 * S, 0);
+        parallel_for(T, S, [&](int, int64_t s0, int64_t s1) {
+            for (int64_t s = s0; s < s1; ++s) {
+                const uint16_t h = to_bf16_even(static_cast<float>(net.w[s]) * (1.0f / 4096.0f));
+                std::memcpy(&net.wbytes[2 * s], &h, 2);
+            }
+        });
+    }
+    std::vector<int32_t>().swap(net.tgt);
+    std::vector<int32_t>().swap(net.w);
+    std::vector<uint8_t>().swap(net.d);
 }
 
 }  // namespace
@@ -439,6 +534,8 @@ bool build_host_network(const snn_spec &spec, const Constants &c, HostNetwork &n
             }
         }
     });
+    net.format = spec.record_format;
+    if (net.format != SNN_RECORD_PLAIN9) pack_records(net, spec.model.n_pops, nthreads);
     return true;
 }
 

@@ -17,7 +17,7 @@ constexpr int kRowAlign = 4;                 // synapse rows padded to whole int
 constexpr int kChunk = 256;                  // synapses per delivery work item (32 lanes x 2 quads)
 constexpr int kUpdateThreads = 128;          // 4 neurons per thread
 constexpr int kDeliverThreads = 256;
-constexpr int kPersistThreads = 1024;        // one CTA per SM in the persistent engine
+constexpr int kPersistThreads = 512;         // one CTA per SM in the persistent engine
 constexpr int kStepDeliverWarps = 8;         // delivery warps per CTA of the pipelined step kernel
 constexpr int kStepMaxThreads = 384;            // neuron warps (<= 4) + delivery warps per CTA
 constexpr int kStepMaxNeuronWarps = 4;
@@ -47,13 +47,29 @@ struct alignas(16) QueueEntry {
     int32_t step;        // low 32 bits of the step index (tells fresh entries from stale ones)
 };
 
-// Tables the update kernel stages in shared memory (in the arena, read-only).
+// int8 read-back of one (source, target) population pair: w = base + code * step.
+struct alignas(8) PairQ {
+    int32_t base;
+    int32_t step;
+};
+
+// Read-only tables in the arena.
 struct alignas(16) StaticTables {
     uint64_t thresholds[SNN_MAX_POPS][kPK];  // 63-bit Poisson CDF thresholds
     int64_t pop_off[SNN_MAX_POPS + 1];
     int32_t n_pops;
     int32_t pad;
+    PairQ i8_pair[SNN_MAX_POPS][SNN_MAX_POPS];  // packed int8 records: read-back per [source][target]
 };
+
+// Packed synapse word: target (20 bits), delay (6), target population (3), padding flag.
+constexpr int kWordTargetBits = 20;
+constexpr uint32_t kWordTargetMask = (1u << kWordTargetBits) - 1;
+constexpr int kWordDelayShift = 20;
+constexpr int kWordPopShift = 26;
+constexpr uint32_t kWordPad = 1u << 31;
+constexpr int64_t kPackedMaxNeurons = int64_t{1} << kWordTargetBits;
+inline int record_bytes(int format) { return format == SNN_RECORD_PACKED_I8 ? 5 : format == SNN_RECORD_PACKED_BF16 ? 6 : 9; }
 
 // Kernel arguments (by value; small).
 struct StepArgs {
@@ -87,6 +103,8 @@ struct StepArgs {
     int32_t n_pops;
     int32_t quad_warps;           // pipelined engine: groups of 128 neurons (one queue region each)
     uint32_t *qcount;             // pipelined engine: spikes per group, [4][quad_warps]
+    int32_t format;               // SNN_RECORD_*
+    int32_t pad2;
 };
 
 // Host constants of one model (§2.2).
@@ -100,6 +118,11 @@ struct Constants {
 
 // Network in host memory, in the device layout.
 struct HostNetwork {
+    int format = SNN_RECORD_PLAIN9;
+    std::vector<uint32_t> word;    // packed records: words
+    std::vector<uint8_t> wbytes;   // packed records: int8 codes or bfloat16 currents
+    int32_t i8_base[SNN_MAX_POPS][SNN_MAX_POPS] = {};
+    int32_t i8_step[SNN_MAX_POPS][SNN_MAX_POPS] = {};
     int64_t n = 0;
     int64_t npad = 0;
     int64_t n_syn = 0;         // true synapses

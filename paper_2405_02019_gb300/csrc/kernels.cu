@@ -173,15 +173,85 @@ __device__ __forceinline__ void append_spikes(const StepArgs &a, int64_t t, int6
     }
 }
 
-// Phase 2 for the spikers list[0 .. nspk), work items grid-strided over warps:
-// item = (spiker, 256-synapse chunk of its row).
-__device__ __forceinline__ void deliver_list(const StepArgs &a, int64_t t, const int32_t *list, int64_t nspk,
-                                             int64_t warp, int64_t nwarps)
+// Population of neuron i from the offsets in the launch arguments.
+__device__ __forceinline__ int pop_of(const StepArgs &a, int64_t i)
 {
-    const int64_t items = nspk * a.chunks_per_row;
+    int b = 0;
+    while (b + 1 < a.n_pops && i >= a.pop_off[b + 1]) ++b;
+    return b;
+}
+
+// One 256-synapse chunk [off, min(off + 256, re)) of a row whose sender belongs to
+// population src_pop: each lane takes two quads, loads them with 16-byte streaming
+// loads and adds every weight into W[(slot + d) mod 64][target].  FMT selects the
+// record format; the padding entries of a row deliver nothing.
+template <int FMT>
+__device__ __forceinline__ void deliver_chunk(const StepArgs &a, int64_t slot, int64_t off, int64_t re, int src_pop)
+{
     const int lane = threadIdx.x & 31;
     int32_t *const ring = a.ring;
     const int64_t npad = a.npad;
+    int4 tg[2];
+    int4 wv[2];
+    uint32_t dv[2];
+    uint2 hv[2];
+    bool ok[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int64_t o = off + u * 128 + lane * 4;
+        ok[u] = o < re;
+        if (ok[u]) {
+            tg[u] = ld_stream4(a.syn_tgt + o);
+            if (FMT == SNN_RECORD_PLAIN9) {
+                wv[u] = ld_stream4(a.syn_w + o);
+                dv[u] = ld_stream_u32(a.syn_d + o);
+            } else if (FMT == SNN_RECORD_PACKED_I8) {
+                dv[u] = ld_stream_u32(reinterpret_cast<const uint8_t *>(a.syn_w) + o);
+            } else {
+                hv[u] = __ldcs(reinterpret_cast<const uint2 *>(reinterpret_cast<const uint16_t *>(a.syn_w) + o));
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        if (!ok[u]) continue;
+        const int32_t tt[4] = {tg[u].x, tg[u].y, tg[u].z, tg[u].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            int32_t w, target;
+            int64_t d;
+            if (FMT == SNN_RECORD_PLAIN9) {
+                const int32_t wq[4] = {wv[u].x, wv[u].y, wv[u].z, wv[u].w};
+                w = wq[e];
+                target = tt[e];
+                d = (dv[u] >> (8 * e)) & 0xFFu;
+            } else {
+                const uint32_t word = static_cast<uint32_t>(tt[e]);
+                if (word & kWordPad) continue;
+                target = static_cast<int32_t>(word & kWordTargetMask);
+                d = (word >> kWordDelayShift) & 63u;
+                const int b = static_cast<int>((word >> kWordPopShift) & 7u);
+                if (FMT == SNN_RECORD_PACKED_I8) {
+                    const int2 pq = __ldg(reinterpret_cast<const int2 *>(&a.tables->i8_pair[src_pop][b]));
+                    const int32_t code = static_cast<int8_t>((dv[u] >> (8 * e)) & 0xFFu);
+                    w = pq.x + code * pq.y;
+                } else {
+                    const uint32_t h = e < 2 ? (hv[u].x >> (16 * e)) : (hv[u].y >> (16 * (e - 2)));
+                    w = __float2int_rn(__fmul_rn(__uint_as_float((h & 0xFFFFu) << 16), 4096.0f));
+                }
+            }
+            if (w != 0) red_add_s32(ring + ((slot + d) & kDMask) * npad + target, w);
+        }
+    }
+}
+
+// Phase 2 for the spikers list[0 .. nspk), work items grid-strided over warps:
+// item = (spiker, 256-synapse chunk of its row).
+template <int FMT>
+__device__ __forceinline__ void deliver_list_fmt(const StepArgs &a, int64_t t, const int32_t *list, int64_t nspk,
+                                                 int64_t warp, int64_t nwarps)
+{
+    const int64_t items = nspk * a.chunks_per_row;
     for (int64_t it = warp; it < items; it += nwarps) {
         const int64_t j = it / a.chunks_per_row;
         const int64_t c = it - j * a.chunks_per_row;
@@ -190,31 +260,16 @@ __device__ __forceinline__ void deliver_list(const StepArgs &a, int64_t t, const
         const int64_t re = a.row_ptr[s + 1];
         const int64_t off = rs + c * kChunk;
         if (off >= re) continue;
-        int4 tg[2], wv[2];
-        uint32_t dv[2];
-        bool ok[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int64_t o = off + u * 128 + lane * 4;
-            ok[u] = o < re;
-            if (ok[u]) {
-                tg[u] = ld_stream4(a.syn_tgt + o);
-                wv[u] = ld_stream4(a.syn_w + o);
-                dv[u] = ld_stream_u32(a.syn_d + o);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            if (!ok[u]) continue;
-            const int32_t tt[4] = {tg[u].x, tg[u].y, tg[u].z, tg[u].w};
-            const int32_t wq[4] = {wv[u].x, wv[u].y, wv[u].z, wv[u].w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int64_t d = (dv[u] >> (8 * e)) & 0xFFu;
-                if (wq[e] != 0) red_add_s32(ring + ((t + d) & kDMask) * npad + tt[e], wq[e]);
-            }
-        }
+        deliver_chunk<FMT>(a, t, off, re, FMT == SNN_RECORD_PACKED_I8 ? pop_of(a, s) : 0);
     }
+}
+
+__device__ __forceinline__ void deliver_list(const StepArgs &a, int64_t t, const int32_t *list, int64_t nspk,
+                                             int64_t warp, int64_t nwarps)
+{
+    if (a.format == SNN_RECORD_PACKED_I8) deliver_list_fmt<SNN_RECORD_PACKED_I8>(a, t, list, nspk, warp, nwarps);
+    else if (a.format == SNN_RECORD_PACKED_BF16) deliver_list_fmt<SNN_RECORD_PACKED_BF16>(a, t, list, nspk, warp, nwarps);
+    else deliver_list_fmt<SNN_RECORD_PLAIN9>(a, t, list, nspk, warp, nwarps);
 }
 
 __global__ void __launch_bounds__(kUpdateThreads) k_update(const StepArgs a, const int k)
@@ -346,14 +401,6 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_persistent(const StepArg
 __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
 {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-// Population of neuron i from the offsets in the launch arguments.
-__device__ __forceinline__ int pop_of(const StepArgs &a, int64_t i)
-{
-    int b = 0;
-    while (b + 1 < a.n_pops && i >= a.pop_off[b + 1]) ++b;
-    return b;
 }
 
 // Poisson count T = #{k : v >= thr[k]} (thresholds nondecreasing): the first eight
@@ -492,9 +539,15 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, i
         const int64_t re = rp[j + 1];
         if (re > rs) {
             prefetch_l2(a.syn_tgt + rs, static_cast<uint32_t>(4 * (re - rs)));
-            prefetch_l2(a.syn_w + rs, static_cast<uint32_t>(4 * (re - rs)));
-            const int64_t d0 = rs & ~int64_t{15}, d1 = (re + 15) & ~int64_t{15};
-            prefetch_l2(a.syn_d + d0, static_cast<uint32_t>(d1 - d0));
+            if (a.format == SNN_RECORD_PLAIN9) {
+                prefetch_l2(a.syn_w + rs, static_cast<uint32_t>(4 * (re - rs)));
+                const int64_t d0 = rs & ~int64_t{15}, d1 = (re + 15) & ~int64_t{15};
+                prefetch_l2(a.syn_d + d0, static_cast<uint32_t>(d1 - d0));
+            } else {
+                const int64_t bp = a.format == SNN_RECORD_PACKED_I8 ? 1 : 2;
+                const int64_t w0 = (rs * bp) & ~int64_t{15}, w1 = (re * bp + 15) & ~int64_t{15};
+                prefetch_l2(reinterpret_cast<const uint8_t *>(a.syn_w) + w0, static_cast<uint32_t>(w1 - w0));
+            }
         }
         QueueEntry e;
         e.row_quad = static_cast<uint32_t>(rs >> 2);
@@ -509,23 +562,14 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, i
 // D(t), run by the delivery warps: grid-stride over (spike, 256-synapse chunk) items
 // of queue t mod 4.  The count, the raster base and the first item's entry are loaded
 // in one round trip.  The warp taking chunk 0 of spike j records it in the raster.
-__device__ __forceinline__ void pipe_deliver(const StepArgs &a, const int64_t &t, int ph, bool leader, int64_t dw,
-                                             int64_t ndw, bool wait_first)
+template <int FMT>
+__device__ __forceinline__ void pipe_deliver_fmt(const StepArgs &a, const int64_t &t, int ph, int64_t dw, int64_t ndw,
+                                                 uint32_t n, uint32_t rbase)
 {
     const int lane = threadIdx.x & 31;
     const QueueEntry *qbuf = a.queue + (ph & 3) * a.npad;
     const int64_t cpr = a.chunks_per_row;
-    int32_t *const ring = a.ring;
     const int64_t npad = a.npad;
-    if (wait_first) wait_previous_grid();
-    const uint32_t n = __ldcg(&a.ctl->qcnt[ph & 3]);
-    const uint32_t rbase = __ldcg(&a.ctl->step_begin[t & 1]);
-    if (leader) {
-        a.ctl->step_begin[(t + 1) & 1] = rbase + n;
-        a.ctl->cursor = rbase + n;
-        a.ctl->qcnt[(ph + 2) & 3] = 0;  // the queue the next kernel fills after this one
-        if (static_cast<uint64_t>(rbase) + n > a.rast_cap) atomicOr(&a.ctl->err, kErrRaster);
-    }
     for (int64_t it = dw;; it += ndw) {
         const int64_t j = it / cpr;
         if (j >= npad) break;
@@ -543,31 +587,25 @@ __device__ __forceinline__ void pipe_deliver(const StepArgs &a, const int64_t &t
         const int64_t re = rs + static_cast<int64_t>(static_cast<uint32_t>(raw.y)) * 4;
         const int64_t off = rs + c * kChunk;
         if (off >= re) continue;
-        int4 tg[2], wv[2];
-        uint32_t dv[2];
-        bool ok[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int64_t o = off + u * 128 + lane * 4;
-            ok[u] = o < re;
-            if (ok[u]) {
-                tg[u] = ld_stream4(a.syn_tgt + o);
-                wv[u] = ld_stream4(a.syn_w + o);
-                dv[u] = ld_stream_u32(a.syn_d + o);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            if (!ok[u]) continue;
-            const int32_t tt[4] = {tg[u].x, tg[u].y, tg[u].z, tg[u].w};
-            const int32_t wq[4] = {wv[u].x, wv[u].y, wv[u].z, wv[u].w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int64_t d = (dv[u] >> (8 * e)) & 0xFFu;
-                if (wq[e] != 0) red_add_s32(ring + ((ph + d) & kDMask) * npad + tt[e], wq[e]);
-            }
-        }
+        deliver_chunk<FMT>(a, ph, off, re, FMT == SNN_RECORD_PACKED_I8 ? pop_of(a, raw.z) : 0);
     }
+}
+
+__device__ __forceinline__ void pipe_deliver(const StepArgs &a, const int64_t &t, int ph, bool leader, int64_t dw,
+                                             int64_t ndw, bool wait_first)
+{
+    if (wait_first) wait_previous_grid();
+    const uint32_t n = __ldcg(&a.ctl->qcnt[ph & 3]);
+    const uint32_t rbase = __ldcg(&a.ctl->step_begin[t & 1]);
+    if (leader) {
+        a.ctl->step_begin[(t + 1) & 1] = rbase + n;
+        a.ctl->cursor = rbase + n;
+        a.ctl->qcnt[(ph + 2) & 3] = 0;  // the queue the next kernel fills after this one
+        if (static_cast<uint64_t>(rbase) + n > a.rast_cap) atomicOr(&a.ctl->err, kErrRaster);
+    }
+    if (a.format == SNN_RECORD_PACKED_I8) pipe_deliver_fmt<SNN_RECORD_PACKED_I8>(a, t, ph, dw, ndw, n, rbase);
+    else if (a.format == SNN_RECORD_PACKED_BF16) pipe_deliver_fmt<SNN_RECORD_PACKED_BF16>(a, t, ph, dw, ndw, n, rbase);
+    else pipe_deliver_fmt<SNN_RECORD_PLAIN9>(a, t, ph, dw, ndw, n, rbase);
 }
 
 // t_base is read before waiting on the previous kernel: within a graph replay it only

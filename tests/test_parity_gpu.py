@@ -472,3 +472,126 @@ def test_load_state_rejects_other_shapes(model):
         a.load_state(b"not a state")
     a.close()
     b.close()
+
+
+# ------------------------------------------------------- compressed synapse records
+
+FORMATS = [snn.RECORD_PACKED_I8, snn.RECORD_PACKED_BF16]
+
+
+def _oracle_weights(onet, fmt):
+    if fmt == snn.RECORD_PACKED_I8:
+        return oracle.quantize_i8(onet)[0]
+    return oracle.quantize_bf16(onet.w_fx)
+
+
+def _decode_device_records(net, fmt):
+    """(row_ptr, target, delay, target population, pad flag, read-back weight) from the
+    device arena, decoded in numpy from the format's definition."""
+    lay = net.layout()
+    n = net.n_neurons
+    sp = int(lay.n_synapses_padded)
+    rp = net.device_view("row_ptr", torch.int64, n + 1).cpu().numpy()
+    word = net.device_view("syn_tgt", torch.int32, sp).cpu().numpy().view(np.uint32)
+    tgt = (word & 0xFFFFF).astype(np.int32)
+    d = ((word >> 20) & 63).astype(np.uint8)
+    pop = ((word >> 26) & 7).astype(np.int64)
+    pad = (word >> 31).astype(bool)
+    info = net.info()
+    if fmt == snn.RECORD_PACKED_I8:
+        code = net.device_view("syn_w", torch.int8, sp).cpu().numpy().astype(np.int64)
+        base = np.ctypeslib.as_array(info.i8_base).astype(np.int64)
+        step = np.ctypeslib.as_array(info.i8_step).astype(np.int64)
+        src = np.repeat(np.searchsorted(np.ctypeslib.as_array(info.pop_offsets)[1:8], np.arange(n), side="right"),
+                        np.diff(rp))
+        w = base[src, pop] + code * step[src, pop]
+    else:
+        h = net.device_view("syn_w", torch.int16, sp).cpu().numpy().view(np.uint16).astype(np.uint32) << 16
+        w = (h.view(np.float32) * np.float32(4096.0)).astype(np.int64)
+    return rp, tgt, d, pop, pad, w
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_packed_records_decode_to_oracle_quantization(model, tiny, fmt):
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=fmt)
+    info = net.info()
+    assert info.record_format == fmt and info.bytes_per_synapse == (5 if fmt == snn.RECORD_PACKED_I8 else 6)
+    if fmt == snn.RECORD_PACKED_I8:
+        _, base, step = oracle.quantize_i8(onet)
+        assert np.array_equal(np.ctypeslib.as_array(info.i8_base), base)
+        assert np.array_equal(np.ctypeslib.as_array(info.i8_step), step)
+    rp, tgt, d, pop, pad, w = _decode_device_records(net, fmt)
+    lens = np.diff(onet.row_ptr)
+    plen = np.diff(rp)
+    pos = np.arange(rp[-1]) - np.repeat(rp[:-1], plen)
+    real = pos < np.repeat(lens, plen)
+    assert np.array_equal(pad[: rp[-1]], ~real)
+    assert np.array_equal(pop[: rp[-1]][real], np.searchsorted(onet.pop_off[1:8], tgt[: rp[-1]][real], side="right"))
+    qw = _oracle_weights(onet, fmt)
+    ow = oracle.with_weights(onet, qw)
+    _row_multisets_equal(ow, rp, tgt, np.where(real, w[: rp[-1]], 0).astype(np.int32), d)
+    net.close()
+
+
+@pytest.mark.parametrize("engine", [PIPE, GRAPH])
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_packed_raster_bit_exact_tiny(model, tiny, fmt, engine):
+    """The compressed forms are bit-exact against the oracle run on the same read-back
+    weights (integer dequantisation), which pins the kernels apart from the precision
+    loss."""
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=fmt,
+                      engine=engine, steps_per_graph=128)
+    net.step(wl.steps)
+    g_t, g_i = net.read_spikes()
+    sim = oracle.Sim(model, oracle.with_weights(onet, _oracle_weights(onet, fmt)), wl.seed)
+    o_t, o_i = sim.run(wl.steps)
+    assert np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
+    _assert_same_state(net, sim)
+    net.close()
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_packed_deliver_spikes_match(model, tiny, fmt):
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=fmt)
+    qw = _oracle_weights(onet, fmt)
+    spikers = np.random.default_rng(5).integers(0, onet.n, 300).astype(np.int32)
+    net.deliver_spikes(torch.from_numpy(spikers).cuda(), 9)
+    torch.cuda.synchronize()
+    npad = int(net.layout().n_neurons_padded)
+    ring = net.device_view("ring", torch.int32, 64 * npad).cpu().numpy().reshape(64, npad).astype(np.int64)
+    exp = np.zeros((64, npad), np.int64)
+    for s_ in spikers:
+        a, b = onet.row_ptr[s_], onet.row_ptr[s_ + 1]
+        np.add.at(exp, ((9 + onet.delay[a:b].astype(np.int64)) % 64, onet.post[a:b]), qw[a:b])
+    assert np.array_equal(ring, exp)
+    net.close()
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_packed_full_scale_parity(model, full, fmt):
+    """Full microcircuit with compressed records, default engine: raster and state
+    identical to the oracle on the read-back weights over 600 steps."""
+    wl, onet = full
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=fmt)
+    net.step(600)
+    g_t, g_i = net.read_spikes()
+    sim = oracle.Sim(model, oracle.with_weights(onet, _oracle_weights(onet, fmt)), wl.seed)
+    o_t, o_i = sim.run(600)
+    assert len(o_t) > 0
+    assert np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
+    _assert_same_state(net, sim)
+    net.close()
+
+
+def test_static_step_rejects_packed(model):
+    import ctypes as C
+    from paper_2405_02019_gb300 import _abi
+
+    net = snn.Network(model, 20, 20, seed=1, record_format=snn.RECORD_PACKED_I8)
+    io = _abi.snn_static_io()
+    rc = snn.load().snn_step_static(C.c_void_p(net._handle), C.byref(io), 1, 0, None)
+    assert rc == _abi.SNN_ENOTSUP
+    net.close()
