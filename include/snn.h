@@ -97,6 +97,15 @@ typedef struct snn_custom_net {
     int64_t pop_offsets[SNN_MAX_POPS + 1];
 } snn_custom_net;
 
+/* One circuit of a batch: its neuron and in-degree scales (permille) and its seed. */
+typedef struct snn_circuit {
+    int32_t scale_n_permille;
+    int32_t scale_k_permille;
+    uint64_t seed;
+} snn_circuit;
+
+#define SNN_MAX_CIRCUITS 4096
+
 /*
  * What to simulate.
  *   scale_n_permille / scale_k_permille: population sizes N_b = round_half_up(N_full_b *
@@ -107,6 +116,12 @@ typedef struct snn_custom_net {
  *   raster_capacity: spikes the device holds between reads (0 = 1<<24);
  *   deliver_blocks: CTAs of the delivery kernel (0 = 2 per SM);
  *   custom: NULL, or an explicit network (then the scales are ignored);
+ *   n_circuits / circuits: 0 and NULL for one circuit (scales and seed above); else a
+ *     batch of independent circuits of the same model, each with its own scales and
+ *     seed, simulated together.  Circuit c occupies neurons [base_c, base_c + N_c) of
+ *     one index space (base_c a multiple of 128; the neurons between circuits are
+ *     inert) and evolves exactly as it would alone: its synapses, initial state and
+ *     thalamic draws use its own seed and circuit-local neuron indices;
  *   n_threads: host threads for network construction (0 = all cores);
  *   engine: how the steps are scheduled; every engine gives the same raster and state:
  *     SNN_ENGINE_PIPELINED (the default): one kernel per step, replayed from a CUDA
@@ -155,6 +170,9 @@ typedef struct snn_spec {
     int32_t record_format;
     snn_model model;
     const snn_custom_net *custom;
+    int32_t n_circuits;
+    int32_t reserved;
+    const snn_circuit *circuits;
 } snn_spec;
 
 /* Sizes for a spec.  arena_bytes is the device arena snn_build_network needs
@@ -207,6 +225,10 @@ typedef struct snn_info {
     int32_t engine;                /* SNN_ENGINE_PIPELINED, SNN_ENGINE_GRAPH or SNN_ENGINE_PERSISTENT */
     int32_t record_format;         /* SNN_RECORD_* */
     int32_t bytes_per_synapse;     /* device bytes of one synapse record */
+    int32_t n_circuits;            /* 1, or the batch size */
+    int32_t schedule_ctas;         /* CTAs of the step (pipelined) or delivery (graph) kernel */
+    int32_t schedule_delivery_warps; /* pipelined engine: delivery warps per CTA */
+    int32_t reserved2;
     int32_t i8_base[SNN_MAX_POPS][SNN_MAX_POPS];  /* SNN_RECORD_PACKED_I8 read-back tables [source][target] */
     int32_t i8_step[SNN_MAX_POPS][SNN_MAX_POPS];
 } snn_info;
@@ -246,13 +268,25 @@ int snn_read_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t capa
 
 /* Waits for the enqueued steps and returns the mean firing rate (Hz) of each
  * population over steps [t_begin, t_end) (§4.1's rate statistic), from all spikes
- * recorded so far.  pop_rates_hz has n_pops entries; neuron_counts (n_neurons
+ * recorded so far (pooled over the circuits of a batch).  pop_rates_hz has n_pops entries; neuron_counts (n_neurons
  * entries, may be NULL) receives per-neuron spike counts in the window.
  * Errors: SNN_EINVAL (empty or negative window), SNN_EOVERFLOW, SNN_ECUDA. */
 int snn_read_rates(snn_net *net, int64_t t_begin, int64_t t_end, double *pop_rates_hz, int32_t *neuron_counts);
 
 /* Fills `out` with the network's constants and counters (host only, no wait). */
 int snn_get_info(const snn_net *net, snn_info *out);
+
+/* Changes the launch schedule of the step kernels and re-captures the step graph
+ * (waits for enqueued steps first): grid_ctas = CTAs of the step kernel (pipelined) or
+ * of the delivery kernel (graph engine), delivery_warps = delivery warps per CTA
+ * (pipelined, 1..8), steps_per_graph as in snn_spec; 0 keeps a value.  The schedule
+ * never changes results, only speed (see paper_2405_02019_gb300.autotune).
+ * Errors: SNN_EINVAL (out of range), SNN_ENOTSUP (persistent engine), SNN_ECUDA. */
+int snn_set_schedule(snn_net *net, int32_t grid_ctas, int32_t delivery_warps, int32_t steps_per_graph);
+
+/* Batched networks: the first neuron and the neuron count of every circuit (host
+ * arrays of n_circuits entries).  A single circuit reports base 0 and N. */
+int snn_get_circuits(const snn_net *net, int64_t *base, int64_t *n_neurons);
 
 /* Copies every neuron's out-degree (synapses in its row, padding excluded) into the
  * host array out[n_neurons] (host only). */
@@ -328,7 +362,8 @@ void snn_destroy(snn_net *net);
  * the same time) race and give wrong results: serialise them.
  * Errors: SNN_EINVAL for more than SNN_STATIC_MAX_NEURONS neurons, a missing or
  * misaligned buffer, a negative t; SNN_ENOTSUP for a network with packed synapse
- * records (this step reads plain records); SNN_ECUDA on a failed CUDA call.
+ * records (this step reads plain records) or a batch of circuits; SNN_ECUDA on a
+ * failed CUDA call.
  */
 #define SNN_STATIC_MAX_NEURONS 131072
 typedef struct snn_static_io {

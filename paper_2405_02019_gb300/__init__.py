@@ -70,7 +70,7 @@ class _Spec:
     """An snn_spec plus the host arrays it points to (kept alive together)."""
 
     def __init__(self, model, scale_n=1000, scale_k=1000, seed=1, custom=None, steps_per_graph=0,
-                 raster_capacity=0, deliver_blocks=0, n_threads=0, engine=0, record_format=0):
+                 raster_capacity=0, deliver_blocks=0, n_threads=0, engine=0, record_format=0, circuits=None):
         s = snn_spec()
         s.engine = int(engine)
         s.record_format = int(record_format)
@@ -105,6 +105,13 @@ class _Spec:
                 cn.pop_offsets[b] = int(po[b]) if b < len(po) else cn.n_neurons
             self._keep.append(cn)
             s.custom = C.pointer(cn)
+        if circuits:
+            arr = (_abi.snn_circuit * len(circuits))()
+            for c, (sn, sk, sd) in enumerate(circuits):
+                arr[c].scale_n_permille, arr[c].scale_k_permille, arr[c].seed = int(sn), int(sk), int(sd)
+            self._keep.append(arr)
+            s.n_circuits = len(circuits)
+            s.circuits = C.cast(arr, C.POINTER(_abi.snn_circuit))
         self.spec = s
 
 
@@ -189,14 +196,14 @@ class Network:
 
     def __init__(self, model, scale_n=1000, scale_k=1000, seed=1, custom=None, steps_per_graph=0,
                  raster_capacity=0, deliver_blocks=0, n_threads=0, device=None, engine=ENGINE_DEFAULT,
-                 record_format=RECORD_PLAIN9):
+                 record_format=RECORD_PLAIN9, circuits=None):
         import torch
 
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
         self.device = torch.device(device if device is not None else "cuda")
         self._spec = _Spec(model, scale_n, scale_k, seed, custom, steps_per_graph, raster_capacity,
-                           deliver_blocks, n_threads, engine, record_format)
+                           deliver_blocks, n_threads, engine, record_format, circuits)
         self.sizes = snn_query_sizes(self._spec.spec)
         self.model = model
         with torch.cuda.device(self.device):
@@ -242,6 +249,20 @@ class Network:
     def load_state(self, blob: bytes) -> None:
         buf = np.frombuffer(blob, np.uint8).copy()
         _check(load().snn_load_state(C.c_void_p(self._handle), C.c_void_p(_ptr(buf)), len(buf)), "snn_load_state")
+
+    def set_schedule(self, grid_ctas: int = 0, delivery_warps: int = 0, steps_per_graph: int = 0) -> None:
+        """Launch shape of the step kernels (results never depend on it)."""
+        _check(load().snn_set_schedule(C.c_void_p(self._handle), int(grid_ctas), int(delivery_warps),
+                                       int(steps_per_graph)), "snn_set_schedule")
+
+    def circuits(self):
+        """(base, n_neurons) arrays: where every circuit of a batch sits in the index space."""
+        k = int(self.info().n_circuits)
+        base = np.zeros(k, np.int64)
+        n = np.zeros(k, np.int64)
+        _check(load().snn_get_circuits(C.c_void_p(self._handle), C.c_void_p(_ptr(base)), C.c_void_p(_ptr(n))),
+               "snn_get_circuits")
+        return base, n
 
     def out_degrees(self) -> np.ndarray:
         out = np.zeros(self.n_neurons, np.int32)

@@ -46,6 +46,10 @@ class snn_custom_net(C.Structure):
     ]
 
 
+class snn_circuit(C.Structure):
+    _fields_ = [("scale_n_permille", C.c_int32), ("scale_k_permille", C.c_int32), ("seed", C.c_uint64)]
+
+
 class snn_spec(C.Structure):
     _fields_ = [
         ("abi_version", C.c_uint32), ("scale_n_permille", C.c_int32), ("scale_k_permille", C.c_int32),
@@ -54,6 +58,8 @@ class snn_spec(C.Structure):
         ("engine", C.c_int32), ("record_format", C.c_int32),
         ("model", snn_model),
         ("custom", C.POINTER(snn_custom_net)),
+        ("n_circuits", C.c_int32), ("reserved", C.c_int32),
+        ("circuits", C.POINTER(snn_circuit)),
     ]
 
 
@@ -85,6 +91,8 @@ class snn_info(C.Structure):
         ("steps_per_graph", C.c_int32), ("deliver_blocks", C.c_int32),
         ("device_error", C.c_uint32), ("engine", C.c_int32),
         ("record_format", C.c_int32), ("bytes_per_synapse", C.c_int32),
+        ("n_circuits", C.c_int32), ("schedule_ctas", C.c_int32), ("schedule_delivery_warps", C.c_int32),
+        ("reserved2", C.c_int32),
         ("i8_base", (C.c_int32 * MAX_POPS) * MAX_POPS), ("i8_step", (C.c_int32 * MAX_POPS) * MAX_POPS),
     ]
 
@@ -115,6 +123,8 @@ PROTOTYPES = {
     "snn_profile_steps": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_double),
                                     C.POINTER(C.c_double)]),
     "snn_get_out_degrees": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "snn_get_circuits": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "snn_set_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
     "snn_save_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.POINTER(C.c_uint64)]),
     "snn_load_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64]),
     "snn_deliver_spikes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p]),

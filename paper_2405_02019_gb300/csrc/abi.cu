@@ -50,6 +50,8 @@ struct snn_net {
     std::vector<int64_t> pop_off;
     std::vector<int32_t> out_degree;
     int format = SNN_RECORD_PLAIN9;
+    std::vector<uint8_t> pop_id;
+    std::vector<snn::CircuitInfo> circuits;
     int32_t i8_base[SNN_MAX_POPS][SNN_MAX_POPS] = {};
     int32_t i8_step[SNN_MAX_POPS][SNN_MAX_POPS] = {};
     uint8_t *arena = nullptr;
@@ -255,6 +257,7 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         net = new snn_net();
         net->spec = *spec;
         net->spec.custom = nullptr;
+        net->spec.circuits = nullptr;
         net->L = snn::make_layout(*spec);
         if (arena_bytes < net->L.total) {
             delete net;
@@ -277,6 +280,7 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         net->pop_off = hn.pop_off;
         net->out_degree = std::move(hn.out_degree);
         net->format = hn.format;
+        net->circuits = hn.circuits;
         std::memcpy(net->i8_base, hn.i8_base, sizeof(net->i8_base));
         std::memcpy(net->i8_step, hn.i8_step, sizeof(net->i8_step));
 
@@ -297,6 +301,19 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
             for (int tb = 0; tb < SNN_MAX_POPS; ++tb) tabs.i8_pair[sa][tb] = {hn.i8_base[sa][tb], hn.i8_step[sa][tb]};
         std::vector<float> u0(net->npad, 0.0f);
         std::copy(hn.u0.begin(), hn.u0.end(), u0.begin());
+        std::vector<uint8_t> pop_dev(net->npad, 0);
+        std::copy(hn.pop_id.begin(), hn.pop_id.end(), pop_dev.begin());
+        std::vector<int32_t> group_circuit(net->npad / 128 + 1, 0);
+        for (size_t g = 0, ci = 0; g < group_circuit.size(); ++g) {
+            while (ci + 1 < hn.circuits.size() && static_cast<int64_t>(g) * 128 >= hn.circuits[ci + 1].base) ++ci;
+            group_circuit[g] = static_cast<int32_t>(ci);
+        }
+        cuda_ok(cudaMemcpyAsync(A + L.pop_id, pop_dev.data(), net->npad, cudaMemcpyHostToDevice, st), "pop_id");
+        cuda_ok(cudaMemcpyAsync(A + L.group_circuit, group_circuit.data(), 4 * group_circuit.size(),
+                                cudaMemcpyHostToDevice, st), "group_circuit");
+        cuda_ok(cudaMemcpyAsync(A + L.circuits, hn.circuits.data(), sizeof(snn::CircuitInfo) * hn.circuits.size(),
+                                cudaMemcpyHostToDevice, st), "circuits");
+        net->pop_id = std::move(pop_dev);
         cuda_ok(cudaMemsetAsync(A + L.ctl, 0, sizeof(snn::Ctl), st), "memset ctl");
         cuda_ok(cudaMemcpyAsync(A + L.tables, &tabs, sizeof(tabs), cudaMemcpyHostToDevice, st), "tables");
         cuda_ok(cudaMemcpyAsync(A + L.U, u0.data(), 4 * net->npad, cudaMemcpyHostToDevice, st), "U");
@@ -341,6 +358,10 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         a.rast_cap = static_cast<uint32_t>(L.rast_cap);
         a.chunks_per_row = net->chunks_per_row;
         a.format = net->format;
+        a.n_circuits = static_cast<int32_t>(net->circuits.size());
+        a.pop_id = A + L.pop_id;
+        a.group_circuit = reinterpret_cast<const int32_t *>(A + L.group_circuit);
+        a.circuits = reinterpret_cast<const snn::CircuitInfo *>(A + L.circuits);
         a.p11 = net->c.p11f;
         a.p21 = net->c.p21f;
         a.p22 = net->c.p22f;
@@ -382,6 +403,7 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
             a.neuron_warps = static_cast<int32_t>(
                 std::min<int64_t>(snn::kStepMaxNeuronWarps,
                                   std::max<int64_t>(1, (quad_warps + net->step_grid - 1) / net->step_grid)));
+            a.delivery_warps = snn::kStepDeliverWarps;
             a.U2 = reinterpret_cast<float *>(A + L.U2);
             a.R2 = A + L.R2;
             a.queue = reinterpret_cast<snn::QueueEntry *>(A + L.queue);
@@ -546,16 +568,16 @@ int snn_read_rates(snn_net *net, int64_t t_begin, int64_t t_end, double *pop_rat
     const auto hi = std::lower_bound(net->hist_t.begin(), net->hist_t.end(), t_end) - net->hist_t.begin();
     for (auto j = lo; j < hi; ++j) {
         const int32_t i = net->hist_i[j];
-        int b = 0;
-        while (b + 1 < P && i >= net->pop_off[b + 1]) ++b;
-        ++pop_cnt[b];
+        ++pop_cnt[net->pop_id[i]];
         if (neuron_counts) ++neuron_counts[i];
     }
+    // population sizes over every circuit (inert neurons between circuits excluded)
+    std::vector<int64_t> pop_n(P, 0);
+    for (const auto &ci : net->circuits)
+        for (int64_t i = ci.base; i < ci.base + ci.n; ++i) ++pop_n[net->pop_id[i]];
     const double secs = static_cast<double>(t_end - t_begin) * net->spec.model.dt_ms * 1e-3;
-    for (int b = 0; b < P; ++b) {
-        const int64_t nb = net->pop_off[b + 1] - net->pop_off[b];
-        pop_rates_hz[b] = nb > 0 ? static_cast<double>(pop_cnt[b]) / (static_cast<double>(nb) * secs) : 0.0;
-    }
+    for (int b = 0; b < P; ++b)
+        pop_rates_hz[b] = pop_n[b] > 0 ? static_cast<double>(pop_cnt[b]) / (static_cast<double>(pop_n[b]) * secs) : 0.0;
     return rc;
 }
 
@@ -599,6 +621,9 @@ int snn_get_info(const snn_net *net, snn_info *out)
     out->engine = net->engine;
     out->record_format = net->format;
     out->bytes_per_synapse = snn::record_bytes(net->format);
+    out->n_circuits = static_cast<int32_t>(net->circuits.size());
+    out->schedule_ctas = net->engine == SNN_ENGINE_PIPELINED ? net->step_grid : net->deliver_grid;
+    out->schedule_delivery_warps = net->engine == SNN_ENGINE_PIPELINED ? net->args.delivery_warps : 0;
     std::memcpy(out->i8_base, net->i8_base, sizeof(out->i8_base));
     std::memcpy(out->i8_step, net->i8_step, sizeof(out->i8_step));
     return SNN_OK;
@@ -703,6 +728,53 @@ int snn_load_state(snn_net *net, const void *host_buf, uint64_t bytes)
     net->read_pos = 0;
     net->events_read = 0;
     net->device_error = 0;
+    return SNN_OK;
+}
+
+int snn_set_schedule(snn_net *net, int32_t grid_ctas, int32_t delivery_warps, int32_t steps_per_graph)
+{
+    if (!net) return fail(SNN_EINVAL, "null network");
+    if (grid_ctas < 0 || grid_ctas > 65535 || delivery_warps < 0 || steps_per_graph < 0 || steps_per_graph > 100000)
+        return fail(SNN_EINVAL, "schedule out of range");
+    int rc = wait_done(net);
+    if (rc) return rc;
+    snn::StepArgs &a = net->args;
+    if (net->engine == SNN_ENGINE_PIPELINED) {
+        if (grid_ctas > 0) net->step_grid = grid_ctas;
+        if (delivery_warps > 0) {
+            if (delivery_warps + snn::kStepMaxNeuronWarps > snn::kStepMaxThreads / 32)
+                return fail(SNN_EINVAL, "too many delivery warps per CTA");
+            a.delivery_warps = delivery_warps;
+        }
+        const int64_t quad_warps = ((net->n + 3) / 4 + 31) / 32;
+        a.neuron_warps = static_cast<int32_t>(std::min<int64_t>(
+            snn::kStepMaxNeuronWarps, std::max<int64_t>(1, (quad_warps + net->step_grid - 1) / net->step_grid)));
+        if (steps_per_graph > 0)
+            net->steps_per_graph = std::max(snn::kPhasePeriod, steps_per_graph / snn::kPhasePeriod * snn::kPhasePeriod);
+    } else if (net->engine == SNN_ENGINE_GRAPH) {
+        if (grid_ctas > 0) net->deliver_grid = grid_ctas;
+        if (steps_per_graph > 0) net->steps_per_graph = steps_per_graph;
+    } else {
+        if (grid_ctas > 0 || delivery_warps > 0 || steps_per_graph > 0)
+            return fail(SNN_ENOTSUP, "the persistent engine has a fixed schedule");
+        return SNN_OK;
+    }
+    if (net->graph_exec) cudaGraphExecDestroy(net->graph_exec);
+    if (net->graph) cudaGraphDestroy(net->graph);
+    if (net->capture_stream) cudaStreamDestroy(net->capture_stream);
+    net->graph_exec = nullptr;
+    net->graph = nullptr;
+    net->capture_stream = nullptr;
+    return capture_graph(net);
+}
+
+int snn_get_circuits(const snn_net *net, int64_t *base, int64_t *n_neurons)
+{
+    if (!net || !base || !n_neurons) return fail(SNN_EINVAL, "null argument");
+    for (size_t c = 0; c < net->circuits.size(); ++c) {
+        base[c] = net->circuits[c].base;
+        n_neurons[c] = net->circuits[c].n;
+    }
     return SNN_OK;
 }
 

@@ -127,23 +127,61 @@ int64_t pair_count(const snn_model &m, int32_t scale_n, int32_t scale_k, int tar
     return static_cast<int64_t>(std::llround(m.conn_p[target][source] * src * static_cast<double>(nb[target])));
 }
 
+namespace {
+
+int64_t circuit_neurons(const snn_model &m, int32_t scale_n)
+{
+    int64_t nb[SNN_MAX_POPS];
+    population_sizes(m, scale_n, nb);
+    int64_t n = 0;
+    for (int b = 0; b < m.n_pops; ++b) n += nb[b];
+    return n;
+}
+
+int64_t circuit_synapses(const snn_model &m, int32_t scale_n, int32_t scale_k)
+{
+    int64_t s = 0;
+    for (int a = 0; a < m.n_pops; ++a)
+        for (int b = 0; b < m.n_pops; ++b) s += pair_count(m, scale_n, scale_k, b, a);
+    return s;
+}
+
+// A single circuit described by the batch entry c (or the spec itself).
+snn_spec circuit_spec(const snn_spec &spec, int c)
+{
+    snn_spec one = spec;
+    one.n_circuits = 0;
+    one.circuits = nullptr;
+    if (spec.n_circuits > 0) {
+        one.scale_n_permille = spec.circuits[c].scale_n_permille;
+        one.scale_k_permille = spec.circuits[c].scale_k_permille;
+        one.seed = spec.circuits[c].seed;
+    }
+    return one;
+}
+
+}  // namespace
+
 int64_t count_neurons(const snn_spec &spec)
 {
     if (spec.custom) return spec.custom->n_neurons;
-    int64_t nb[SNN_MAX_POPS];
-    population_sizes(spec.model, spec.scale_n_permille, nb);
-    int64_t n = 0;
-    for (int b = 0; b < spec.model.n_pops; ++b) n += nb[b];
-    return n;
+    if (spec.n_circuits <= 0) return circuit_neurons(spec.model, spec.scale_n_permille);
+    int64_t base = 0, last = 0;
+    for (int c = 0; c < spec.n_circuits; ++c) {
+        base = (base + last + 127) / 128 * 128;
+        last = circuit_neurons(spec.model, spec.circuits[c].scale_n_permille);
+        if (c == 0) base = 0;
+    }
+    return base + last;
 }
 
 int64_t count_synapses(const snn_spec &spec)
 {
     if (spec.custom) return spec.custom->n_synapses;
+    if (spec.n_circuits <= 0) return circuit_synapses(spec.model, spec.scale_n_permille, spec.scale_k_permille);
     int64_t s = 0;
-    for (int a = 0; a < spec.model.n_pops; ++a)
-        for (int b = 0; b < spec.model.n_pops; ++b)
-            s += pair_count(spec.model, spec.scale_n_permille, spec.scale_k_permille, b, a);
+    for (int c = 0; c < spec.n_circuits; ++c)
+        s += circuit_synapses(spec.model, spec.circuits[c].scale_n_permille, spec.circuits[c].scale_k_permille);
     return s;
 }
 
@@ -181,6 +219,25 @@ bool validate_spec(const snn_spec &spec, std::string &why)
         return fail("unknown record_format");
     if (spec.record_format != SNN_RECORD_PLAIN9 && count_neurons(spec) > kPackedMaxNeurons)
         return fail("packed records hold at most 2^20 neurons");
+    if (spec.n_circuits < 0 || spec.n_circuits > SNN_MAX_CIRCUITS) return fail("n_circuits out of [0, SNN_MAX_CIRCUITS]");
+    if (spec.n_circuits > 0 && !spec.circuits) return fail("circuits missing");
+    if (spec.n_circuits > 0 && spec.custom) return fail("a custom network cannot be batched");
+    for (int c = 0; c < spec.n_circuits; ++c) {
+        snn_spec one = spec;
+        one.n_circuits = 0;
+        one.circuits = nullptr;
+        one.scale_n_permille = spec.circuits[c].scale_n_permille;
+        one.scale_k_permille = spec.circuits[c].scale_k_permille;
+        if (!validate_spec(one, why)) {
+            why = "circuit " + std::to_string(c) + ": " + why;
+            return false;
+        }
+    }
+    if (spec.n_circuits > 0) {
+        if (count_neurons(spec) > (int64_t{1} << 30)) return fail("batched neuron count above 2^30");
+        if (count_synapses(spec) > (int64_t{1} << 35)) return fail("batched synapse count above 2^35");
+        return true;
+    }
     if (spec.custom) {
         const snn_custom_net &c = *spec.custom;
         if (c.n_neurons < 1 || c.n_neurons > (int64_t{1} << 30)) return fail("custom n_neurons out of [1, 2^30]");
@@ -241,6 +298,9 @@ Layout make_layout(const snn_spec &spec)
     L.R2 = o; o = up(o + L.npad);
     L.queue = o; o = up(o + uint64_t{4} * sizeof(QueueEntry) * L.npad);
     L.qcount = o; o = up(o + uint64_t{4} * 4 * (L.npad / 128 + 1));
+    L.pop_id = o; o = up(o + L.npad);
+    L.group_circuit = o; o = up(o + 4 * (L.npad / 128 + 1));
+    L.circuits = o; o = up(o + sizeof(CircuitInfo) * std::max(1, spec.n_circuits));
     L.total = o;
     return L;
 }
@@ -312,13 +372,6 @@ void sample_edges(const snn_spec &spec, const Constants &c, EdgeList &e, int nth
     });
 }
 
-inline int pop_index(const std::vector<int64_t> &off, int n_pops, int64_t i)
-{
-    int b = 0;
-    while (b + 1 < n_pops && i >= off[b + 1]) ++b;
-    return b;
-}
-
 uint16_t to_bf16_even(float f)
 {
     uint32_t u;
@@ -329,7 +382,7 @@ uint16_t to_bf16_even(float f)
 
 // Compressed records (§5.3): packed words, and int8 codes fitted per population pair or
 // bfloat16 currents; the plain arrays are released afterwards.
-void pack_records(HostNetwork &net, int n_pops, int nthreads)
+void pack_records(HostNetwork &net, int /*n_pops*/, int nthreads)
 {
     const int64_t n = net.n;
     const int64_t S = net.n_syn_padded;
@@ -340,10 +393,10 @@ void pack_records(HostNetwork &net, int n_pops, int nthreads)
     std::vector<std::vector<int64_t>> lo(T, std::vector<int64_t>(64, INT64_MAX)), hi(T, std::vector<int64_t>(64, INT64_MIN));
     parallel_for(T, n, [&](int th, int64_t r0, int64_t r1) {
         for (int64_t i = r0; i < r1; ++i) {
-            const int a = pop_index(net.pop_off, n_pops, i);
+            const int a = net.pop_id[i];
             const int64_t real_end = net.row_ptr[i] + net.out_degree[i];
             for (int64_t s = net.row_ptr[i]; s < net.row_ptr[i + 1]; ++s) {
-                const int b = pop_index(net.pop_off, n_pops, net.tgt[s]);
+                const int b = net.pop_id[net.tgt[s]];
                 tpop[s] = static_cast<uint8_t>(b);
                 uint32_t w = static_cast<uint32_t>(net.tgt[s]) | (static_cast<uint32_t>(net.d[s]) << kWordDelayShift) |
                              (static_cast<uint32_t>(b) << kWordPopShift);
@@ -376,7 +429,7 @@ void pack_records(HostNetwork &net, int n_pops, int nthreads)
         net.wbytes.assign(S, 0);
         parallel_for(T, n, [&](int, int64_t r0, int64_t r1) {
             for (int64_t i = r0; i < r1; ++i) {
-                const int a = pop_index(net.pop_off, n_pops, i);
+                const int a = net.pop_id[i];
                 const int64_t real_end = net.row_ptr[i] + net.out_degree[i];
                 for (int64_t s = net.row_ptr[i]; s < real_end; ++s) {
                     const int b = tpop[s];
@@ -403,7 +456,65 @@ void pack_records(HostNetwork &net, int n_pops, int nthreads)
 
 }  // namespace
 
+namespace {
+bool build_one(const snn_spec &spec, const Constants &c, HostNetwork &net, std::string &why);
+}
+
 bool build_host_network(const snn_spec &spec, const Constants &c, HostNetwork &net, std::string &why)
+{
+    if (spec.n_circuits <= 0) {
+        if (!build_one(spec, c, net, why)) return false;
+        net.circuits = {CircuitInfo{0, net.n, spec.seed, 0}};
+        return true;
+    }
+    // a batch: every circuit built alone (in plain records), placed at a 128-aligned base
+    const int fmt = spec.record_format;
+    HostNetwork all;
+    all.format = SNN_RECORD_PLAIN9;
+    int64_t base = 0;
+    for (int ci = 0; ci < spec.n_circuits; ++ci) {
+        snn_spec one = circuit_spec(spec, ci);
+        one.record_format = SNN_RECORD_PLAIN9;
+        HostNetwork h;
+        if (!build_one(one, c, h, why)) return false;
+        if (ci > 0) base = (all.n + 127) / 128 * 128;
+        // neurons: gap (inert) then the circuit
+        const int64_t syn_base = all.row_ptr.empty() ? 0 : all.row_ptr.back();
+        if (all.row_ptr.empty()) all.row_ptr.push_back(0);
+        while (all.n < base) {
+            all.row_ptr.push_back(syn_base);
+            all.out_degree.push_back(0);
+            all.u0.push_back(0.0f);
+            all.pop_id.push_back(0);
+            ++all.n;
+        }
+        for (int64_t i = 0; i < h.n; ++i) {
+            all.row_ptr.push_back(syn_base + h.row_ptr[i + 1]);
+            all.out_degree.push_back(h.out_degree[i]);
+            all.u0.push_back(h.u0[i]);
+            all.pop_id.push_back(h.pop_id[i]);
+        }
+        all.n += h.n;
+        for (size_t s2 = 0; s2 < h.tgt.size(); ++s2) all.tgt.push_back(h.tgt[s2] + static_cast<int32_t>(base));
+        all.w.insert(all.w.end(), h.w.begin(), h.w.end());
+        all.d.insert(all.d.end(), h.d.begin(), h.d.end());
+        all.n_syn += h.n_syn;
+        all.max_row = std::max(all.max_row, h.max_row);
+        all.circuits.push_back(CircuitInfo{base, h.n, one.seed, 0});
+    }
+    all.npad = (all.n + kNeuronAlign - 1) / kNeuronAlign * kNeuronAlign;
+    all.n_syn_padded = all.row_ptr.back();
+    all.pop_off.assign(SNN_MAX_POPS + 1, all.n);
+    all.pop_off[0] = 0;
+    all.format = fmt;
+    if (fmt != SNN_RECORD_PLAIN9) pack_records(all, spec.model.n_pops, resolve_threads(spec.n_threads));
+    net = std::move(all);
+    return true;
+}
+
+namespace {
+
+bool build_one(const snn_spec &spec, const Constants &c, HostNetwork &net, std::string &why)
 {
     const int nthreads = resolve_threads(spec.n_threads);
     const snn_model &m = spec.model;
@@ -534,9 +645,14 @@ bool build_host_network(const snn_spec &spec, const Constants &c, HostNetwork &n
             }
         }
     });
+    net.pop_id.assign(n, 0);
+    for (int b = 0; b < m.n_pops; ++b)
+        for (int64_t i = net.pop_off[b]; i < net.pop_off[b + 1]; ++i) net.pop_id[i] = static_cast<uint8_t>(b);
     net.format = spec.record_format;
     if (net.format != SNN_RECORD_PLAIN9) pack_records(net, spec.model.n_pops, nthreads);
     return true;
 }
+
+}  // namespace
 
 }  // namespace snn

@@ -53,6 +53,14 @@ struct alignas(8) PairQ {
     int32_t step;
 };
 
+// One circuit of the neuron index space (a single network is circuit 0).
+struct alignas(16) CircuitInfo {
+    int64_t base;    // first neuron (a multiple of 128)
+    int64_t n;       // neurons
+    uint64_t seed;   // seed of its random streams
+    int64_t pad;
+};
+
 // Read-only tables in the arena.
 struct alignas(16) StaticTables {
     uint64_t thresholds[SNN_MAX_POPS][kPK];  // 63-bit Poisson CDF thresholds
@@ -104,7 +112,12 @@ struct StepArgs {
     int32_t quad_warps;           // pipelined engine: groups of 128 neurons (one queue region each)
     uint32_t *qcount;             // pipelined engine: spikes per group, [4][quad_warps]
     int32_t format;               // SNN_RECORD_*
-    int32_t pad2;
+    int32_t n_circuits;
+    int32_t delivery_warps;       // pipelined engine: delivery warps per CTA
+    int32_t pad3;
+    const uint8_t *pop_id;        // population of every neuron [npad]
+    const int32_t *group_circuit; // circuit of every group of 128 neurons [npad / 128]
+    const CircuitInfo *circuits;  // [n_circuits]
 };
 
 // Host constants of one model (§2.2).
@@ -119,6 +132,8 @@ struct Constants {
 // Network in host memory, in the device layout.
 struct HostNetwork {
     int format = SNN_RECORD_PLAIN9;
+    std::vector<uint8_t> pop_id;         // population of every neuron
+    std::vector<CircuitInfo> circuits;   // circuit table (one entry for a single network)
     std::vector<uint32_t> word;    // packed records: words
     std::vector<uint8_t> wbytes;   // packed records: int8 codes or bfloat16 currents
     int32_t i8_base[SNN_MAX_POPS][SNN_MAX_POPS] = {};
@@ -139,7 +154,8 @@ struct HostNetwork {
 
 // Arena layout for a spec.
 struct Layout {
-    uint64_t ctl, tables, U, I, R, ring, row_ptr, syn_tgt, syn_w, syn_d, rast_nrn, rast_t, U2, R2, queue, qcount, total;
+    uint64_t ctl, tables, U, I, R, ring, row_ptr, syn_tgt, syn_w, syn_d, rast_nrn, rast_t, U2, R2, queue, qcount, pop_id,
+        group_circuit, circuits, total;
     int64_t npad, syn_padded_max, rast_cap;
 };
 

@@ -72,15 +72,11 @@ __device__ __forceinline__ void red_release_add_u32(uint32_t *addr, uint32_t v)
 
 struct SharedTables {
     uint64_t thr[SNN_MAX_POPS * kPK];
-    int64_t off[SNN_MAX_POPS + 1];
-    int n_pops;
 };
 
 __device__ __forceinline__ void stage_tables(const StepArgs &a, SharedTables &s)
 {
     for (int j = threadIdx.x; j < SNN_MAX_POPS * kPK; j += blockDim.x) s.thr[j] = (&a.tables->thresholds[0][0])[j];
-    if (threadIdx.x <= SNN_MAX_POPS) s.off[threadIdx.x] = a.tables->pop_off[threadIdx.x];
-    if (threadIdx.x == 0) s.n_pops = a.tables->n_pops;
     __syncthreads();
 }
 
@@ -116,18 +112,19 @@ __device__ __forceinline__ void update_quad(const StepArgs &a, const SharedTable
     int32_t *wrow = a.ring + slot * a.npad + i0;
     const int4 w4 = __ldcg(reinterpret_cast<const int4 *>(wrow));
     *reinterpret_cast<int4 *>(wrow) = make_int4(0, 0, 0, 0);
-    const Block4 rnd =
-        philox4x64_10(static_cast<uint64_t>(t), static_cast<uint64_t>(q), 0, 0, a.seed, kStreamThalamic);
+    const CircuitInfo ci = a.circuits[a.group_circuit[i0 >> 7]];
+    const uint32_t pops = *reinterpret_cast<const uint32_t *>(a.pop_id + i0);
+    const Block4 rnd = philox4x64_10(static_cast<uint64_t>(t), static_cast<uint64_t>((i0 - ci.base) >> 2), 0, 0,
+                                     ci.seed, kStreamThalamic);
     float uu[4] = {u4.x, u4.y, u4.z, u4.w};
     float cc[4] = {c4.x, c4.y, c4.z, c4.w};
     const int32_t ww[4] = {w4.x, w4.y, w4.z, w4.w};
     uint32_t rr[4] = {r4 & 0xFFu, (r4 >> 8) & 0xFFu, (r4 >> 16) & 0xFFu, r4 >> 24};
-    int b = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int64_t i = i0 + j;
-        if (i < a.n) {
-            while (b + 1 < s.n_pops && i >= s.off[b + 1]) ++b;
+        if (i < ci.base + ci.n) {
+            const int b = (pops >> (8 * j)) & 0xFF;
             const uint64_t v = rnd.w[j] >> 1;
             const uint64_t *thr = s.thr + b * kPK;
             uint32_t T = 0;
@@ -171,14 +168,6 @@ __device__ __forceinline__ void append_spikes(const StepArgs &a, int64_t t, int6
             ++pos;
         }
     }
-}
-
-// Population of neuron i from the offsets in the launch arguments.
-__device__ __forceinline__ int pop_of(const StepArgs &a, int64_t i)
-{
-    int b = 0;
-    while (b + 1 < a.n_pops && i >= a.pop_off[b + 1]) ++b;
-    return b;
 }
 
 // One 256-synapse chunk [off, min(off + 256, re)) of a row whose sender belongs to
@@ -260,7 +249,7 @@ __device__ __forceinline__ void deliver_list_fmt(const StepArgs &a, int64_t t, c
         const int64_t re = a.row_ptr[s + 1];
         const int64_t off = rs + c * kChunk;
         if (off >= re) continue;
-        deliver_chunk<FMT>(a, t, off, re, FMT == SNN_RECORD_PACKED_I8 ? pop_of(a, s) : 0);
+        deliver_chunk<FMT>(a, t, off, re, FMT == SNN_RECORD_PACKED_I8 ? __ldg(a.pop_id + s) : 0);
     }
 }
 
@@ -434,17 +423,22 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, i
     const int phn = ph + 1;  // phase of the step whose spikes are decided here
     int32_t spk[4] = {0, 0, 0, 0};
     int64_t rp[5] = {0, 0, 0, 0, 0};
-    // independent of the previous step: network, tables, random numbers
+    // independent of the previous step: network, tables, circuit, random numbers
     uint64_t tr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     Block4 rnd = {{0, 0, 0, 0}};
     int b0 = 0;
+    uint32_t pops = 0;
+    int64_t end_valid = 0;  // neurons of the quad's circuit end here
     const uint64_t *thr0 = a.tables->thresholds[0];
     if (valid) {
         const longlong2 rpa = __ldg(reinterpret_cast<const longlong2 *>(a.row_ptr + i0));
         const longlong2 rpb = __ldg(reinterpret_cast<const longlong2 *>(a.row_ptr + i0 + 2));
         const int64_t rpc = __ldg(a.row_ptr + i0 + 4);
         rp[0] = rpa.x; rp[1] = rpa.y; rp[2] = rpb.x; rp[3] = rpb.y; rp[4] = rpc;
-        b0 = pop_of(a, i0);
+        const CircuitInfo ci = a.circuits[__ldg(a.group_circuit + g)];
+        end_valid = ci.base + ci.n;
+        pops = __ldg(reinterpret_cast<const unsigned int *>(a.pop_id + i0));
+        b0 = pops & 0xFF;
         thr0 = &a.tables->thresholds[b0][0];
         if (do_b) {
 #pragma unroll
@@ -453,7 +447,8 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, i
                 tr[k] = v2.x;
                 tr[k + 1] = v2.y;
             }
-            rnd = philox4x64_10(static_cast<uint64_t>(t), static_cast<uint64_t>(q), 0, 0, a.seed, kStreamThalamic);
+            rnd = philox4x64_10(static_cast<uint64_t>(t), static_cast<uint64_t>((i0 - ci.base) >> 2), 0, 0, ci.seed,
+                                kStreamThalamic);
         }
     }
     if (wait_first) wait_previous_grid();
@@ -478,8 +473,8 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, i
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int64_t i = i0 + j;
-                if (i < a.n) {
-                    const int b = pop_of(a, i);
+                if (i < end_valid) {
+                    const int b = (pops >> (8 * j)) & 0xFF;
                     const uint64_t v = rnd.w[j] >> 1;
                     uint32_t T;
                     if (b == b0) {
@@ -498,7 +493,7 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, i
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            if (i0 + j >= a.n) continue;
+            if (i0 + j >= end_valid) continue;
             if (rr[j] == 0u) {
                 float x = __fadd_rn(__fmul_rn(a.p22, uu[j]), __fmul_rn(a.p21, cc[j]));
                 if (x >= a.theta) {
@@ -587,7 +582,7 @@ __device__ __forceinline__ void pipe_deliver_fmt(const StepArgs &a, const int64_
         const int64_t re = rs + static_cast<int64_t>(static_cast<uint32_t>(raw.y)) * 4;
         const int64_t off = rs + c * kChunk;
         if (off >= re) continue;
-        deliver_chunk<FMT>(a, ph, off, re, FMT == SNN_RECORD_PACKED_I8 ? pop_of(a, raw.z) : 0);
+        deliver_chunk<FMT>(a, ph, off, re, FMT == SNN_RECORD_PACKED_I8 ? __ldg(a.pop_id + raw.z) : 0);
     }
 }
 
@@ -647,7 +642,7 @@ __global__ void __launch_bounds__(kStepMaxThreads, 2) k_prime(const StepArgs a)
 
 int step_grid(int num_sms) { return num_sms; }
 
-int step_threads(const StepArgs &a) { return 32 * (a.neuron_warps + kStepDeliverWarps); }
+int step_threads(const StepArgs &a) { return 32 * (a.neuron_warps + a.delivery_warps); }
 
 static size_t step_smem(const StepArgs &) { return 0; }
 

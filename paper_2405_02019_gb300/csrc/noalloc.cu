@@ -216,6 +216,7 @@ extern "C" int snn_step_static(const snn_net *net, const snn_static_io *io, uint
     if (snn_get_info(net, &info) != SNN_OK) return static_fail(SNN_EINVAL, "snn_step_static: bad network handle");
     if (info.record_format != SNN_RECORD_PLAIN9)
         return static_fail(SNN_ENOTSUP, "snn_step_static: only plain synapse records are supported");
+    if (info.n_circuits != 1) return static_fail(SNN_ENOTSUP, "snn_step_static: batched networks are not supported");
     if (info.n_neurons > SNN_STATIC_MAX_NEURONS)
         return static_fail(SNN_EINVAL,
                            "snn_step_static: network has more neurons than the static scratch holds "

@@ -595,3 +595,82 @@ def test_static_step_rejects_packed(model):
     rc = snn.load().snn_step_static(C.c_void_p(net._handle), C.byref(io), 1, 0, None)
     assert rc == _abi.SNN_ENOTSUP
     net.close()
+
+
+
+# ------------------------------------------------------------ batched circuits
+
+BATCH = [(20, 40, 5), (35, 10, 6), (13, 50, 7), (50, 50, 8), (1, 1, 9)]
+
+
+@pytest.mark.parametrize("fmt", [snn.RECORD_PLAIN9, snn.RECORD_PACKED_BF16])
+@pytest.mark.parametrize("engine", ENGINES)
+def test_batched_circuits_equal_standalone_runs(model, engine, fmt):
+    """Circuits of uneven scale and seed stepped together: every circuit's slice of the
+    batched raster and state equals the oracle run of that circuit alone."""
+    net = snn.Network(model, circuits=BATCH, steps_per_graph=128, engine=engine, record_format=fmt)
+    base, n = net.circuits()
+    assert np.all(base % 128 == 0) and np.all(base[1:] >= base[:-1] + n[:-1])
+    steps = 400
+    net.step(steps)
+    g_t, g_i = net.read_spikes()
+    U, I, R = _state(net)
+    for c, (sn, sk, seed) in enumerate(BATCH):
+        onet = oracle.build_network(model, sn, sk, seed)
+        if fmt == snn.RECORD_PACKED_BF16:
+            onet = oracle.with_weights(onet, oracle.quantize_bf16(onet.w_fx))
+        assert n[c] == onet.n
+        sim = oracle.Sim(model, onet, seed)
+        o_t, o_i = sim.run(steps)
+        sel = (g_i >= base[c]) & (g_i < base[c] + n[c])
+        assert np.array_equal(g_t[sel], o_t), c
+        assert np.array_equal(g_i[sel] - base[c], o_i), c
+        sl = slice(base[c], base[c] + n[c])
+        assert np.array_equal(U[sl].view(np.uint32), sim.U.view(np.uint32)), c
+        assert np.array_equal(I[sl].view(np.uint32), sim.I.view(np.uint32)), c
+        assert np.array_equal(R[sl], sim.R), c
+    # inert neurons between circuits never spike
+    inside = np.zeros(len(U), bool)
+    for c in range(len(BATCH)):
+        inside[base[c]: base[c] + n[c]] = True
+    assert inside[g_i].all()
+    net.close()
+
+
+# ------------------------------------------------------------ schedules, autotuner
+
+
+@pytest.mark.parametrize("engine,sched", [(PIPE, dict(grid_ctas=304, delivery_warps=4, steps_per_graph=256)),
+                                          (PIPE, dict(grid_ctas=37, delivery_warps=2)),
+                                          (GRAPH, dict(grid_ctas=17, steps_per_graph=100))])
+def test_schedule_does_not_change_results(model, tiny, engine, sched):
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, steps_per_graph=128, engine=engine)
+    net.step(300)
+    net.set_schedule(**sched)
+    info = net.info()
+    assert info.schedule_ctas == sched["grid_ctas"]
+    net.step(700)
+    g = net.read_spikes()
+    o = oracle.Sim(model, onet, wl.seed).run(1000)
+    assert np.array_equal(g[0], o[0]) and np.array_equal(g[1], o[1])
+    net.close()
+
+
+def test_autotune_keeps_dynamics(model, tiny, tmp_path):
+    from paper_2405_02019_gb300 import autotune
+
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed)
+    net.step(200)
+    first = net.read_spikes()
+    res = autotune.autotune(net, steps=256, cache_path=str(tmp_path / "sched.json"))
+    assert res["schedule"] and len(res["timings"]) >= 2
+    net.step(300)
+    second = net.read_spikes()
+    o = oracle.Sim(model, onet, wl.seed).run(500)
+    assert np.array_equal(np.concatenate([first[0], second[0]]), o[0])
+    assert np.array_equal(np.concatenate([first[1], second[1]]), o[1])
+    res2 = autotune.autotune(net, steps=256, cache_path=str(tmp_path / "sched.json"))
+    assert res2["schedule"] == res["schedule"]
+    net.close()
