@@ -412,6 +412,71 @@ def run_gpu(args):
                                 "in tests/test_precision_accuracy.py"}
         fnet.close()
 
+    torch.cuda.empty_cache()
+
+    def run_workload(label, circuits=None, wlx=None, fmt=snn.RECORD_PLAIN9, n_steps=None, tune=False):
+        """Build, optionally autotune, warm up and time a workload; returns a summary."""
+        t0 = time.perf_counter()
+        if circuits is not None:
+            xnet = snn.Network(model, circuits=circuits, steps_per_graph=tps, raster_capacity=1 << 27, device=dev,
+                               engine=engine, record_format=fmt)
+        else:
+            xnet = snn.Network(model, wlx.scale_n_permille, wlx.scale_k_permille, wlx.seed + rank,
+                               steps_per_graph=tps, raster_capacity=1 << 27, device=dev, engine=engine,
+                               record_format=fmt)
+        build = time.perf_counter() - t0
+        tuned = None
+        if tune:
+            from paper_2405_02019_gb300 import autotune
+
+            tuned = autotune.autotune(xnet, steps=tps, cache_path=None)
+        xnet.step(tps)
+        xnet.read_spikes()
+        x0 = xnet.info().events_read
+        s0 = xnet.info().spikes_read
+        nsteps = n_steps // tps * tps
+        torch.cuda.synchronize(dev)
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        xnet.step(nsteps)
+        b1.record(stream)
+        torch.cuda.synchronize(dev)
+        xsecs = b0.elapsed_time(b1) * 1e-3
+        xnet.read_spikes()
+        xi = xnet.info()
+        ev = xi.events_read - x0
+        out = {"workload": label, "neurons": int(xi.n_neurons), "synapses": int(xi.n_synapses),
+               "circuits": int(xi.n_circuits), "bytes_per_synapse": int(xi.bytes_per_synapse),
+               "steps": nsteps, "value": ev / xsecs, "unit": "synaptic events/s",
+               "us_per_step": xsecs / nsteps * 1e6, "rtf": xsecs / (nsteps * model.dt_ms * 1e-3),
+               "spikes_per_step": (xi.spikes_read - s0) / nsteps, "events_per_step": ev / nsteps,
+               "build_s": build}
+        if tuned is not None:
+            out["autotuned_schedule"] = tuned["schedule"]
+            out["autotune_timings"] = tuned["timings"]
+        xnet.close()
+        del xnet
+        torch.cuda.empty_cache()
+        return out
+
+    extra = {}
+    if "batched" in args.extra:
+        bw = workload.batched_workloads(32, 2026, 20000)
+        extra["batched"] = run_workload("32 PD circuits, neuron/in-degree scales U{100..1000} permille, seeds "
+                                        "1000+c, 2 s each", circuits=[(w.scale_n_permille, w.scale_k_permille, w.seed)
+                                                                      for w in bw],
+                                        n_steps=args.batched_steps, tune=True)
+        extra["batched"]["speedup_vs_single_circuit"] = extra["batched"]["value"] / value
+    if "x4" in args.extra:
+        wx = workload.WORKLOADS["pd_x4"]
+        extra["scaled_up_plain"] = run_workload("pd_x4 plain: 308,676 neurons, full in-degrees", wlx=wx,
+                                                n_steps=args.x4_steps)
+        extra["scaled_up_int8"] = run_workload("pd_x4 packed int8 records", wlx=wx, fmt=snn.RECORD_PACKED_I8,
+                                               n_steps=args.x4_steps)
+        extra["scaled_up_int8"]["speedup_vs_plain"] = (extra["scaled_up_int8"]["value"] /
+                                                       extra["scaled_up_plain"]["value"])
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu, _, _ = cpu_oracle_sample(model, wl, args.cpu_ticks)
@@ -443,6 +508,7 @@ def run_gpu(args):
                                       snn.ENGINE_GRAPH: 2 * tps + 1}[info.engine],
         "roofline": roofline, "kernels": kernels,
         "compressed_records": forms,
+        "workloads": extra,
         "delivery_saturating": {"kernel": "k_deliver_list", "bound": "hbm", "peak": peak, "unit": "GB/s",
                                 "traffic_20480": _recorded_traffic("k_deliver_list"),
                                 "note": "phase 2 alone over random senders of the same network "
@@ -472,6 +538,9 @@ def main():
     ap.add_argument("--saturating", type=int, nargs="*", default=[2048, 8192, 20480])
     ap.add_argument("--saturating-reps", type=int, default=5)
     ap.add_argument("--forms", nargs="*", default=["int8_pair", "bf16"])
+    ap.add_argument("--extra", nargs="*", default=["batched", "x4"])
+    ap.add_argument("--batched-steps", type=int, default=20480)
+    ap.add_argument("--x4-steps", type=int, default=10240)
     ap.add_argument("--form-steps", type=int, default=20)
     ap.add_argument("--engine", default="default", choices=["default", "graph", "persistent", "pipelined"])
     args = ap.parse_args()

@@ -292,9 +292,11 @@ class Network:
         return self._arena[start: start + count * item].view(dtype)
 
     def close(self) -> None:
+        """Releases the handle and the device arena."""
         if getattr(self, "_handle", 0):
             snn_destroy(self._handle)
             self._handle = 0
+        self._arena = None
 
     def __del__(self):
         try:

@@ -471,6 +471,17 @@ bool build_host_network(const snn_spec &spec, const Constants &c, HostNetwork &n
     const int fmt = spec.record_format;
     HostNetwork all;
     all.format = SNN_RECORD_PLAIN9;
+    {
+        const int64_t n_all = count_neurons(spec);
+        const int64_t s_all = count_synapses(spec) + int64_t{kRowAlign - 1} * n_all;
+        all.row_ptr.reserve(n_all + 1);
+        all.out_degree.reserve(n_all);
+        all.u0.reserve(n_all);
+        all.pop_id.reserve(n_all);
+        all.tgt.reserve(s_all);
+        all.w.reserve(s_all);
+        all.d.reserve(s_all);
+    }
     int64_t base = 0;
     for (int ci = 0; ci < spec.n_circuits; ++ci) {
         snn_spec one = circuit_spec(spec, ci);
