@@ -116,8 +116,10 @@ class ClockSampler:
         mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[j] for r in self.rows for j in range(4) if r[3 + j].lower() == "active"})
+        pw = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(self.rows),
+                "power_w_mean": float(np.mean(pw)) if pw else None}
 
 
 def _dist():
@@ -517,6 +519,13 @@ def run_gpu(args):
         "clocks": clk.summary(), "build_s": build_s,
         "paper_context": {"fpga_best_rtf": 0.79, "hardware": "Intel Agilex 7 FPGA (horiz/multi/s)"},
     }
+    pw = line["clocks"].get("power_w_mean")
+    if pw is not None and events > 0:
+        # board power sampled over the timed region x its duration / recurrent events (the
+        # energy-per-synaptic-event metric of Sec. 5, whole board, as the paper's upper bound)
+        line["energy"] = {"power_w_mean": pw, "nj_per_event": pw * secs_max / events * 1e9,
+                          "joules": pw * secs_max, "source": "nvidia-smi power.draw, whole GPU board",
+                          "paper_context": "21 nJ (whole FPGA board, 44.9 W) / 9 nJ (fabric only)"}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:

@@ -236,20 +236,32 @@ __device__ __forceinline__ void deliver_chunk(const StepArgs &a, int64_t slot, i
 
 // Phase 2 for the spikers list[0 .. nspk), work items grid-strided over warps:
 // item = (spiker, 256-synapse chunk of its row).
+// Items per spike when nspk spikes share nwarps warps: enough to keep every warp busy
+// while there are few spikes (one 256-synapse chunk per item), fewer and longer items
+// (consecutive chunks of one row) when spikes outnumber warps.
+__device__ __forceinline__ int64_t items_per_spike(int64_t cpr, int64_t nspk, int64_t nwarps)
+{
+    const int64_t ipj = nspk > 0 ? nwarps / nspk : cpr;
+    return ipj < 1 ? 1 : (ipj > cpr ? cpr : ipj);
+}
+
 template <int FMT>
 __device__ __forceinline__ void deliver_list_fmt(const StepArgs &a, int64_t t, const int32_t *list, int64_t nspk,
                                                  int64_t warp, int64_t nwarps)
 {
-    const int64_t items = nspk * a.chunks_per_row;
+    const int64_t cpr = a.chunks_per_row;
+    const int64_t ipj = items_per_spike(cpr, nspk, nwarps);
+    const int64_t per = (cpr + ipj - 1) / ipj;  // chunks per item
+    const int64_t items = nspk * ipj;
     for (int64_t it = warp; it < items; it += nwarps) {
-        const int64_t j = it / a.chunks_per_row;
-        const int64_t c = it - j * a.chunks_per_row;
+        const int64_t j = it / ipj;
+        const int64_t part = it - j * ipj;
         const int32_t s = __ldcg(list + j);
         const int64_t rs = a.row_ptr[s];
         const int64_t re = a.row_ptr[s + 1];
-        const int64_t off = rs + c * kChunk;
-        if (off >= re) continue;
-        deliver_chunk<FMT>(a, t, off, re, FMT == SNN_RECORD_PACKED_I8 ? __ldg(a.pop_id + s) : 0);
+        const int src = FMT == SNN_RECORD_PACKED_I8 ? __ldg(a.pop_id + s) : 0;
+        for (int64_t c = part * per, off = rs + c * kChunk; c < (part + 1) * per && off < re; ++c, off += kChunk)
+            deliver_chunk<FMT>(a, t, off, re, src);
     }
 }
 
@@ -559,19 +571,22 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, i
 // in one round trip.  The warp taking chunk 0 of spike j records it in the raster.
 template <int FMT>
 __device__ __forceinline__ void pipe_deliver_fmt(const StepArgs &a, const int64_t &t, int ph, int64_t dw, int64_t ndw,
-                                                 uint32_t n, uint32_t rbase)
+                                                 uint32_t n, uint32_t rbase, int4 first)
 {
     const int lane = threadIdx.x & 31;
     const QueueEntry *qbuf = a.queue + (ph & 3) * a.npad;
     const int64_t cpr = a.chunks_per_row;
     const int64_t npad = a.npad;
+    // items are (spike, run of `per` chunks); when every item is one chunk (few spikes) the
+    // entry `first` loaded before n arrived belongs to this warp's first item
+    const int64_t ipj = items_per_spike(cpr, n, ndw);
+    const int64_t per = (cpr + ipj - 1) / ipj;
     for (int64_t it = dw;; it += ndw) {
-        const int64_t j = it / cpr;
-        if (j >= npad) break;
-        const int4 raw = __ldcg(reinterpret_cast<const int4 *>(qbuf + j));  // issued before n is known
-        if (j >= n) break;
-        const int64_t c = it - j * cpr;
-        if (c == 0 && lane == 0) {
+        const int64_t j = it / ipj;
+        if (j >= npad || j >= n) break;
+        const int4 raw = (it == dw && ipj == cpr) ? first : __ldcg(reinterpret_cast<const int4 *>(qbuf + j));
+        const int64_t part = it - j * ipj;
+        if (part == 0 && lane == 0) {
             const uint64_t pos = static_cast<uint64_t>(rbase) + static_cast<uint64_t>(j);
             if (pos < a.rast_cap) {
                 a.rast_nrn[pos] = raw.z;
@@ -580,9 +595,9 @@ __device__ __forceinline__ void pipe_deliver_fmt(const StepArgs &a, const int64_
         }
         const int64_t rs = static_cast<int64_t>(static_cast<uint32_t>(raw.x)) * 4;
         const int64_t re = rs + static_cast<int64_t>(static_cast<uint32_t>(raw.y)) * 4;
-        const int64_t off = rs + c * kChunk;
-        if (off >= re) continue;
-        deliver_chunk<FMT>(a, ph, off, re, FMT == SNN_RECORD_PACKED_I8 ? __ldg(a.pop_id + raw.z) : 0);
+        const int src = FMT == SNN_RECORD_PACKED_I8 ? __ldg(a.pop_id + raw.z) : 0;
+        for (int64_t c = part * per, off = rs + c * kChunk; c < (part + 1) * per && off < re; ++c, off += kChunk)
+            deliver_chunk<FMT>(a, ph, off, re, src);
     }
 }
 
@@ -592,15 +607,20 @@ __device__ __forceinline__ void pipe_deliver(const StepArgs &a, const int64_t &t
     if (wait_first) wait_previous_grid();
     const uint32_t n = __ldcg(&a.ctl->qcnt[ph & 3]);
     const uint32_t rbase = __ldcg(&a.ctl->step_begin[t & 1]);
+    // speculative: the entry of this warp's first item under one chunk per item, issued
+    // alongside the count so both arrive in one round trip
+    const int64_t j0 = dw / a.chunks_per_row;
+    const int4 first = j0 < a.npad ? __ldcg(reinterpret_cast<const int4 *>(a.queue + (ph & 3) * a.npad + j0))
+                                   : make_int4(0, 0, 0, 0);
     if (leader) {
         a.ctl->step_begin[(t + 1) & 1] = rbase + n;
         a.ctl->cursor = rbase + n;
         a.ctl->qcnt[(ph + 2) & 3] = 0;  // the queue the next kernel fills after this one
         if (static_cast<uint64_t>(rbase) + n > a.rast_cap) atomicOr(&a.ctl->err, kErrRaster);
     }
-    if (a.format == SNN_RECORD_PACKED_I8) pipe_deliver_fmt<SNN_RECORD_PACKED_I8>(a, t, ph, dw, ndw, n, rbase);
-    else if (a.format == SNN_RECORD_PACKED_BF16) pipe_deliver_fmt<SNN_RECORD_PACKED_BF16>(a, t, ph, dw, ndw, n, rbase);
-    else pipe_deliver_fmt<SNN_RECORD_PLAIN9>(a, t, ph, dw, ndw, n, rbase);
+    if (a.format == SNN_RECORD_PACKED_I8) pipe_deliver_fmt<SNN_RECORD_PACKED_I8>(a, t, ph, dw, ndw, n, rbase, first);
+    else if (a.format == SNN_RECORD_PACKED_BF16) pipe_deliver_fmt<SNN_RECORD_PACKED_BF16>(a, t, ph, dw, ndw, n, rbase, first);
+    else pipe_deliver_fmt<SNN_RECORD_PLAIN9>(a, t, ph, dw, ndw, n, rbase, first);
 }
 
 // t_base is read before waiting on the previous kernel: within a graph replay it only
