@@ -40,6 +40,7 @@ TICKS_PER_STEP = 1024
 UPDATE_BYTES_PER_NEURON = 26   # U r/w 8 + I r/w 8 + R r/w 2 + ring slot read + clear 8
 EVENT_BYTES = 13               # tgt 4 + w 4 + delay 1 read + 4-byte ring reduction
 SPIKE_BYTES = 20               # row_ptr pair 16 + queue entry 4
+BLOCKED_EVENT_BYTES = 6        # blocked records: uint16 local target | delay + int32 weight
 WORKLOAD = "pd_full"
 METRIC = "synaptic events/s and real-time factor (full microcircuit, 1 GB300), % HBM roofline"
 
@@ -370,11 +371,13 @@ def run_gpu(args):
 
     # compressed synapse records on the same workload: step time and saturating delivery
     forms = {}
-    for fname, fmt in (("int8_pair", snn.RECORD_PACKED_I8), ("bf16", snn.RECORD_PACKED_BF16)):
+    for fname, fmt in (("int8_pair", snn.RECORD_PACKED_I8), ("bf16", snn.RECORD_PACKED_BF16),
+                       ("blocked6", snn.RECORD_BLOCKED6)):
         if fname not in args.forms:
             continue
+        feng = snn.ENGINE_DEFAULT if fmt == snn.RECORD_BLOCKED6 else engine
         fnet = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, seed, steps_per_graph=tps,
-                           raster_capacity=1 << 25, device=dev, engine=engine, record_format=fmt)
+                           raster_capacity=1 << 25, device=dev, engine=feng, record_format=fmt)
         fnet.step(args.warmup * tps)
         fnet.read_spikes()
         fe0 = fnet.info().events_read
@@ -390,10 +393,16 @@ def run_gpu(args):
         fnet.read_spikes()
         fev = fnet.info().events_read - fe0
         fsat = []
-        for nsp in args.saturating[-1:]:
-            ms_l = []
+        finfo = fnet.info()
+        blocked = fmt == snn.RECORD_BLOCKED6
+        for nsp in (args.saturating if blocked else args.saturating[-1:]):
+            ms_l, ev_l, nnz_l = [], [], []
+            ring = fnet.device_view("ring", torch.int32, 64 * int(fnet.layout().n_neurons_padded)) if blocked else None
             for r in range(args.saturating_reps + 2):
-                spk = torch.from_numpy(rng.integers(0, n, nsp).astype(np.int32)).to(dev)
+                spk_np = rng.integers(0, n, nsp).astype(np.int32)
+                spk = torch.from_numpy(spk_np).to(dev)
+                if blocked:
+                    ring.zero_()  # so that the entries this launch updates can be counted
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize(dev)
@@ -403,11 +412,27 @@ def run_gpu(args):
                 torch.cuda.synchronize(dev)
                 if r >= 2:
                     ms_l.append(e0.elapsed_time(e1))
-            fsat.append({"spikers": nsp, "ms": float(np.mean(ms_l)),
-                         "speedup_vs_plain": float([p_["ms"] for p_ in sat if p_["spikers"] == nsp][0] /
-                                                   np.mean(ms_l))})
-        finfo = fnet.info()
+                    ev_l.append(int(outdeg[spk_np].sum()))
+                    if blocked:
+                        nnz_l.append(int(torch.count_nonzero(ring).item()))
+            ms_avg, ev_avg = float(np.mean(ms_l)), float(np.mean(ev_l))
+            plain_ms = [p_["ms"] for p_ in sat if p_["spikers"] == nsp]
+            pt = {"spikers": nsp, "events": ev_avg, "ms": ms_avg, "events_per_s": ev_avg / (ms_avg * 1e-3),
+                  "speedup_vs_plain": float(plain_ms[0] / ms_avg) if plain_ms else None}
+            if blocked:
+                # the blocked kernel's own algorithmic bytes: 6 B records per event; per
+                # sender its list entry, row start and block-table row; 8 B (read + write)
+                # per ring entry it updates
+                nnz = float(np.mean(nnz_l))
+                nb = finfo.target_blocks
+                nbytes = BLOCKED_EVENT_BYTES * ev_avg + (12 + 2 * (nb + 1)) * nsp + 8 * nnz
+                pt.update({"ring_entries_updated": nnz, "bytes": nbytes, "gbs": nbytes / (ms_avg * 1e-3) / 1e9,
+                           "frac": nbytes / (ms_avg * 1e-3) / 1e9 / peak,
+                           "plain_equivalent_gbs": (EVENT_BYTES * ev_avg + SPIKE_BYTES * nsp) / (ms_avg * 1e-3) / 1e9})
+            fsat.append(pt)
         forms[fname] = {"bytes_per_synapse": finfo.bytes_per_synapse, "value": fev / fsecs,
+                        "engine": {snn.ENGINE_GRAPH: "graph", snn.ENGINE_PERSISTENT: "persistent",
+                                   snn.ENGINE_PIPELINED: "pipelined"}[finfo.engine],
                         "unit": "synaptic events/s", "rtf": fsecs / (args.form_steps * tps * model.dt_ms * 1e-3),
                         "steps": args.form_steps * tps, "delivery_saturating": fsat,
                         "note": "raster bit-exact with the oracle on the read-back weights; statistics vs FP64 "
@@ -515,7 +540,12 @@ def run_gpu(args):
                                 "traffic_20480": _recorded_traffic("k_deliver_list"),
                                 "note": "phase 2 alone over random senders of the same network "
                                         "(13 B per event + 20 B per sender); int32 red.add into the ring",
-                                "points": sat},
+                                "points": sat,
+                                "blocked6": {"kernel": "k_deliver_blocked",
+                                             "note": "one CTA per target block, sums in shared memory; frac on "
+                                                     "its own bytes (6 B per event, sender index, 8 B per ring "
+                                                     "entry updated)",
+                                             "points": forms.get("blocked6", {}).get("delivery_saturating")}},
         "clocks": clk.summary(), "build_s": build_s,
         "paper_context": {"fpga_best_rtf": 0.79, "hardware": "Intel Agilex 7 FPGA (horiz/multi/s)"},
     }
@@ -546,7 +576,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--saturating", type=int, nargs="*", default=[2048, 8192, 20480])
     ap.add_argument("--saturating-reps", type=int, default=5)
-    ap.add_argument("--forms", nargs="*", default=["int8_pair", "bf16"])
+    ap.add_argument("--forms", nargs="*", default=["int8_pair", "bf16", "blocked6"])
     ap.add_argument("--extra", nargs="*", default=["batched", "x4"])
     ap.add_argument("--batched-steps", type=int, default=20480)
     ap.add_argument("--x4-steps", type=int, default=10240)

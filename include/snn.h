@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define SNN_ABI_VERSION 1u
+#define SNN_ABI_VERSION 2u
 #define SNN_MAX_POPS 8       /* populations per circuit (the microcircuit has 8) */
 #define SNN_MAX_OVERRIDES 4  /* per-pair amplitude overrides (the doubled L4E->L23E pathway) */
 #define SNN_D_MAX 64         /* ring rows; delays are whole steps in [1, SNN_D_MAX-1] (§3.2) */
@@ -151,12 +151,22 @@ typedef struct snn_circuit {
  *                           step), -127, 127): 5 bytes;
  *   SNN_RECORD_PACKED_BF16: the same word and the current in pA as bfloat16 (round to
  *                           nearest even): 6 bytes.
+ *   SNN_RECORD_BLOCKED6:    target-blocked rows, exact.  The targets are cut into
+ *                           blocks of at most 768 consecutive neurons (boundaries at
+ *                           multiples of 32, balanced by in-degree, as many as fill whole
+ *                           waves of one CTA per SM of the device), each sender's row is
+ *                           grouped by block (delay order within a block), and a synapse
+ *                           is a uint16 (target - block start : 10 | delay : 6) plus the
+ *                           int32 weight: 6 bytes.  Delivery runs one CTA per block, which
+ *                           sums the block's events in shared memory before it adds them
+ *                           to the ring.  One circuit only; the engine is the graph engine.
  * Packed formats hold up to 2^20 neurons.  The dynamics are the plain ones applied to
- * the read-back weights; accumulation stays int32.
+ * the read-back weights (unchanged for SNN_RECORD_BLOCKED6); accumulation stays int32.
  */
 #define SNN_RECORD_PLAIN9 0
 #define SNN_RECORD_PACKED_I8 1
 #define SNN_RECORD_PACKED_BF16 2
+#define SNN_RECORD_BLOCKED6 3
 typedef struct snn_spec {
     uint32_t abi_version; /* must be SNN_ABI_VERSION */
     int32_t scale_n_permille;
@@ -194,12 +204,16 @@ typedef struct snn_sizes {
  * synapse arrays (rows sorted by delay, each padded to a multiple of 4 with entries
  * that deliver nothing); plain records: syn_tgt, syn_w int32[n_synapses_padded],
  * syn_delay uint8[...]; packed records: syn_tgt holds the uint32 words, syn_w the
- * int8 codes or bfloat16 currents, syn_delay is unused;
+ * int8 codes or bfloat16 currents, syn_delay is unused; blocked records: row_ptr holds
+ * unpadded row offsets, syn_tgt the uint16 records, syn_w the int32 weights, syn_delay
+ * the uint16 table [n_neurons][target_blocks + 1] of each row's block starts relative
+ * to its row start, and blocks the int32 block boundaries [target_blocks + 1];
  * rast_neuron, rast_step int32[raster_capacity]. */
 typedef struct snn_layout {
     uint64_t ctl, U, I, R, ring, row_ptr, syn_tgt, syn_w, syn_delay, rast_neuron, rast_step, params;
     int64_t n_neurons_padded;
     int64_t n_synapses_padded;
+    uint64_t blocks;
 } snn_layout;
 
 /* Constants and counters of a built network. */
@@ -228,7 +242,7 @@ typedef struct snn_info {
     int32_t n_circuits;            /* 1, or the batch size */
     int32_t schedule_ctas;         /* CTAs of the step (pipelined) or delivery (graph) kernel */
     int32_t schedule_delivery_warps; /* pipelined engine: delivery warps per CTA */
-    int32_t reserved2;
+    int32_t target_blocks;         /* SNN_RECORD_BLOCKED6: number of target blocks (else 0) */
     int32_t i8_base[SNN_MAX_POPS][SNN_MAX_POPS];  /* SNN_RECORD_PACKED_I8 read-back tables [source][target] */
     int32_t i8_step[SNN_MAX_POPS][SNN_MAX_POPS];
 } snn_info;
@@ -278,7 +292,8 @@ int snn_get_info(const snn_net *net, snn_info *out);
 
 /* Changes the launch schedule of the step kernels and re-captures the step graph
  * (waits for enqueued steps first): grid_ctas = CTAs of the step kernel (pipelined) or
- * of the delivery kernel (graph engine), delivery_warps = delivery warps per CTA
+ * of the delivery kernel (graph engine; SNN_RECORD_BLOCKED6 keeps one CTA per target
+ * block), delivery_warps = delivery warps per CTA
  * (pipelined, 1..8), steps_per_graph as in snn_spec; 0 keeps a value.  The schedule
  * never changes results, only speed (see paper_2405_02019_gb300.autotune).
  * Errors: SNN_EINVAL (out of range), SNN_ENOTSUP (persistent engine), SNN_ECUDA. */
@@ -321,7 +336,8 @@ int snn_load_state(snn_net *net, const void *host_buf, uint64_t bytes);
  * synapse of the senders spikers[0 .. n_spikers) (device int32 neuron ids, each
  * below n_neurons; repeats allowed) into the ring as spikes of step t, i.e.
  * W[(t + d) mod 64][target] += w, in one launch of `blocks` CTAs (0 = full
- * occupancy) on `cuda_stream`; returns without waiting.  The ring keeps the added
+ * occupancy; SNN_RECORD_BLOCKED6 always launches one CTA per target block) on
+ * `cuda_stream`; returns without waiting.  The ring keeps the added
  * input, so the simulated dynamics change accordingly.
  * Errors: SNN_EINVAL (null or negative arguments), SNN_ECUDA. */
 int snn_deliver_spikes(snn_net *net, const int32_t *spikers, int64_t n_spikers, int64_t t, int32_t blocks,

@@ -10,9 +10,9 @@ MAX_OVERRIDES = 4
 D_MAX = 64
 FX_SHIFT = 12
 POISSON_KMAX = 24
-ABI_VERSION = 1
+ABI_VERSION = 2
 ENGINE_DEFAULT, ENGINE_GRAPH, ENGINE_PERSISTENT, ENGINE_PIPELINED = 0, 1, 2, 3
-RECORD_PLAIN9, RECORD_PACKED_I8, RECORD_PACKED_BF16 = 0, 1, 2
+RECORD_PLAIN9, RECORD_PACKED_I8, RECORD_PACKED_BF16, RECORD_BLOCKED6 = 0, 1, 2, 3
 
 STATUS = {0: "SNN_OK", 1: "SNN_EINVAL", 2: "SNN_ENOMEM", 3: "SNN_ECUDA", 4: "SNN_EOVERFLOW",
           5: "SNN_ETIMEOUT", 6: "SNN_ESTATE", 7: "SNN_ENOTSUP"}
@@ -73,7 +73,7 @@ class snn_sizes(C.Structure):
 class snn_layout(C.Structure):
     _fields_ = [(f, C.c_uint64) for f in ("ctl", "U", "I", "R", "ring", "row_ptr", "syn_tgt", "syn_w",
                                           "syn_delay", "rast_neuron", "rast_step", "params")] + [
-        ("n_neurons_padded", C.c_int64), ("n_synapses_padded", C.c_int64)]
+        ("n_neurons_padded", C.c_int64), ("n_synapses_padded", C.c_int64), ("blocks", C.c_uint64)]
 
 
 class snn_info(C.Structure):
@@ -92,7 +92,7 @@ class snn_info(C.Structure):
         ("device_error", C.c_uint32), ("engine", C.c_int32),
         ("record_format", C.c_int32), ("bytes_per_synapse", C.c_int32),
         ("n_circuits", C.c_int32), ("schedule_ctas", C.c_int32), ("schedule_delivery_warps", C.c_int32),
-        ("reserved2", C.c_int32),
+        ("target_blocks", C.c_int32),
         ("i8_base", (C.c_int32 * MAX_POPS) * MAX_POPS), ("i8_step", (C.c_int32 * MAX_POPS) * MAX_POPS),
     ]
 

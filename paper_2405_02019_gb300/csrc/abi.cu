@@ -80,6 +80,13 @@ struct snn_net {
 
 namespace {
 
+// Phase 2 of graph-engine step t_base + k: blocked records have their own kernel.
+void launch_phase2(const snn_net *net, int k, cudaStream_t st)
+{
+    if (net->format == SNN_RECORD_BLOCKED6) snn::launch_deliver_blocked(net->args, nullptr, 0, 0, k, st);
+    else snn::launch_deliver(net->args, k, net->deliver_grid, st);
+}
+
 // m steps launched one by one, starting at step t0 (the device counter t_base equals t0).
 int launch_steps_direct(snn_net *net, int64_t m, cudaStream_t st, int64_t t0)
 {
@@ -89,7 +96,7 @@ int launch_steps_direct(snn_net *net, int64_t m, cudaStream_t st, int64_t t0)
             snn::launch_step(net->args, static_cast<int>(k), ph, net->step_grid, st);
         } else {
             snn::launch_update(net->args, static_cast<int>(k), net->update_grid, st);
-            snn::launch_deliver(net->args, static_cast<int>(k), net->deliver_grid, st);
+            launch_phase2(net, static_cast<int>(k), st);
         }
     }
     snn::launch_advance(net->args.ctl, m, st);
@@ -128,7 +135,7 @@ int capture_graph(snn_net *net)
             }
         } else {
             snn::launch_update(net->args, k, net->update_grid, net->capture_stream);
-            snn::launch_deliver(net->args, k, net->deliver_grid, net->capture_stream);
+            launch_phase2(net, k, net->capture_stream);
         }
     }
     snn::launch_advance(net->args.ctl, net->steps_per_graph, net->capture_stream);
@@ -265,7 +272,9 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         }
         snn::compute_constants(spec->model, net->c);
         snn::HostNetwork hn;
-        if (!snn::build_host_network(*spec, net->c, hn, why)) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, attr.device) != cudaSuccess) sms = 0;
+        if (!snn::build_host_network(*spec, net->c, hn, why, sms)) {
             delete net;
             return fail(SNN_EINVAL, why);
         }
@@ -327,6 +336,18 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
                     "tgt");
             cuda_ok(cudaMemcpyAsync(A + L.syn_w, hn.w.data(), 4 * net->n_syn_padded, cudaMemcpyHostToDevice, st), "w");
             cuda_ok(cudaMemcpyAsync(A + L.syn_d, hn.d.data(), net->n_syn_padded, cudaMemcpyHostToDevice, st), "d");
+        } else if (hn.format == SNN_RECORD_BLOCKED6) {
+            if (net->n_syn_padded > 0) {
+                cuda_ok(cudaMemcpyAsync(A + L.syn_tgt, hn.rec16.data(), 2 * net->n_syn_padded, cudaMemcpyHostToDevice,
+                                        st),
+                        "records");
+                cuda_ok(cudaMemcpyAsync(A + L.syn_w, hn.w.data(), 4 * net->n_syn_padded, cudaMemcpyHostToDevice, st),
+                        "w");
+            }
+            cuda_ok(cudaMemcpyAsync(A + L.syn_d, hn.seg.data(), 2 * hn.seg.size(), cudaMemcpyHostToDevice, st),
+                    "block table");
+            cuda_ok(cudaMemcpyAsync(A + L.blocks, hn.blk.data(), 4 * hn.blk.size(), cudaMemcpyHostToDevice, st),
+                    "blocks");
         } else if (net->n_syn_padded > 0) {
             cuda_ok(cudaMemcpyAsync(A + L.syn_tgt, hn.word.data(), 4 * net->n_syn_padded, cudaMemcpyHostToDevice, st),
                     "words");
@@ -362,6 +383,10 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         a.pop_id = A + L.pop_id;
         a.group_circuit = reinterpret_cast<const int32_t *>(A + L.group_circuit);
         a.circuits = reinterpret_cast<const snn::CircuitInfo *>(A + L.circuits);
+        a.blk_rec = reinterpret_cast<const uint16_t *>(A + L.syn_tgt);
+        a.blk_seg = reinterpret_cast<const uint16_t *>(A + L.syn_d);
+        a.blk_off = reinterpret_cast<const int32_t *>(A + L.blocks);
+        a.n_blocks = hn.format == SNN_RECORD_BLOCKED6 ? static_cast<int32_t>(hn.blk.size()) - 1 : 0;
         a.p11 = net->c.p11f;
         a.p21 = net->c.p21f;
         a.p22 = net->c.p22f;
@@ -385,7 +410,13 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         net->update_grid = snn::update_grid(net->n);
         net->deliver_grid = spec->deliver_blocks > 0 ? spec->deliver_blocks : 2 * net->num_sms;
         net->steps_per_graph = spec->steps_per_graph > 0 ? spec->steps_per_graph : 1000;
-        net->engine = spec->engine == SNN_ENGINE_DEFAULT ? SNN_ENGINE_PIPELINED : spec->engine;
+        net->engine = spec->engine != SNN_ENGINE_DEFAULT     ? spec->engine
+                      : net->format == SNN_RECORD_BLOCKED6 ? SNN_ENGINE_GRAPH
+                                                           : SNN_ENGINE_PIPELINED;
+        if (net->format == SNN_RECORD_BLOCKED6 && snn::prepare_blocked_kernel() != 0) {
+            snn_destroy(net);
+            return fail(SNN_ECUDA, "shared memory opt-in of the blocked delivery kernel failed");
+        }
         if (net->engine == SNN_ENGINE_PERSISTENT) {
             int coop = 0;
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, net->device);
@@ -501,7 +532,7 @@ int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *
             } else {
                 snn::launch_update(net->args, static_cast<int>(k), net->update_grid, st);
                 cudaEventRecord(ev[3 * k + 1], st);
-                snn::launch_deliver(net->args, static_cast<int>(k), net->deliver_grid, st);
+                launch_phase2(net, static_cast<int>(k), st);
             }
             cudaEventRecord(ev[3 * k + 2], st);
         }
@@ -624,6 +655,7 @@ int snn_get_info(const snn_net *net, snn_info *out)
     out->n_circuits = static_cast<int32_t>(net->circuits.size());
     out->schedule_ctas = net->engine == SNN_ENGINE_PIPELINED ? net->step_grid : net->deliver_grid;
     out->schedule_delivery_warps = net->engine == SNN_ENGINE_PIPELINED ? net->args.delivery_warps : 0;
+    out->target_blocks = net->args.n_blocks;
     std::memcpy(out->i8_base, net->i8_base, sizeof(out->i8_base));
     std::memcpy(out->i8_step, net->i8_step, sizeof(out->i8_step));
     return SNN_OK;
@@ -648,6 +680,7 @@ int snn_get_layout(const snn_net *net, snn_layout *out)
     out->rast_step = L.rast_t;
     out->n_neurons_padded = net->npad;
     out->n_synapses_padded = net->n_syn_padded;
+    out->blocks = L.blocks;
     return SNN_OK;
 }
 
@@ -791,6 +824,11 @@ int snn_deliver_spikes(snn_net *net, const int32_t *spikers, int64_t n_spikers, 
     if (!net || (n_spikers > 0 && !spikers)) return fail(SNN_EINVAL, "null argument");
     if (n_spikers < 0 || t < 0 || blocks < 0) return fail(SNN_EINVAL, "negative argument");
     if (n_spikers == 0) return SNN_OK;
+    if (net->format == SNN_RECORD_BLOCKED6) {
+        snn::launch_deliver_blocked(net->args, spikers, n_spikers, t, 0, cuda_stream);
+        SNN_CUDA_TRY(cudaGetLastError());
+        return SNN_OK;
+    }
     const int grid = blocks > 0 ? blocks : net->num_sms * snn::deliver_list_blocks_per_sm();
     snn::launch_deliver_list(net->args, spikers, n_spikers, t, grid, cuda_stream);
     SNN_CUDA_TRY(cudaGetLastError());

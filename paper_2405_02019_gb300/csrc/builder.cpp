@@ -215,10 +215,16 @@ bool validate_spec(const snn_spec &spec, std::string &why)
     if (spec.steps_per_graph < 0 || spec.steps_per_graph > 100000) return fail("steps_per_graph out of [0, 100000]");
     if (spec.deliver_blocks < 0 || spec.deliver_blocks > 65535) return fail("deliver_blocks out of range");
     if (spec.engine < SNN_ENGINE_DEFAULT || spec.engine > SNN_ENGINE_PIPELINED) return fail("unknown engine");
-    if (spec.record_format < SNN_RECORD_PLAIN9 || spec.record_format > SNN_RECORD_PACKED_BF16)
+    if (spec.record_format < SNN_RECORD_PLAIN9 || spec.record_format > SNN_RECORD_BLOCKED6)
         return fail("unknown record_format");
-    if (spec.record_format != SNN_RECORD_PLAIN9 && count_neurons(spec) > kPackedMaxNeurons)
+    if ((spec.record_format == SNN_RECORD_PACKED_I8 || spec.record_format == SNN_RECORD_PACKED_BF16) &&
+        count_neurons(spec) > kPackedMaxNeurons)
         return fail("packed records hold at most 2^20 neurons");
+    if (spec.record_format == SNN_RECORD_BLOCKED6) {
+        if (spec.n_circuits > 0) return fail("blocked records take one circuit");
+        if (spec.engine == SNN_ENGINE_PERSISTENT || spec.engine == SNN_ENGINE_PIPELINED)
+            return fail("blocked records run on the graph engine");
+    }
     if (spec.n_circuits < 0 || spec.n_circuits > SNN_MAX_CIRCUITS) return fail("n_circuits out of [0, SNN_MAX_CIRCUITS]");
     if (spec.n_circuits > 0 && !spec.circuits) return fail("circuits missing");
     if (spec.n_circuits > 0 && spec.custom) return fail("a custom network cannot be batched");
@@ -289,9 +295,19 @@ Layout make_layout(const snn_spec &spec)
     L.row_ptr = o; o = up(o + 8 * (n + 5));  // 4 spare entries: quads read row_ptr[i0 .. i0+4]
     const int fmt = spec.record_format;
     const uint64_t wbytes = fmt == SNN_RECORD_PACKED_I8 ? 1 : fmt == SNN_RECORD_PACKED_BF16 ? 2 : 4;
-    L.syn_tgt = o; o = up(o + 4 * L.syn_padded_max);
-    L.syn_w = o; o = up(o + wbytes * L.syn_padded_max + 16);
-    L.syn_d = o; o = up(o + (fmt == SNN_RECORD_PLAIN9 ? L.syn_padded_max : 0) + 16);
+    if (fmt == SNN_RECORD_BLOCKED6) {
+        // rows of quad-padded block segments: uint16 records, int32 weights, the per-row
+        // block table (a nonempty segment gains at most kBlockQuad - 1 pad entries)
+        L.syn_padded_max = s + (kBlockQuad - 1) * std::min<int64_t>(s, n * int64_t{max_target_blocks(n)});
+        L.syn_tgt = o; o = up(o + 2 * L.syn_padded_max + 16);
+        L.syn_w = o; o = up(o + 4 * L.syn_padded_max + 16);
+        L.syn_d = o; o = up(o + 2 * uint64_t(n) * (max_target_blocks(n) + 1) + 16);
+    } else {
+        L.syn_tgt = o; o = up(o + 4 * L.syn_padded_max);
+        L.syn_w = o; o = up(o + wbytes * L.syn_padded_max + 16);
+        L.syn_d = o; o = up(o + (fmt == SNN_RECORD_PLAIN9 ? L.syn_padded_max : 0) + 16);
+    }
+    L.blocks = o; o = up(o + 4 * (fmt == SNN_RECORD_BLOCKED6 ? max_target_blocks(n) + 1 : 1));
     L.rast_nrn = o; o = up(o + 4 * L.rast_cap);
     L.rast_t = o; o = up(o + 4 * L.rast_cap);
     L.U2 = o; o = up(o + 4 * L.npad);
@@ -457,13 +473,135 @@ void pack_records(HostNetwork &net, int /*n_pops*/, int nthreads)
 }  // namespace
 
 namespace {
-bool build_one(const snn_spec &spec, const Constants &c, HostNetwork &net, std::string &why);
+
+// Target blocks of the blocked format: boundaries at multiples of kBlockAlign, no block
+// wider than kBlockMaxWidth.  One CTA per SM delivers into a block, so the launch takes
+// as long as its heaviest block: the cut minimises the largest in-degree sum of a block
+// (the events a block receives from uniformly drawn senders) for a block count of at
+// most `budget`.  For a bound L, cutting greedily wherever the next group of kBlockAlign
+// targets would pass L or the width limit gives the fewest blocks; the smallest L whose
+// greedy cut fits the budget is found by bisection.
+std::vector<int32_t> cut_blocks(const std::vector<int64_t> &grp, int64_t n, int64_t L)
+{
+    std::vector<int32_t> blk{0};
+    int64_t load = 0;
+    for (size_t g = 0; g < grp.size(); ++g) {
+        const int64_t j = static_cast<int64_t>(g) * kBlockAlign;
+        if (j > blk.back() && (j - blk.back() + kBlockAlign > kBlockMaxWidth || load + grp[g] > L)) {
+            blk.push_back(static_cast<int32_t>(j));
+            load = 0;
+        }
+        load += grp[g];
+    }
+    blk.push_back(static_cast<int32_t>(n));
+    return blk;
 }
 
-bool build_host_network(const snn_spec &spec, const Constants &c, HostNetwork &net, std::string &why)
+// Budget: the fewest whole waves of `num_sms` CTAs that the width limit allows, but no
+// more blocks than leave segments of ~16 synapses on average (shorter ones are mostly
+// quad padding) and no more than the layout holds; num_sms = 0 asks for n / 512 blocks.
+std::vector<int32_t> target_blocks(const std::vector<int64_t> &indeg, int64_t n, int num_sms)
+{
+    std::vector<int64_t> grp((n + kBlockAlign - 1) / kBlockAlign, 0);
+    int64_t total = 0, gmax = 0;
+    for (int64_t j = 0; j < n; ++j) grp[j / kBlockAlign] += indeg[j];
+    for (int64_t g : grp) {
+        total += g;
+        gmax = std::max(gmax, g);
+    }
+    const int64_t min_blocks = n / (kBlockMaxWidth - kBlockAlign) + 1;
+    int64_t budget;
+    if (num_sms > 0) {
+        budget = (min_blocks + num_sms - 1) / num_sms * num_sms;
+        budget = std::min(budget, std::max(min_blocks, total / (16 * std::max<int64_t>(n, 1))));
+    } else {
+        budget = std::max(min_blocks, (n + kBlockAvgWidth - 1) / kBlockAvgWidth);
+    }
+    budget = std::min<int64_t>(budget, max_target_blocks(n));
+    int64_t lo = gmax, hi = std::max(gmax, total);
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (static_cast<int64_t>(cut_blocks(grp, n, mid).size()) - 1 <= budget) hi = mid;
+        else lo = mid + 1;
+    }
+    return cut_blocks(grp, n, lo);
+}
+
+// Regroups the delay-sorted rows into block-grouped rows (delay order kept inside a
+// block) and encodes each synapse as (local target | delay << 10).  Every (row, block)
+// segment is padded to a multiple of kBlockQuad records with zero-weight entries
+// (local target 0, delay 1), so that a segment is a whole number of aligned quads.
+bool pack_blocked(HostNetwork &net, int nthreads, int num_sms, std::string &why)
+{
+    const int64_t n = net.n;
+    std::vector<int64_t> indeg(n, 0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t s = net.row_ptr[i], e = net.row_ptr[i] + net.out_degree[i]; s < e; ++s) ++indeg[net.tgt[s]];
+    net.blk = target_blocks(indeg, n, num_sms);
+    const int B = static_cast<int>(net.blk.size()) - 1;
+    if (B > max_target_blocks(n)) {
+        why = "internal: more target blocks than the layout bound";
+        return false;
+    }
+    std::vector<int32_t> block_of(n);
+    for (int b = 0; b < B; ++b)
+        for (int64_t j = net.blk[b]; j < net.blk[b + 1]; ++j) block_of[j] = b;
+    // padded segment lengths give the row lengths
+    net.seg.assign(static_cast<size_t>(n) * (B + 1), 0);
+    std::vector<int64_t> rp(n + 1, 0);
+    bool too_long = false;
+    parallel_for(nthreads, n, [&](int, int64_t lo, int64_t hi) {
+        std::vector<int64_t> cnt(B);
+        for (int64_t i = lo; i < hi; ++i) {
+            std::fill(cnt.begin(), cnt.end(), 0);
+            for (int64_t s = net.row_ptr[i], e = s + net.out_degree[i]; s < e; ++s) ++cnt[block_of[net.tgt[s]]];
+            uint16_t *sg = &net.seg[static_cast<size_t>(i) * (B + 1)];
+            int64_t run = 0;
+            for (int b = 0; b < B; ++b) {
+                sg[b] = static_cast<uint16_t>(run);
+                run += (cnt[b] + kBlockQuad - 1) / kBlockQuad * kBlockQuad;
+                if (run > 65535) too_long = true;
+            }
+            sg[B] = static_cast<uint16_t>(run);
+            rp[i + 1] = run;
+        }
+    });
+    if (too_long) {
+        why = "blocked records hold rows of at most 65535 padded synapses";
+        return false;
+    }
+    for (int64_t i = 0; i < n; ++i) rp[i + 1] += rp[i];
+    const int64_t S = rp[n];
+    net.rec16.assign(S, static_cast<uint16_t>(1u << kBlockLocalBits));
+    std::vector<int32_t> w(S, 0);
+    parallel_for(nthreads, n, [&](int, int64_t lo, int64_t hi) {
+        std::vector<int64_t> pos(B);
+        for (int64_t i = lo; i < hi; ++i) {
+            const uint16_t *sg = &net.seg[static_cast<size_t>(i) * (B + 1)];
+            for (int b = 0; b < B; ++b) pos[b] = rp[i] + sg[b];
+            for (int64_t s = net.row_ptr[i], e = s + net.out_degree[i]; s < e; ++s) {
+                const int b = block_of[net.tgt[s]];
+                const int64_t dst = pos[b]++;
+                net.rec16[dst] = static_cast<uint16_t>((net.tgt[s] - net.blk[b]) | (int32_t{net.d[s]} << kBlockLocalBits));
+                w[dst] = net.w[s];
+            }
+        }
+    });
+    net.row_ptr = std::move(rp);
+    net.w = std::move(w);
+    net.n_syn_padded = S;
+    std::vector<int32_t>().swap(net.tgt);
+    std::vector<uint8_t>().swap(net.d);
+    return true;
+}
+
+bool build_one(const snn_spec &spec, const Constants &c, HostNetwork &net, std::string &why, int num_sms);
+}
+
+bool build_host_network(const snn_spec &spec, const Constants &c, HostNetwork &net, std::string &why, int num_sms)
 {
     if (spec.n_circuits <= 0) {
-        if (!build_one(spec, c, net, why)) return false;
+        if (!build_one(spec, c, net, why, num_sms)) return false;
         net.circuits = {CircuitInfo{0, net.n, spec.seed, 0}};
         return true;
     }
@@ -487,7 +625,7 @@ bool build_host_network(const snn_spec &spec, const Constants &c, HostNetwork &n
         snn_spec one = circuit_spec(spec, ci);
         one.record_format = SNN_RECORD_PLAIN9;
         HostNetwork h;
-        if (!build_one(one, c, h, why)) return false;
+        if (!build_one(one, c, h, why, 0)) return false;
         if (ci > 0) base = (all.n + 127) / 128 * 128;
         // neurons: gap (inert) then the circuit
         const int64_t syn_base = all.row_ptr.empty() ? 0 : all.row_ptr.back();
@@ -525,7 +663,7 @@ bool build_host_network(const snn_spec &spec, const Constants &c, HostNetwork &n
 
 namespace {
 
-bool build_one(const snn_spec &spec, const Constants &c, HostNetwork &net, std::string &why)
+bool build_one(const snn_spec &spec, const Constants &c, HostNetwork &net, std::string &why, int num_sms)
 {
     const int nthreads = resolve_threads(spec.n_threads);
     const snn_model &m = spec.model;
@@ -660,6 +798,7 @@ bool build_one(const snn_spec &spec, const Constants &c, HostNetwork &net, std::
     for (int b = 0; b < m.n_pops; ++b)
         for (int64_t i = net.pop_off[b]; i < net.pop_off[b + 1]; ++i) net.pop_id[i] = static_cast<uint8_t>(b);
     net.format = spec.record_format;
+    if (net.format == SNN_RECORD_BLOCKED6) return pack_blocked(net, nthreads, num_sms, why);
     if (net.format != SNN_RECORD_PLAIN9) pack_records(net, spec.model.n_pops, nthreads);
     return true;
 }

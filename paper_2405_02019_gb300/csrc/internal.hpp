@@ -77,7 +77,26 @@ constexpr int kWordDelayShift = 20;
 constexpr int kWordPopShift = 26;
 constexpr uint32_t kWordPad = 1u << 31;
 constexpr int64_t kPackedMaxNeurons = int64_t{1} << kWordTargetBits;
-inline int record_bytes(int format) { return format == SNN_RECORD_PACKED_I8 ? 5 : format == SNN_RECORD_PACKED_BF16 ? 6 : 9; }
+inline int record_bytes(int format)
+{
+    return format == SNN_RECORD_PACKED_I8 ? 5 : format == SNN_RECORD_PACKED_BF16 || format == SNN_RECORD_BLOCKED6 ? 6 : 9;
+}
+
+// Blocked records: target blocks and the delivery kernel that owns one block per CTA.
+constexpr int kBlockLocalBits = 10;          // record = local target | delay << 10
+constexpr int kBlockMaxWidth = 768;          // targets per block (shared-memory bins [64][768])
+constexpr int kBlockAvgWidth = 512;          // sets the number of in-degree quotas
+constexpr int kBlockAlign = 32;              // block boundaries are multiples of 32
+constexpr int kBlockQuad = 4;                // (row, block) segments are whole quads of records
+constexpr int kBlockedThreads = 512;
+constexpr int kBlockedBatch = 2048;          // senders staged per pass
+constexpr int kBlockedWindow = 8192;        // quads of a pass mapped to their segments at once
+constexpr int kBlockedRounds = 8;            // quads in flight per lane (32 per round and warp)
+constexpr int64_t kBlockedAggregateMin = 64; // fewer senders: reduce straight into the ring
+inline int max_target_blocks(int64_t n)
+{
+    return static_cast<int>((n + kBlockAvgWidth - 1) / kBlockAvgWidth + n / (kBlockMaxWidth - kBlockAlign) + 2);
+}
 
 // Kernel arguments (by value; small).
 struct StepArgs {
@@ -118,6 +137,11 @@ struct StepArgs {
     const uint8_t *pop_id;        // population of every neuron [npad]
     const int32_t *group_circuit; // circuit of every group of 128 neurons [npad / 128]
     const CircuitInfo *circuits;  // [n_circuits]
+    const uint16_t *blk_rec;      // blocked records: local target | delay << 10
+    const uint16_t *blk_seg;      // blocked records: [n][n_blocks + 1] block starts within each row
+    const int32_t *blk_off;       // blocked records: block boundaries [n_blocks + 1]
+    int32_t n_blocks;
+    int32_t pad4;
 };
 
 // Host constants of one model (§2.2).
@@ -150,12 +174,15 @@ struct HostNetwork {
     std::vector<int32_t> w;
     std::vector<uint8_t> d;
     std::vector<float> u0;
+    std::vector<int32_t> blk;      // blocked records: block boundaries
+    std::vector<uint16_t> rec16;   // blocked records: local target | delay << 10
+    std::vector<uint16_t> seg;     // blocked records: [n][blocks + 1] block starts per row
 };
 
 // Arena layout for a spec.
 struct Layout {
     uint64_t ctl, tables, U, I, R, ring, row_ptr, syn_tgt, syn_w, syn_d, rast_nrn, rast_t, U2, R2, queue, qcount, pop_id,
-        group_circuit, circuits, total;
+        group_circuit, circuits, blocks, total;
     int64_t npad, syn_padded_max, rast_cap;
 };
 
@@ -167,7 +194,9 @@ int64_t pair_count(const snn_model &m, int32_t scale_n, int32_t scale_k, int tar
 int64_t count_neurons(const snn_spec &spec);
 int64_t count_synapses(const snn_spec &spec);
 Layout make_layout(const snn_spec &spec);
-bool build_host_network(const snn_spec &spec, const Constants &c, HostNetwork &net, std::string &why);
+// num_sms: SMs of the device (blocked records size their target blocks to it; 0 = no limit)
+bool build_host_network(const snn_spec &spec, const Constants &c, HostNetwork &net, std::string &why,
+                        int num_sms = 0);
 int resolve_threads(int32_t requested);
 
 // kernels.cu
@@ -175,6 +204,10 @@ void launch_update(const StepArgs &a, int k, int grid, void *stream);
 void launch_deliver(const StepArgs &a, int k, int grid, void *stream);
 void launch_advance(Ctl *ctl, int64_t m, void *stream);
 void launch_deliver_list(const StepArgs &a, const int32_t *list, int64_t n, int64_t t, int grid, void *stream);
+// blocked records: one CTA per target block; list == nullptr delivers step t_base + k's
+// spikes from the raster (graph engine), else list[0 .. n) as spikes of step t
+int prepare_blocked_kernel();
+void launch_deliver_blocked(const StepArgs &a, const int32_t *list, int64_t n, int64_t t, int k, void *stream);
 int deliver_list_blocks_per_sm();
 int update_grid(int64_t n);
 int persistent_blocks_per_sm();

@@ -658,6 +658,213 @@ __global__ void __launch_bounds__(kStepMaxThreads, 2) k_prime(const StepArgs a)
         pipe_quad(a, t, -1, g, g * 32 + (threadIdx.x & 31) < nquads, false, false);
 }
 
+
+// ---------------------------------------------------------------------------------
+// Blocked records: phase 2 with one CTA per block of consecutive targets.
+//
+// Each sender's row is grouped by target block, so CTA p reads, for every sender, only
+// the segment that lands in its block (row_ptr[s] + seg[s][p] .. + seg[s][p + 1]); a
+// segment is a whole number of aligned quads of records (zero-weight padding).  Per
+// pass the CTA stages up to kBlockedBatch senders' segments (first quad, quad count and
+// the exclusive prefix of the counts), which makes the pass one stream of quads.  The
+// stream is taken in windows of kBlockedWindow quads; for a window every quad's segment
+// is written into a shared table, after which the quads are independent work: warp w
+// takes rounds w, w + 16, ... of 32 consecutive quads, kBlockedRounds rounds at a time,
+// issuing all their loads (8 bytes of records, 16 of weights per quad) before adding
+// any.  With many senders the weights are summed per (delay, local target) in shared
+// memory and each nonzero sum is added to its ring entry once at the end; only this CTA
+// writes these ring columns during the launch, so that final add is a plain
+// read-modify-write.  With few senders the weights go straight to the ring as
+// reductions.  Integer addition makes both orders give the same ring.
+// ---------------------------------------------------------------------------------
+
+constexpr int kBlockedWarps = kBlockedThreads / 32;
+constexpr size_t kBlockedBinsBytes = sizeof(int32_t) * kDMax * kBlockMaxWidth;
+constexpr size_t kBlockedSmemBytes = kBlockedBinsBytes + sizeof(uint32_t) * kBlockedBatch +
+                                     sizeof(int32_t) * (kBlockedBatch + kBlockedWarps) +
+                                     sizeof(uint16_t) * kBlockedWindow;
+static_assert(kBlockedSmemBytes <= 232448, "blocked delivery: shared memory above the 227 KB opt-in limit");
+static_assert(sizeof(uint16_t) * kBlockedWindow >= sizeof(int32_t) * kBlockedThreads, "scan output must fit the table");
+static_assert(kBlockedBatch % kBlockedThreads == 0 && kBlockedBatch <= 65536, "staged senders per thread / table");
+
+template <bool kAggregate>
+__device__ __forceinline__ void blocked_apply(const StepArgs &a, int32_t *bins, int64_t t, int32_t base, uint32_t rec,
+                                              int32_t w)
+{
+    if (w == 0) return;  // padding (adding zero changes nothing)
+    const int d = static_cast<int>(rec >> kBlockLocalBits);
+    const int lt = static_cast<int>(rec & ((1u << kBlockLocalBits) - 1));
+    if (kAggregate) atomicAdd(bins + d * kBlockMaxWidth + lt, w);
+    else red_add_s32(a.ring + ((t + d) & kDMask) * a.npad + base + lt, w);
+}
+
+// Exclusive prefix sum of one value per thread over the CTA into out[threadIdx.x];
+// returns the total.
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *out, int32_t *warp_sums)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = lane < kBlockedWarps ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kBlockedWarps) warp_sums[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    out[threadIdx.x] = (warp > 0 ? warp_sums[warp - 1] : 0) + x - v;
+    return warp_sums[kBlockedWarps - 1];
+}
+
+// Quads [w0, w1) of the staged stream; seg_of[e - w0] is the segment of quad e.
+template <bool kAggregate>
+__device__ __forceinline__ void blocked_window(const StepArgs &a, int32_t *bins, const uint32_t *seg_q,
+                                               const int32_t *pfx, const uint16_t *seg_of, int32_t w0, int32_t w1,
+                                               int64_t t, int32_t base)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint2 *recq = reinterpret_cast<const uint2 *>(a.blk_rec);
+    const int4 *wq = reinterpret_cast<const int4 *>(a.syn_w);
+    // round k of a step is quads e0 + 32 * (warp + kBlockedWarps * k) + lane: the warps
+    // of the CTA interleave, so that a window's rounds spread evenly over them
+    for (int32_t e0 = w0; e0 < w1; e0 += kBlockedThreads * kBlockedRounds) {
+        uint2 rec[kBlockedRounds];
+        int4 w[kBlockedRounds];
+#pragma unroll
+        for (int k = 0; k < kBlockedRounds; ++k) {
+            const int32_t e = e0 + 32 * (warp + kBlockedWarps * k) + lane;
+            if (e < w1) {
+                const int j = seg_of[e - w0];
+                const int64_t q = static_cast<int64_t>(seg_q[j]) + (e - pfx[j]);
+                rec[k] = __ldcs(recq + q);
+                w[k] = __ldcs(wq + q);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kBlockedRounds; ++k) {
+            if (e0 + 32 * (warp + kBlockedWarps * k) + lane >= w1) continue;
+            blocked_apply<kAggregate>(a, bins, t, base, rec[k].x & 0xffffu, w[k].x);
+            blocked_apply<kAggregate>(a, bins, t, base, rec[k].x >> 16, w[k].y);
+            blocked_apply<kAggregate>(a, bins, t, base, rec[k].y & 0xffffu, w[k].z);
+            blocked_apply<kAggregate>(a, bins, t, base, rec[k].y >> 16, w[k].w);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBlockedThreads, 1)
+    k_deliver_blocked(const StepArgs a, const int32_t *list, int64_t n_list, int64_t t_list, int k)
+{
+    extern __shared__ int4 smem4[];
+    int32_t *bins = reinterpret_cast<int32_t *>(smem4);                               // [64][kBlockMaxWidth]
+    uint32_t *seg_q = reinterpret_cast<uint32_t *>(bins + kDMax * kBlockMaxWidth);  // first quad
+    int32_t *pfx = reinterpret_cast<int32_t *>(seg_q + kBlockedBatch);              // [kBlockedBatch]
+    int32_t *warp_sums = pfx + kBlockedBatch + 1;
+    uint16_t *seg_of = reinterpret_cast<uint16_t *>(warp_sums + kBlockedWarps);     // [kBlockedWindow]
+
+    int64_t t;
+    const int32_t *spk;
+    int64_t nspk;
+    if (list != nullptr) {
+        t = t_list;
+        spk = list;
+        nspk = n_list;
+    } else {
+        // graph engine: the spikes step t appended to the raster
+        t = a.ctl->t_base + k;
+        const uint32_t cur = a.ctl->cursor;
+        const uint32_t begin = a.ctl->step_begin[t & 1];
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->step_begin[(t + 1) & 1] = cur;
+        const uint32_t end = cur < a.rast_cap ? cur : a.rast_cap;
+        spk = a.rast_nrn + begin;
+        nspk = end > begin ? static_cast<int64_t>(end - begin) : 0;
+    }
+    if (nspk == 0) return;
+
+    const int p = blockIdx.x;
+    const int32_t base = a.blk_off[p];
+    const int32_t width = a.blk_off[p + 1] - base;
+    const bool aggregate = nspk >= kBlockedAggregateMin;
+    const int tid = threadIdx.x;
+    const int64_t stride = a.n_blocks + 1;
+    constexpr int kPer = kBlockedBatch / kBlockedThreads;  // senders staged per thread
+
+    if (aggregate)
+        for (int j = tid; j < kDMax * kBlockMaxWidth / 4; j += kBlockedThreads) smem4[j] = make_int4(0, 0, 0, 0);
+
+    for (int64_t b0 = 0; b0 < nspk; b0 += kBlockedBatch) {
+        const int nb = static_cast<int>(nspk - b0 < kBlockedBatch ? nspk - b0 : kBlockedBatch);
+        // thread tid stages senders tid * kPer .. + kPer (consecutive, for the scan)
+        int32_t nq[kPer];
+        int32_t mine = 0;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int j = tid * kPer + i;
+            nq[i] = 0;
+            if (j < nb) {
+                const int32_t s = __ldcg(spk + b0 + j);
+                const uint16_t *sg = a.blk_seg + static_cast<int64_t>(s) * stride + p;
+                const int32_t o0 = __ldg(sg), o1 = __ldg(sg + 1);
+                seg_q[j] = static_cast<uint32_t>((__ldg(a.row_ptr + s) + o0) / kBlockQuad);
+                nq[i] = (o1 - o0) / kBlockQuad;
+            }
+            mine += nq[i];
+        }
+        // the window table is idle here: it holds the scan's per-thread output
+        int32_t *scan_out = reinterpret_cast<int32_t *>(seg_of);
+        const int32_t total = block_exclusive_scan(mine, scan_out, warp_sums);
+        {
+            int32_t run = scan_out[tid];
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) {
+                pfx[tid * kPer + i] = run;
+                run += nq[i];
+            }
+        }
+        __syncthreads();
+        for (int32_t w0 = 0; w0 < total; w0 += kBlockedWindow) {
+            const int32_t w1 = total - w0 < kBlockedWindow ? total : w0 + kBlockedWindow;
+            // segment of every quad of the window
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) {
+                const int j = tid * kPer + i;
+                if (j >= nb) break;
+                const int32_t lo = max(pfx[j], w0), hi = min(pfx[j] + nq[i], w1);
+                for (int32_t e = lo; e < hi; ++e) seg_of[e - w0] = static_cast<uint16_t>(j);
+            }
+            __syncthreads();
+            if (aggregate) blocked_window<true>(a, bins, seg_q, pfx, seg_of, w0, w1, t, base);
+            else blocked_window<false>(a, bins, seg_q, pfx, seg_of, w0, w1, t, base);
+            __syncthreads();  // the table is rebuilt for the next window
+        }
+    }
+    if (!aggregate) return;
+    // add the sums of delays 1..63 to their ring rows; width is a multiple of 4 except
+    // for the last block, whose extra columns lie inside the padded ring row (sum 0)
+    const int w4 = (width + 3) >> 2;
+    for (int q = tid; q < (kDMax - 1) * w4; q += kBlockedThreads) {
+        const int d = 1 + q / w4;
+        const int c4 = q - (d - 1) * w4;
+        const int4 v = smem4[(d * kBlockMaxWidth) / 4 + c4];
+        if ((v.x | v.y | v.z | v.w) == 0) continue;
+        int4 *dst = reinterpret_cast<int4 *>(a.ring + ((t + d) & kDMask) * a.npad + base) + c4;
+        int4 o = __ldcg(dst);
+        o.x = static_cast<int32_t>(static_cast<uint32_t>(o.x) + static_cast<uint32_t>(v.x));
+        o.y = static_cast<int32_t>(static_cast<uint32_t>(o.y) + static_cast<uint32_t>(v.y));
+        o.z = static_cast<int32_t>(static_cast<uint32_t>(o.z) + static_cast<uint32_t>(v.z));
+        o.w = static_cast<int32_t>(static_cast<uint32_t>(o.w) + static_cast<uint32_t>(v.w));
+        __stcg(dst, o);
+    }
+}
+
 }  // namespace
 
 int step_grid(int num_sms) { return num_sms; }
@@ -707,6 +914,18 @@ void launch_deliver(const StepArgs &a, int k, int grid, void *stream)
 void launch_deliver_list(const StepArgs &a, const int32_t *list, int64_t n, int64_t t, int grid, void *stream)
 {
     k_deliver_list<<<grid, kDeliverThreads, 0, static_cast<cudaStream_t>(stream)>>>(a, list, n, t);
+}
+
+int prepare_blocked_kernel()
+{
+    return static_cast<int>(cudaFuncSetAttribute(k_deliver_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(kBlockedSmemBytes)));
+}
+
+void launch_deliver_blocked(const StepArgs &a, const int32_t *list, int64_t n, int64_t t, int k, void *stream)
+{
+    k_deliver_blocked<<<a.n_blocks, kBlockedThreads, kBlockedSmemBytes, static_cast<cudaStream_t>(stream)>>>(a, list, n,
+                                                                                                            t, k);
 }
 
 int deliver_list_blocks_per_sm()

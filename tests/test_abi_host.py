@@ -108,3 +108,26 @@ def test_product_path_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cpp", ".hpp", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "oracle.c" not in text and "liboracle" not in text, f
+
+
+def test_blocked_records_sizes_and_rules(lib):
+    """Blocked records: 6 bytes per synapse plus the per-row block table; one circuit
+    on the graph engine (the default resolves to it); other engines and batches are
+    rejected on the host."""
+    m = workload.microcircuit_model()
+    plain = snn.snn_query_sizes(snn._Spec(m, 1000, 1000, 1).spec)
+    blk = snn.snn_query_sizes(snn._Spec(m, 1000, 1000, 1, record_format=snn.RECORD_BLOCKED6).spec)
+    n, S = blk.n_neurons, blk.n_synapses
+    bmax = (n + 511) // 512 + n // 736 + 2
+    # every nonempty (row, block) segment is padded to a whole quad of records
+    assert S == plain.n_synapses and blk.n_synapses_padded_max == S + 3 * min(S, n * bmax)
+    assert blk.arena_bytes < plain.arena_bytes
+    for engine in (snn.ENGINE_PIPELINED, snn.ENGINE_PERSISTENT):
+        spec = snn._Spec(m, 100, 100, 1, record_format=snn.RECORD_BLOCKED6, engine=engine).spec
+        with pytest.raises(snn.SnnError):
+            snn.snn_query_sizes(spec)
+    spec = snn._Spec(m, record_format=snn.RECORD_BLOCKED6, circuits=[(100, 100, 1), (200, 200, 2)]).spec
+    with pytest.raises(snn.SnnError):
+        snn.snn_query_sizes(spec)
+    spec = snn._Spec(m, 100, 100, 1, record_format=snn.RECORD_BLOCKED6, engine=snn.ENGINE_GRAPH).spec
+    assert snn.snn_query_sizes(spec).n_neurons == 7718

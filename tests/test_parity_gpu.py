@@ -603,6 +603,221 @@ def test_static_step_rejects_packed(model):
 BATCH = [(20, 40, 5), (35, 10, 6), (13, 50, 7), (50, 50, 8), (1, 1, 9)]
 
 
+# ------------------------------------------------------------ blocked records
+
+BLK = snn.RECORD_BLOCKED6
+
+
+def _check_blocked_structure(net, onet, rows=None):
+    """Decodes the blocked records in the arena and compares them with the oracle's
+    network: every synapse (rows=None) or the given rows exactly plus global sums.
+    Zero weights mark the padding that ends every (row, block) segment on a quad."""
+    info = net.info()
+    n, B, S = net.n_neurons, info.target_blocks, info.n_synapses
+    SP = int(net.layout().n_synapses_padded)
+    blk = net.device_view("blocks", torch.int32, B + 1).cpu().numpy().astype(np.int64)
+    rp = net.device_view("row_ptr", torch.int64, n + 1).cpu().numpy()
+    seg = net.device_view("syn_delay", torch.int16, n * (B + 1)).cpu().numpy().view(np.uint16)
+    seg = seg.reshape(n, B + 1).astype(np.int64)
+    rec = net.device_view("syn_tgt", torch.int16, SP).cpu().numpy().view(np.uint16)
+    w = net.device_view("syn_w", torch.int32, SP).cpu().numpy()
+    assert blk[0] == 0 and blk[-1] == n and np.all(np.diff(blk) > 0)
+    assert np.all(blk[1:-1] % 32 == 0) and np.all(np.diff(blk) <= 768)
+    lens = np.diff(onet.row_ptr)
+    plen = np.diff(rp)
+    assert rp[0] == 0 and rp[-1] == SP and np.all(plen >= lens) and np.all(rp % 4 == 0)
+    assert np.all(seg[:, 0] == 0) and np.array_equal(seg[:, -1], plen) and np.all(np.diff(seg, axis=1) >= 0)
+    assert np.all(seg % 4 == 0)
+    real = w != 0
+    assert int(real.sum()) == S and np.all(rec[~real] == 1024)
+    # block of every entry, segment starts, then chunked decode
+    bid = np.repeat(np.tile(np.arange(B, dtype=np.int16), n), np.diff(seg, axis=1).ravel())
+    start = np.zeros(SP + 1, bool)
+    start[(rp[:-1, None] + seg[:, :-1]).ravel()] = True
+    width = np.diff(blk)
+    sums = np.zeros(3, np.int64)
+    for c0 in range(0, SP, 1 << 24):
+        c1 = min(SP, c0 + (1 << 24))
+        r = rec[c0:c1].astype(np.int64)
+        b = bid[c0:c1].astype(np.int64)
+        rl = real[c0:c1]
+        local, d = r & 1023, r >> 10
+        assert np.all(local < width[b])
+        # padding only after the real entries of a segment; delay order among them
+        assert not np.any(~rl[:-1] & rl[1:] & ~start[c0 + 1:c1])
+        dd = np.diff(d)
+        assert np.all(dd[~start[c0 + 1:c1] & rl[1:] & rl[:-1]] >= 0)
+        sums += [int((blk[b] + local)[rl].sum()), int(d[rl].sum()), int(w[c0:c1].astype(np.int64).sum())]
+    assert sums[0] == int(onet.post.astype(np.int64).sum())
+    assert sums[1] == int(onet.delay.astype(np.int64).sum())
+    assert sums[2] == int(onet.w_fx.astype(np.int64).sum())
+    if rows is None:
+        rows = np.arange(n)
+        # fewer than 4 padding entries per segment
+        segid = np.repeat(np.arange(n * B), np.diff(seg, axis=1).ravel())
+        pads = np.bincount(segid[~real], minlength=n * B)
+        assert pads.max() < 4
+    for i in rows:
+        a, L = onet.row_ptr[i], lens[i]
+        sl = slice(rp[i], rp[i + 1])
+        keep = real[sl]
+        r = rec[sl].astype(np.int64)[keep]
+        tg = blk[bid[sl].astype(np.int64)[keep]] + (r & 1023)
+        o = np.sort(onet.post[a:a + L].astype(np.int64) << 38 | onet.delay[a:a + L].astype(np.int64) << 32
+                    | (onet.w_fx[a:a + L].astype(np.int64) + 2**31))
+        g = np.sort(tg << 38 | (r >> 10) << 32 | (w[sl][keep].astype(np.int64) + 2**31))
+        assert np.array_equal(o, g), i
+    # blocks balanced by in-degree (the heaviest within 30 % of the mean, up to one
+    # 32-neuron group), and no more than whole waves of one CTA per SM
+    indeg = np.bincount(onet.post, minlength=n)
+    grp = np.add.reduceat(indeg, np.arange(0, n, 32))
+    loads = np.add.reduceat(indeg, blk[:-1])
+    assert loads.max() <= 1.3 * loads.mean() + grp.max()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    waves = -(-(n // 736 + 1) // sms)
+    assert B <= waves * sms
+    return B
+
+
+def test_blocked_structure_and_raster_tiny(model, tiny):
+    """Blocked records of the tiny circuit: block boundaries, per-row block table and
+    decoded synapses equal the oracle's network; 1,000 steps give the oracle's raster
+    and state bit for bit."""
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=BLK,
+                      steps_per_graph=96)
+    info = net.info()
+    assert info.record_format == BLK and info.bytes_per_synapse == 6 and info.engine == GRAPH
+    assert _check_blocked_structure(net, onet) == info.target_blocks
+    net.step(1000)
+    g_t, g_i = net.read_spikes()
+    sim = oracle.Sim(model, onet, wl.seed)
+    o_t, o_i = sim.run(1000)
+    assert len(o_t) > 0 and np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
+    _assert_same_state(net, sim)
+    net.close()
+
+
+def _expected_ring(onet, spikers, t, npad):
+    lens = np.diff(onet.row_ptr)
+    starts = onet.row_ptr[spikers]
+    cnt = lens[spikers]
+    idx = np.repeat(starts - np.concatenate([[0], np.cumsum(cnt)[:-1]]), cnt) + np.arange(cnt.sum())
+    flat = ((t + onet.delay[idx].astype(np.int64)) % 64) * npad + onet.post[idx]
+    exp = np.bincount(flat, weights=onet.w_fx[idx].astype(np.float64), minlength=64 * npad)
+    assert np.abs(exp).max() < 2**31
+    return exp.astype(np.int64).reshape(64, npad)
+
+
+@pytest.mark.parametrize("nspk", [1, 63, 64, 700, 1024, 1025, 3000])
+def test_blocked_deliver_spikes_matches_oracle_network(model, tiny, nspk):
+    """Phase 2 alone with blocked records, below (reductions straight into the ring) and
+    above (shared-memory sums) the 64-sender switch and across the 1,024-sender staging
+    passes, repeats included: the ring equals the sums over the oracle's rows."""
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=BLK)
+    rng = np.random.default_rng(100 + nspk)
+    spikers = rng.integers(0, onet.n, nspk).astype(np.int32)
+    t = 61
+    net.deliver_spikes(torch.from_numpy(spikers).cuda(), t)
+    torch.cuda.synchronize()
+    npad = int(net.layout().n_neurons_padded)
+    ring = net.device_view("ring", torch.int32, 64 * npad).cpu().numpy().reshape(64, npad).astype(np.int64)
+    assert np.array_equal(ring, _expected_ring(onet, spikers, t, npad))
+    net.close()
+
+
+@pytest.mark.parametrize("n", [1, 13, 517, 2000])
+def test_blocked_ragged_counts_no_synapses(n):
+    """No synapses (blocks cut by width alone: 768, 768, 464 for 2,000 neurons)."""
+    m = workload.microcircuit_model()
+    rng = np.random.default_rng(n)
+    u0 = rng.uniform(0, 16, n).astype(np.float32)
+    custom = dict(pre=[], post=[], w_fx=[], delay=[], u0=u0, pop_offsets=[0] + [n] * 8)
+    o = _custom_parity(m, custom, 300, record_format=BLK)
+    assert len(o[0]) > 0
+
+
+def test_blocked_long_rows_all_delays():
+    """Rows longer than a 32-lane pass, every delay, autapses, multapses, mixed signs,
+    targets in several blocks (n = 2,301), with many senders per step."""
+    m = workload.microcircuit_model()
+    rng = np.random.default_rng(12)
+    n = 2301
+    pre, post, w, d = [], [], [], []
+    for s, L in ((0, 1), (5, 255), (6, 256), (7, 257), (8, 1000), (9, 3001), (2300, 513)):
+        pre += [s] * L
+        post += list(rng.integers(0, n, L))
+        w += list(rng.integers(-3_000_000, 3_000_000, L))
+        d += list(rng.integers(1, 64, L))
+    pre += [10] * 64
+    post += [10] * 64
+    w += [400_000] * 64
+    d += list(range(1, 64)) + [63]
+    # a dense random block so that some steps have more than 64 senders
+    k = 40000
+    pre += list(rng.integers(100, 2300, k))
+    post += list(rng.integers(0, n, k))
+    w += list(rng.integers(-600_000, 900_000, k))
+    d += list(rng.integers(1, 64, k))
+    u0 = rng.uniform(10, 16, n).astype(np.float32)
+    po = [0, 300, 600, 900, 1200, 1500, 1800, 2100, n]
+    custom = dict(pre=pre, post=post, w_fx=w, delay=d, u0=u0, pop_offsets=po)
+    o = _custom_parity(m, custom, 400, spg=33, record_format=BLK)
+    assert np.bincount(o[0]).max() >= 64
+
+
+@pytest.mark.parametrize("t1", [2, 63, 64])
+@pytest.mark.parametrize("d", [1, 16, 63])
+def test_blocked_hand_placed_spike_arrival(t1, d):
+    m = workload.microcircuit_model().replace(k_ext=[0.0] * 8)
+    w2 = 12345 * 16
+    c = _chain(t1 - 1, d, w2)
+    net = snn.Network(m, custom=c, steps_per_graph=7, record_format=BLK)
+    t_arr = t1 + d
+    net.step(t_arr)
+    _, I, _ = _state(net)
+    assert I[2] == 0.0
+    net.step(1)
+    _, I, _ = _state(net)
+    assert I[2] == np.float32(w2) * np.float32(2.0**-12)
+    net.close()
+
+
+def test_blocked_rejects_other_engines_and_batches(model):
+    for eng in (PIPE, PERSIST):
+        with pytest.raises(snn.SnnError):
+            snn.Network(model, 20, 20, seed=1, record_format=BLK, engine=eng)
+    with pytest.raises(snn.SnnError):
+        snn.Network(model, circuits=[(20, 20, 1), (30, 30, 2)], record_format=BLK)
+
+
+def test_blocked_full_scale_parity(model, full):
+    """Full microcircuit with blocked records: the structure (boundaries, quotas, every
+    synapse), 1,200 steps of raster and state equal to the oracle, and a saturating
+    delivery of 4,096 random senders equal to the ring sums over the oracle's rows."""
+    wl, onet = full
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=BLK)
+    assert net.info().n_synapses == 284_811_022
+    _check_blocked_structure(net, onet, rows=np.random.default_rng(3).integers(0, onet.n, 2000))
+    steps = 1200
+    net.step(steps)
+    g_t, g_i = net.read_spikes()
+    sim = oracle.Sim(model, onet, wl.seed)
+    o_t, o_i = sim.run(steps)
+    assert len(o_t) > 0 and np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
+    _assert_same_state(net, sim)
+    net.close()
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=BLK)
+    spikers = np.random.default_rng(7).integers(0, onet.n, 4096).astype(np.int32)
+    net.deliver_spikes(torch.from_numpy(spikers).cuda(), 40)
+    torch.cuda.synchronize()
+    npad = int(net.layout().n_neurons_padded)
+    ring = net.device_view("ring", torch.int32, 64 * npad).cpu().numpy().reshape(64, npad).astype(np.int64)
+    assert np.array_equal(ring, _expected_ring(onet, spikers, 40, npad))
+    net.close()
+
+
 @pytest.mark.parametrize("fmt", [snn.RECORD_PLAIN9, snn.RECORD_PACKED_BF16])
 @pytest.mark.parametrize("engine", ENGINES)
 def test_batched_circuits_equal_standalone_runs(model, engine, fmt):
