@@ -441,12 +441,13 @@ def run_gpu(args):
 
     torch.cuda.empty_cache()
 
-    def run_workload(label, circuits=None, wlx=None, fmt=snn.RECORD_PLAIN9, n_steps=None, tune=False):
+    def run_workload(label, circuits=None, wlx=None, fmt=snn.RECORD_PLAIN9, n_steps=None, tune=False, weng=None):
         """Build, optionally autotune, warm up and time a workload; returns a summary."""
         t0 = time.perf_counter()
+        weng = engine if weng is None else weng
         if circuits is not None:
             xnet = snn.Network(model, circuits=circuits, steps_per_graph=tps, raster_capacity=1 << 27, device=dev,
-                               engine=engine, record_format=fmt)
+                               engine=weng, record_format=fmt)
         else:
             xnet = snn.Network(model, wlx.scale_n_permille, wlx.scale_k_permille, wlx.seed + rank,
                                steps_per_graph=tps, raster_capacity=1 << 27, device=dev, engine=engine,
@@ -473,7 +474,10 @@ def run_gpu(args):
         xnet.read_spikes()
         xi = xnet.info()
         ev = xi.events_read - x0
-        out = {"workload": label, "neurons": int(xi.n_neurons), "synapses": int(xi.n_synapses),
+        out = {"workload": label, "engine": {snn.ENGINE_GRAPH: "graph", snn.ENGINE_PERSISTENT: "persistent",
+                                             snn.ENGINE_PIPELINED: "pipelined"}[xi.engine],
+               "circuits_per_group": int(xi.circuits_per_group),
+               "neurons": int(xi.n_neurons), "synapses": int(xi.n_synapses),
                "circuits": int(xi.n_circuits), "bytes_per_synapse": int(xi.bytes_per_synapse),
                "steps": nsteps, "value": ev / xsecs, "unit": "synaptic events/s",
                "us_per_step": xsecs / nsteps * 1e6, "rtf": xsecs / (nsteps * model.dt_ms * 1e-3),
@@ -493,7 +497,8 @@ def run_gpu(args):
         extra["batched"] = run_workload("32 PD circuits, neuron/in-degree scales U{100..1000} permille, seeds "
                                         "1000+c, 2 s each", circuits=[(w.scale_n_permille, w.scale_k_permille, w.seed)
                                                                       for w in bw],
-                                        n_steps=args.batched_steps, tune=True)
+                                        n_steps=args.batched_steps, tune=True,
+                                        weng=snn.ENGINE_GRAPH if args.engine == "default" else engine)
         extra["batched"]["speedup_vs_single_circuit"] = extra["batched"]["value"] / value
     if "x4" in args.extra:
         wx = workload.WORKLOADS["pd_x4"]

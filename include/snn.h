@@ -245,6 +245,8 @@ typedef struct snn_info {
     int32_t target_blocks;         /* SNN_RECORD_BLOCKED6: number of target blocks (else 0) */
     int32_t i8_base[SNN_MAX_POPS][SNN_MAX_POPS];  /* SNN_RECORD_PACKED_I8 read-back tables [source][target] */
     int32_t i8_step[SNN_MAX_POPS][SNN_MAX_POPS];
+    int32_t circuits_per_group;    /* graph engine, batches: see snn_set_circuit_groups (0 = one group) */
+    int32_t reserved3;
 } snn_info;
 
 typedef struct snn_net snn_net;
@@ -298,6 +300,17 @@ int snn_get_info(const snn_net *net, snn_info *out);
  * never changes results, only speed (see paper_2405_02019_gb300.autotune).
  * Errors: SNN_EINVAL (out of range), SNN_ENOTSUP (persistent engine), SNN_ECUDA. */
 int snn_set_schedule(snn_net *net, int32_t grid_ctas, int32_t delivery_warps, int32_t steps_per_graph);
+
+/* Batched networks on the graph engine: runs the circuits in groups of
+ * `circuits_per_group` consecutive circuits (0, or at least n_circuits, = one group) and
+ * re-captures the step graph (waits for enqueued steps first).  Every run of steps
+ * (a graph replay, or the steps one snn_step_n launches directly) is taken group by
+ * group: the first group's circuits take all the run's steps, then the next group's,
+ * and so on.  Circuits never interact, so results do not change; each group's ring and
+ * neuron state then stay in L2 through the run (a whole 32-circuit batch's ring is
+ * larger than L2).  Errors: SNN_EINVAL (negative), SNN_ENOTSUP (not the graph engine),
+ * SNN_ECUDA. */
+int snn_set_circuit_groups(snn_net *net, int32_t circuits_per_group);
 
 /* Batched networks: the first neuron and the neuron count of every circuit (host
  * arrays of n_circuits entries).  A single circuit reports base 0 and N. */

@@ -255,6 +255,12 @@ class Network:
         _check(load().snn_set_schedule(C.c_void_p(self._handle), int(grid_ctas), int(delivery_warps),
                                        int(steps_per_graph)), "snn_set_schedule")
 
+    def set_circuit_groups(self, circuits_per_group: int) -> None:
+        """Graph engine, batches: run consecutive circuits in groups of this many, one group
+        after another over each run of steps (0 = all at once); results never depend on it."""
+        _check(load().snn_set_circuit_groups(C.c_void_p(self._handle), int(circuits_per_group)),
+               "snn_set_circuit_groups")
+
     def circuits(self):
         """(base, n_neurons) arrays: where every circuit of a batch sits in the index space."""
         k = int(self.info().n_circuits)

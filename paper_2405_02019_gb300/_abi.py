@@ -94,6 +94,7 @@ class snn_info(C.Structure):
         ("n_circuits", C.c_int32), ("schedule_ctas", C.c_int32), ("schedule_delivery_warps", C.c_int32),
         ("target_blocks", C.c_int32),
         ("i8_base", (C.c_int32 * MAX_POPS) * MAX_POPS), ("i8_step", (C.c_int32 * MAX_POPS) * MAX_POPS),
+        ("circuits_per_group", C.c_int32), ("reserved3", C.c_int32),
     ]
 
 
@@ -125,6 +126,7 @@ PROTOTYPES = {
     "snn_get_out_degrees": (C.c_int, [C.c_void_p, C.c_void_p]),
     "snn_get_circuits": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "snn_set_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
+    "snn_set_circuit_groups": (C.c_int, [C.c_void_p, C.c_int32]),
     "snn_save_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.POINTER(C.c_uint64)]),
     "snn_load_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64]),
     "snn_deliver_spikes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p]),

@@ -1,8 +1,8 @@
 """Autotuner of the step kernels' launch schedule.
 
 The schedule -- CTAs of the step kernel, delivery warps per CTA, steps per captured
-graph (pipelined engine), or CTAs of the delivery kernel (graph engine) -- changes
-only speed, never results.  ``autotune`` times candidate schedules on the live
+graph (pipelined engine), or CTAs of the delivery kernel and, for a batch, circuits
+per group (graph engine) -- changes only speed, never results.  ``autotune`` times candidate schedules on the live
 network between a checkpoint and its restore (so the dynamics are untouched, but the
 host spike history restarts: read spikes before tuning), keeps the fastest, and
 remembers it in a JSON cache keyed by GPU, network shape, record format and engine.
@@ -27,9 +27,17 @@ def candidates(net: Network, num_sms: int) -> List[Dict[str, int]]:
         return [dict(grid_ctas=g, delivery_warps=w, steps_per_graph=s)
                 for g in (num_sms, 2 * num_sms) for w in (4, 8) for s in (1024,)]
     if info.engine == ENGINE_GRAPH:
-        return [dict(grid_ctas=g, delivery_warps=0, steps_per_graph=s)
-                for g in (num_sms, 2 * num_sms, 4 * num_sms) for s in (1024,)]
+        groups = [0] + [g for g in (4, 8, 16) if g < info.n_circuits]
+        return [dict(grid_ctas=g, delivery_warps=0, steps_per_graph=s, circuits_per_group=c)
+                for g in (num_sms, 2 * num_sms, 4 * num_sms) for s in (1024,) for c in groups]
     return []
+
+
+def _apply(net: Network, cand: Dict[str, int]) -> None:
+    sched = {k: v for k, v in cand.items() if k != "circuits_per_group"}
+    net.set_schedule(**sched)
+    if "circuits_per_group" in cand:
+        net.set_circuit_groups(cand["circuits_per_group"])
 
 
 def _key(net: Network) -> str:
@@ -54,7 +62,7 @@ def autotune(net: Network, trials: Optional[Iterable[Dict[str, int]]] = None, st
         except (OSError, ValueError):
             cache = {}
     if use_cache and key in cache:
-        net.set_schedule(**cache[key]["schedule"])
+        _apply(net, cache[key]["schedule"])
         return cache[key]
     num_sms = torch.cuda.get_device_properties(net.device).multi_processor_count
     trials = list(trials) if trials is not None else candidates(net, num_sms)
@@ -64,7 +72,7 @@ def autotune(net: Network, trials: Optional[Iterable[Dict[str, int]]] = None, st
     stream = torch.cuda.current_stream(net.device)
     timings = []
     for cand in trials:
-        net.set_schedule(**cand)
+        _apply(net, cand)
         net.step(steps)  # warm-up
         torch.cuda.synchronize(net.device)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -76,7 +84,7 @@ def autotune(net: Network, trials: Optional[Iterable[Dict[str, int]]] = None, st
         net.read_spikes(allow_overflow=True)
     best = min(timings, key=lambda r: r["us_per_step"])
     net.load_state(blob)
-    net.set_schedule(**best["schedule"])
+    _apply(net, best["schedule"])
     result = {"schedule": best["schedule"], "us_per_step": best["us_per_step"], "timings": timings}
     if cache_path:
         os.makedirs(os.path.dirname(cache_path), exist_ok=True)

@@ -76,6 +76,11 @@ struct snn_net {
     int64_t events_read = 0;
     int32_t *pin_nrn = nullptr, *pin_t = nullptr;
     int64_t pin_cap = 0;
+    // graph engine, batches: circuits per group (0 = one group) and each group's update
+    // arguments and grid; empty when the whole index space updates in one launch
+    int32_t circuits_per_group = 0;
+    std::vector<snn::StepArgs> group_args;
+    std::vector<int> group_grid;
 };
 
 namespace {
@@ -87,19 +92,57 @@ void launch_phase2(const snn_net *net, int k, cudaStream_t st)
     else snn::launch_deliver(net->args, k, net->deliver_grid, st);
 }
 
+// Graph engine, batches: consecutive circuits in groups of circuits_per_group, each
+// group updating only its own neuron range.  The groups are independent, so a run of
+// steps may take them one after another: each group's ring and state then stay in L2
+// for the whole run instead of the whole batch's competing for it every step.
+void build_groups(snn_net *net)
+{
+    net->group_args.clear();
+    net->group_grid.clear();
+    const int C = static_cast<int>(net->circuits.size());
+    const int cpg = net->circuits_per_group;
+    if (net->engine != SNN_ENGINE_GRAPH || cpg <= 0 || cpg >= C) return;
+    for (int c0 = 0; c0 < C; c0 += cpg) {
+        const int c1 = std::min(C, c0 + cpg);
+        const int64_t lo = net->circuits[c0].base;  // a multiple of 128
+        const int64_t hi = net->circuits[c1 - 1].base + net->circuits[c1 - 1].n;
+        snn::StepArgs a = net->args;
+        a.quad_base = lo / 4;
+        a.n = hi;
+        net->group_args.push_back(a);
+        net->group_grid.push_back(snn::update_grid(hi - lo));
+    }
+}
+
+// Graph engine: m steps from the device's t_base, every group in turn, then t_base += m.
+void enqueue_graph_steps(snn_net *net, int64_t m, cudaStream_t st)
+{
+    const size_t G = net->group_args.size();
+    for (size_t g = 0; g < std::max<size_t>(G, 1); ++g) {
+        const snn::StepArgs &a = G ? net->group_args[g] : net->args;
+        const int grid = G ? net->group_grid[g] : net->update_grid;
+        for (int64_t k = 0; k < m; ++k) {
+            snn::launch_update(a, static_cast<int>(k), grid, st);
+            launch_phase2(net, static_cast<int>(k), st);
+        }
+        if (g + 1 < G) snn::launch_resync(net->args.ctl, st);
+    }
+    snn::launch_advance(net->args.ctl, m, st);
+}
+
 // m steps launched one by one, starting at step t0 (the device counter t_base equals t0).
 int launch_steps_direct(snn_net *net, int64_t m, cudaStream_t st, int64_t t0)
 {
-    for (int64_t k = 0; k < m; ++k) {
-        if (net->engine == SNN_ENGINE_PIPELINED) {
+    if (net->engine == SNN_ENGINE_PIPELINED) {
+        for (int64_t k = 0; k < m; ++k) {
             const int ph = static_cast<int>((t0 + k) % snn::kPhasePeriod);
             snn::launch_step(net->args, static_cast<int>(k), ph, net->step_grid, st);
-        } else {
-            snn::launch_update(net->args, static_cast<int>(k), net->update_grid, st);
-            launch_phase2(net, static_cast<int>(k), st);
         }
+        snn::launch_advance(net->args.ctl, m, st);
+    } else {
+        enqueue_graph_steps(net, m, st);
     }
-    snn::launch_advance(net->args.ctl, m, st);
     SNN_CUDA_TRY(cudaGetLastError());
     return SNN_OK;
 }
@@ -121,8 +164,8 @@ int capture_graph(snn_net *net)
 {
     SNN_CUDA_TRY(cudaStreamCreateWithFlags(&net->capture_stream, cudaStreamNonBlocking));
     SNN_CUDA_TRY(cudaStreamBeginCapture(net->capture_stream, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < net->steps_per_graph; ++k) {
-        if (net->engine == SNN_ENGINE_PIPELINED) {
+    if (net->engine == SNN_ENGINE_PIPELINED) {
+        for (int k = 0; k < net->steps_per_graph; ++k) {
             // replays start on a multiple of the phase period (see snn_step_n); consecutive
             // step kernels overlap their launch with the previous one (programmatic edges)
             const int e = snn::launch_step(net->args, k, k % snn::kPhasePeriod, net->step_grid, net->capture_stream,
@@ -133,12 +176,11 @@ int capture_graph(snn_net *net)
                 if (g) cudaGraphDestroy(g);
                 return fail(SNN_ECUDA, std::string("capture: ") + cudaGetErrorString(static_cast<cudaError_t>(e)));
             }
-        } else {
-            snn::launch_update(net->args, k, net->update_grid, net->capture_stream);
-            launch_phase2(net, k, net->capture_stream);
         }
+        snn::launch_advance(net->args.ctl, net->steps_per_graph, net->capture_stream);
+    } else {
+        enqueue_graph_steps(net, net->steps_per_graph, net->capture_stream);
     }
-    snn::launch_advance(net->args.ctl, net->steps_per_graph, net->capture_stream);
     cudaError_t launch_err = cudaGetLastError();
     cudaGraph_t g = nullptr;
     cudaError_t end_err = cudaStreamEndCapture(net->capture_stream, &g);
@@ -147,6 +189,18 @@ int capture_graph(snn_net *net)
     net->graph = g;
     SNN_CUDA_TRY(cudaGraphInstantiate(&net->graph_exec, net->graph, 0));
     return SNN_OK;
+}
+
+// Replaces the captured step graph after a schedule change.
+int recapture(snn_net *net)
+{
+    if (net->graph_exec) cudaGraphExecDestroy(net->graph_exec);
+    if (net->graph) cudaGraphDestroy(net->graph);
+    if (net->capture_stream) cudaStreamDestroy(net->capture_stream);
+    net->graph_exec = nullptr;
+    net->graph = nullptr;
+    net->capture_stream = nullptr;
+    return capture_graph(net);
 }
 
 int wait_done(snn_net *net)
@@ -518,32 +572,39 @@ int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     double su = 0.0, sd = 0.0;
     const int64_t batch = 256;
-    std::vector<cudaEvent_t> ev(3 * batch);
+    const size_t G = net->engine == SNN_ENGINE_PIPELINED ? 1 : std::max<size_t>(net->group_args.size(), 1);
+    std::vector<cudaEvent_t> ev(3 * batch * G);
     for (auto &e : ev) SNN_CUDA_TRY(cudaEventCreate(&e));
     int rc = SNN_OK;
     for (int64_t done = 0; done < n_steps && rc == SNN_OK; done += batch) {
         const int64_t m = std::min(batch, n_steps - done);
-        for (int64_t k = 0; k < m; ++k) {
-            cudaEventRecord(ev[3 * k], st);
-            if (net->engine == SNN_ENGINE_PIPELINED) {
-                const int ph = static_cast<int>((net->t + done + k) % snn::kPhasePeriod);
-                snn::launch_step(net->args, static_cast<int>(k), ph, net->step_grid, st);
-                cudaEventRecord(ev[3 * k + 1], st);
-            } else {
-                snn::launch_update(net->args, static_cast<int>(k), net->update_grid, st);
-                cudaEventRecord(ev[3 * k + 1], st);
-                launch_phase2(net, static_cast<int>(k), st);
+        int64_t used = 0;  // event triples recorded in this batch
+        for (size_t g = 0; g < G; ++g) {
+            for (int64_t k = 0; k < m; ++k, ++used) {
+                cudaEventRecord(ev[3 * used], st);
+                if (net->engine == SNN_ENGINE_PIPELINED) {
+                    const int ph = static_cast<int>((net->t + done + k) % snn::kPhasePeriod);
+                    snn::launch_step(net->args, static_cast<int>(k), ph, net->step_grid, st);
+                    cudaEventRecord(ev[3 * used + 1], st);
+                } else {
+                    const bool grouped = !net->group_args.empty();
+                    snn::launch_update(grouped ? net->group_args[g] : net->args, static_cast<int>(k),
+                                       grouped ? net->group_grid[g] : net->update_grid, st);
+                    cudaEventRecord(ev[3 * used + 1], st);
+                    launch_phase2(net, static_cast<int>(k), st);
+                }
+                cudaEventRecord(ev[3 * used + 2], st);
             }
-            cudaEventRecord(ev[3 * k + 2], st);
+            if (g + 1 < G) snn::launch_resync(net->args.ctl, st);
         }
         snn::launch_advance(net->args.ctl, m, st);
         cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[3 * m - 1]);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[3 * used - 1]);
         if (e != cudaSuccess) {
             rc = fail(SNN_ECUDA, std::string("profile: ") + cudaGetErrorString(e));
             break;
         }
-        for (int64_t k = 0; k < m; ++k) {
+        for (int64_t k = 0; k < used; ++k) {
             float a = 0.f, b = 0.f;
             cudaEventElapsedTime(&a, ev[3 * k], ev[3 * k + 1]);
             cudaEventElapsedTime(&b, ev[3 * k + 1], ev[3 * k + 2]);
@@ -656,6 +717,7 @@ int snn_get_info(const snn_net *net, snn_info *out)
     out->schedule_ctas = net->engine == SNN_ENGINE_PIPELINED ? net->step_grid : net->deliver_grid;
     out->schedule_delivery_warps = net->engine == SNN_ENGINE_PIPELINED ? net->args.delivery_warps : 0;
     out->target_blocks = net->args.n_blocks;
+    out->circuits_per_group = net->circuits_per_group;
     std::memcpy(out->i8_base, net->i8_base, sizeof(out->i8_base));
     std::memcpy(out->i8_step, net->i8_step, sizeof(out->i8_step));
     return SNN_OK;
@@ -792,13 +854,21 @@ int snn_set_schedule(snn_net *net, int32_t grid_ctas, int32_t delivery_warps, in
             return fail(SNN_ENOTSUP, "the persistent engine has a fixed schedule");
         return SNN_OK;
     }
-    if (net->graph_exec) cudaGraphExecDestroy(net->graph_exec);
-    if (net->graph) cudaGraphDestroy(net->graph);
-    if (net->capture_stream) cudaStreamDestroy(net->capture_stream);
-    net->graph_exec = nullptr;
-    net->graph = nullptr;
-    net->capture_stream = nullptr;
-    return capture_graph(net);
+    build_groups(net);  // the group arguments copy the schedule
+    return recapture(net);
+}
+
+int snn_set_circuit_groups(snn_net *net, int32_t circuits_per_group)
+{
+    if (!net) return fail(SNN_EINVAL, "null network");
+    if (circuits_per_group < 0) return fail(SNN_EINVAL, "circuits_per_group < 0");
+    if (net->engine != SNN_ENGINE_GRAPH)
+        return fail(SNN_ENOTSUP, "circuit groups run on the graph engine");
+    const int rc = wait_done(net);
+    if (rc) return rc;
+    net->circuits_per_group = circuits_per_group >= static_cast<int32_t>(net->circuits.size()) ? 0 : circuits_per_group;
+    build_groups(net);
+    return recapture(net);
 }
 
 int snn_get_circuits(const snn_net *net, int64_t *base, int64_t *n_neurons)

@@ -142,6 +142,7 @@ struct StepArgs {
     const int32_t *blk_off;       // blocked records: block boundaries [n_blocks + 1]
     int32_t n_blocks;
     int32_t pad4;
+    int64_t quad_base;            // graph engine: first quad the update kernel covers (n = end neuron)
 };
 
 // Host constants of one model (§2.2).
@@ -203,13 +204,15 @@ int resolve_threads(int32_t requested);
 void launch_update(const StepArgs &a, int k, int grid, void *stream);
 void launch_deliver(const StepArgs &a, int k, int grid, void *stream);
 void launch_advance(Ctl *ctl, int64_t m, void *stream);
+// circuit groups: the next group starts the same steps where the raster now ends
+void launch_resync(Ctl *ctl, void *stream);
 void launch_deliver_list(const StepArgs &a, const int32_t *list, int64_t n, int64_t t, int grid, void *stream);
 // blocked records: one CTA per target block; list == nullptr delivers step t_base + k's
 // spikes from the raster (graph engine), else list[0 .. n) as spikes of step t
 int prepare_blocked_kernel();
 void launch_deliver_blocked(const StepArgs &a, const int32_t *list, int64_t n, int64_t t, int k, void *stream);
 int deliver_list_blocks_per_sm();
-int update_grid(int64_t n);
+int update_grid(int64_t n);  // CTAs of k_update for n neurons
 int persistent_blocks_per_sm();
 int launch_persistent(const StepArgs &a, int64_t n_steps, int grid, void *stream);
 // pipelined: B(t), A(t+1), D(t); ph = t mod 64.  With `programmatic`, the launch may

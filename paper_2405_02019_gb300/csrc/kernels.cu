@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kUpdateThreads) k_update(const StepArgs a, con
     __shared__ SharedTables s;
     stage_tables(a, s);
     const int64_t t = a.ctl->t_base + k;
-    const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t q = a.quad_base + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     int32_t spk[4] = {0, 0, 0, 0};
     if (q * 4 < a.n) update_quad(a, s, t, q, spk);
     append_spikes(a, t, q * 4, spk);
@@ -305,6 +305,10 @@ __global__ void __launch_bounds__(kDeliverThreads) k_deliver_list(const StepArgs
 }
 
 __global__ void k_advance(Ctl *ctl, int64_t m) { ctl->t_base += m; }
+
+// Circuit groups run the same steps one group after another: the next group's first
+// step appends its spikes from where the raster ends now.
+__global__ void k_resync(Ctl *ctl) { ctl->step_begin[ctl->t_base & 1] = ctl->cursor; }
 
 // Grid-wide barrier of a cooperative launch: the `index`-th barrier of the launch
 // waits until all gridDim.x blocks have arrived index times.  The wait is bounded by
@@ -939,6 +943,8 @@ void launch_advance(Ctl *ctl, int64_t m, void *stream)
 {
     k_advance<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(ctl, m);
 }
+
+void launch_resync(Ctl *ctl, void *stream) { k_resync<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(ctl); }
 
 int persistent_blocks_per_sm()
 {

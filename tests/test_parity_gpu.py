@@ -852,6 +852,48 @@ def test_batched_circuits_equal_standalone_runs(model, engine, fmt):
     net.close()
 
 
+@pytest.mark.parametrize("cpg", [1, 2, 3])
+def test_circuit_groups_equal_one_launch(model, cpg):
+    """Graph engine: circuits taken in groups (each group through a whole run of steps
+    before the next) give the raster and state of the ungrouped batch, across graph
+    replays, directly launched remainders, the profiling path, a checkpoint and a change
+    of grouping."""
+    ref = snn.Network(model, circuits=BATCH, steps_per_graph=64, engine=GRAPH)
+    ref.step(300)
+    r_t, r_i = ref.read_spikes()
+    rU, rI, rR = _state(ref)
+    ref.close()
+    net = snn.Network(model, circuits=BATCH, steps_per_graph=64, engine=GRAPH)
+    net.set_circuit_groups(cpg)
+    assert net.info().circuits_per_group == (cpg if cpg < len(BATCH) else 0)
+    net.step(100)   # one replay and 36 direct steps
+    blob = net.save_state()
+    part = net.read_spikes()
+    net.step(77)
+    net.load_state(blob)  # back to step 100; the host history restarts there
+    net.set_circuit_groups(0 if cpg > 1 else 2)
+    net.step(50)
+    net.set_circuit_groups(cpg)
+    net.step(100)
+    net.profile_steps(50)  # the kernel-by-kernel path takes the groups too
+    g_t, g_i = net.read_spikes()
+    g_t = np.concatenate([part[0], g_t])
+    g_i = np.concatenate([part[1], g_i])
+    assert np.array_equal(g_t, r_t) and np.array_equal(g_i, r_i)
+    U, I, R = _state(net)
+    assert np.array_equal(U.view(np.uint32), rU.view(np.uint32)) and np.array_equal(I.view(np.uint32),
+                                                                                      rI.view(np.uint32))
+    assert np.array_equal(R, rR)
+    net.close()
+
+
+def test_circuit_groups_need_the_graph_engine(model):
+    net = snn.Network(model, circuits=BATCH, engine=PIPE)
+    with pytest.raises(snn.SnnError):
+        net.set_circuit_groups(2)
+    net.close()
+
+
 # ------------------------------------------------------------ schedules, autotuner
 
 
