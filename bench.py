@@ -547,6 +547,7 @@ def run_gpu(args):
                                         "(13 B per event + 20 B per sender); int32 red.add into the ring",
                                 "points": sat,
                                 "blocked6": {"kernel": "k_deliver_blocked",
+                                             "traffic_20480": _recorded_traffic("k_deliver_blocked"),
                                              "note": "one CTA per target block, sums in shared memory; frac on "
                                                      "its own bytes (6 B per event, sender index, 8 B per ring "
                                                      "entry updated)",
