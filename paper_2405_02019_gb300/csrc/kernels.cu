@@ -683,10 +683,12 @@ __global__ void __launch_bounds__(kStepMaxThreads, 2) k_prime(const StepArgs a)
 // ---------------------------------------------------------------------------------
 
 constexpr int kBlockedWarps = kBlockedThreads / 32;
-constexpr size_t kBlockedBinsBytes = sizeof(int32_t) * kDMax * kBlockMaxWidth;
-constexpr size_t kBlockedSmemBytes = kBlockedBinsBytes + sizeof(uint32_t) * kBlockedBatch +
-                                     sizeof(int32_t) * (kBlockedBatch + kBlockedWarps) +
-                                     sizeof(uint16_t) * kBlockedWindow;
+// dynamic shared memory of k_deliver_blocked, in bytes from its start
+constexpr size_t kBlockedOffSegQ = sizeof(int32_t) * kDMax * kBlockMaxWidth;         // bins [64][768]
+constexpr size_t kBlockedOffPfx = kBlockedOffSegQ + sizeof(uint32_t) * kBlockedBatch;  // first quad per sender
+constexpr size_t kBlockedOffWarp = kBlockedOffPfx + sizeof(int32_t) * kBlockedBatch;   // quad prefix per sender
+constexpr size_t kBlockedOffSegOf = kBlockedOffWarp + sizeof(int32_t) * kBlockedWarps; // scan scratch
+constexpr size_t kBlockedSmemBytes = kBlockedOffSegOf + sizeof(uint16_t) * kBlockedWindow;
 static_assert(kBlockedSmemBytes <= 232448, "blocked delivery: shared memory above the 227 KB opt-in limit");
 static_assert(sizeof(uint16_t) * kBlockedWindow >= sizeof(int32_t) * kBlockedThreads, "scan output must fit the table");
 static_assert(kBlockedBatch % kBlockedThreads == 0 && kBlockedBatch <= 65536, "staged senders per thread / table");
@@ -768,11 +770,12 @@ __global__ void __launch_bounds__(kBlockedThreads, 1)
     k_deliver_blocked(const StepArgs a, const int32_t *list, int64_t n_list, int64_t t_list, int k)
 {
     extern __shared__ int4 smem4[];
-    int32_t *bins = reinterpret_cast<int32_t *>(smem4);                               // [64][kBlockMaxWidth]
-    uint32_t *seg_q = reinterpret_cast<uint32_t *>(bins + kDMax * kBlockMaxWidth);  // first quad
-    int32_t *pfx = reinterpret_cast<int32_t *>(seg_q + kBlockedBatch);              // [kBlockedBatch]
-    int32_t *warp_sums = pfx + kBlockedBatch + 1;
-    uint16_t *seg_of = reinterpret_cast<uint16_t *>(warp_sums + kBlockedWarps);     // [kBlockedWindow]
+    uint8_t *sm = reinterpret_cast<uint8_t *>(smem4);
+    int32_t *bins = reinterpret_cast<int32_t *>(sm);                          // [64][kBlockMaxWidth]
+    uint32_t *seg_q = reinterpret_cast<uint32_t *>(sm + kBlockedOffSegQ);     // [kBlockedBatch]
+    int32_t *pfx = reinterpret_cast<int32_t *>(sm + kBlockedOffPfx);          // [kBlockedBatch]
+    int32_t *warp_sums = reinterpret_cast<int32_t *>(sm + kBlockedOffWarp);   // [kBlockedWarps]
+    uint16_t *seg_of = reinterpret_cast<uint16_t *>(sm + kBlockedOffSegOf);   // [kBlockedWindow]
 
     int64_t t;
     const int32_t *spk;
