@@ -807,9 +807,16 @@ __global__ void __launch_bounds__(kBlockedThreads, 1)
     if (aggregate)
         for (int j = tid; j < kDMax * kBlockMaxWidth / 4; j += kBlockedThreads) smem4[j] = make_int4(0, 0, 0, 0);
 
+    // thread tid stages senders tid * kPer .. + kPer of every pass (consecutive, for the
+    // scan); the ids of the next pass are loaded while the current pass streams
+    int32_t ids[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int64_t j = static_cast<int64_t>(tid) * kPer + i;
+        ids[i] = j < nspk ? __ldcg(spk + j) : 0;
+    }
     for (int64_t b0 = 0; b0 < nspk; b0 += kBlockedBatch) {
         const int nb = static_cast<int>(nspk - b0 < kBlockedBatch ? nspk - b0 : kBlockedBatch);
-        // thread tid stages senders tid * kPer .. + kPer (consecutive, for the scan)
         int32_t nq[kPer];
         int32_t mine = 0;
 #pragma unroll
@@ -817,7 +824,7 @@ __global__ void __launch_bounds__(kBlockedThreads, 1)
             const int j = tid * kPer + i;
             nq[i] = 0;
             if (j < nb) {
-                const int32_t s = __ldcg(spk + b0 + j);
+                const int32_t s = ids[i];
                 const uint16_t *sg = a.blk_seg + static_cast<int64_t>(s) * stride + p;
                 const int32_t o0 = __ldg(sg), o1 = __ldg(sg + 1);
                 seg_q[j] = static_cast<uint32_t>((__ldg(a.row_ptr + s) + o0) / kBlockQuad);
@@ -837,6 +844,11 @@ __global__ void __launch_bounds__(kBlockedThreads, 1)
             }
         }
         __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int64_t j = b0 + kBlockedBatch + static_cast<int64_t>(tid) * kPer + i;
+            ids[i] = j < nspk ? __ldcg(spk + j) : 0;
+        }
         for (int32_t w0 = 0; w0 < total; w0 += kBlockedWindow) {
             const int32_t w1 = total - w0 < kBlockedWindow ? total : w0 + kBlockedWindow;
             // segment of every quad of the window
