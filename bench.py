@@ -185,6 +185,29 @@ def cpu_oracle_sample(model, wl, ticks: int):
             "spikes": int(len(st))}, onet, sim
 
 
+def cpu_mt_sample(model, wl, onet, ticks: int):
+    """The oracle's step on every host core (oracle/cpu_mt.c: neurons and ring split by
+    thread-owned target ranges, no atomics; same raster as the oracle), first `ticks`
+    steps of the workload."""
+    import oracle
+
+    threads = os.cpu_count() or 1
+    try:
+        oracle.build_mt()
+    except Exception as e:  # no OpenMP toolchain on this host
+        return {"unavailable": f"could not build the multithreaded baseline: {e}"}
+    t0 = time.perf_counter()
+    sim = oracle.SimMT(model, onet, wl.seed, threads)
+    prep = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    st, si = sim.run(ticks)
+    secs = time.perf_counter() - t0
+    events = int(np.diff(onet.row_ptr)[si].sum())
+    return {"value": events / secs, "unit": "synaptic events/s", "cores": threads, "kind": "oracle, thread-partitioned",
+            "sample": f"first {ticks} steps of {wl.name}, seed {wl.seed}; partition by target range {prep:.1f} s, "
+                      f"not timed", "rtf": secs / (ticks * model.dt_ms * 1e-3), "seconds": secs, "events": events}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -511,13 +534,14 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu, _, _ = cpu_oracle_sample(model, wl, args.cpu_ticks)
+        cpu, onet, _ = cpu_oracle_sample(model, wl, args.cpu_ticks)
         try:
             import multiprocessing
 
             cpu["host_cores_available"] = multiprocessing.cpu_count()
         except Exception:
             pass
+        cpu["multithreaded"] = cpu_mt_sample(model, wl, onet, args.cpu_ticks)
 
     line = {
         "metric": METRIC,

@@ -12,6 +12,8 @@ Functions mirror the paper's steps:
   poisson_table / draws       -- thalamic Poisson drive (§2.2)
   lif_trace                   -- one neuron under a given input (Listing push, Eqs. mem/psc/ref)
   Sim.run                     -- the full deferred-push step loop (Listings push, push2; §3.2 ring)
+  SimMT.run                   -- the same loop on host threads that own target ranges (cpu_mt.c),
+                                 a CPU timing baseline with the oracle's raster
 """
 
 from __future__ import annotations
@@ -310,3 +312,81 @@ class Sim:
         self.t += n_steps
         k = nr.value
         return rt[:k].copy(), ri[:k].copy()
+
+
+# --------------------------------------------------------------------------- multithreaded baseline
+
+_MT_SRC = os.path.join(_HERE, "cpu_mt.c")
+_MT_LIB = os.path.join(_HERE, "liboracle_mt.so")
+_mt = None
+
+
+def build_mt(force: bool = False) -> str:
+    """Compile cpu_mt.c (the oracle's definitions, thread-partitioned; OpenMP)."""
+    newest = max(os.path.getmtime(_MT_SRC), os.path.getmtime(_SRC))
+    if force or not os.path.exists(_MT_LIB) or os.path.getmtime(_MT_LIB) < newest:
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+               "-Wall", "-Wextra", "-Wno-unused-function", _MT_SRC, "-o", _MT_LIB + ".tmp", "-lm"]
+        subprocess.run(cmd, check=True, cwd=_HERE)
+        os.replace(_MT_LIB + ".tmp", _MT_LIB)
+    return _MT_LIB
+
+
+def lib_mt():
+    global _mt
+    if _mt is None:
+        L = C.CDLL(build_mt())
+        vp = C.c_void_p
+        L.mt_build.argtypes = [C.c_int32, C.c_int64, vp, vp, vp, vp]
+        L.mt_build.restype = vp
+        L.mt_free.argtypes = [vp]
+        L.mt_run.argtypes = [C.POINTER(OrModel), C.c_uint64, vp, vp, vp, vp, vp, vp, C.c_int64, C.c_int64, vp,
+                             vp, C.c_int64, C.POINTER(C.c_int64)]
+        L.mt_run.restype = C.c_int
+        _mt = L
+    return _mt
+
+
+class SimMT:
+    """The step loop of Sim on `threads` host threads (a CPU timing baseline): the same
+    raster and state as Sim, with an int32 ring."""
+
+    def __init__(self, m, net: Network, seed: int, threads: int):
+        self.m, self.net, self.seed, self.threads = m, net, int(seed), int(threads)
+        self._cm = _model(m)
+        n = net.n
+        post = net.post if len(net.post) else np.zeros(1, np.int32)
+        w = net.w_fx if len(net.w_fx) else np.zeros(1, np.int32)
+        d = net.delay if len(net.delay) else np.zeros(1, np.uint8)
+        self._h = lib_mt().mt_build(self.threads, n, _p(net.row_ptr), _p(post), _p(w), _p(d))
+        if not self._h:
+            raise MemoryError("thread partition failed")
+        self.U = net.u0.astype(np.float32)
+        self.I = np.zeros(n, np.float32)
+        self.R = np.zeros(n, np.int32)
+        self.W = np.zeros(D_MAX * n, np.int32)
+        self.t = 0
+
+    def run(self, n_steps: int, raster_cap: Optional[int] = None):
+        cap = raster_cap if raster_cap is not None else max(1024, 64 * self.net.n + 1024)
+        cap = min(cap, max(1, n_steps) * max(1, self.net.n))
+        rt = np.zeros(cap, np.int32)
+        ri = np.zeros(cap, np.int32)
+        nr = C.c_int64(0)
+        rc = lib_mt().mt_run(C.byref(self._cm), self.seed, self._h, _p(self.net.pop_off), _p(self.U), _p(self.I),
+                             _p(self.R), _p(self.W), self.t, n_steps, _p(rt), _p(ri), cap, C.byref(nr))
+        if rc < 0:
+            raise MemoryError("baseline run failed")
+        if rc == 1:
+            raise OverflowError("raster capacity exceeded")
+        self.t += n_steps
+        k = nr.value
+        return rt[:k].copy(), ri[:k].copy()
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib_mt().mt_free(self._h)
+                self._h = None
+        except Exception:
+            pass
