@@ -233,7 +233,7 @@ def run_reference(args):
     bio = args.steps * ticks * model.dt_ms * 1e-3
     line = {
         "impl": "reference", "metric": METRIC,
-        "value": value, "unit": "synaptic events/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "value": value, "unit": "synaptic events/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32/i32", "data": "synthetic (PD microcircuit sampled from the paper's tables)",
         "config": {"workload": f"{wl.name}: 77,169 neurons, 284,811,022 synapses, dt 0.1 ms, seed {wl.seed}",
