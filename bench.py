@@ -12,7 +12,13 @@ one JSON line.
             host memory every bench step (snn_step_n + snn_read_spikes)
   roofline  the dominant kernel's algorithmic bytes per launch / its average
             CUDA-event duration, against the measured HBM copy bandwidth
-  cpu_baseline  the CPU oracle (single thread) on a bounded sample of the workload
+  cpu_baseline  the CPU oracle (single thread) on a bounded sample of the workload,
+            and in its `multithreaded` entry the same step on every host core
+  energy    board power sampled over the timed region x time / recurrent events
+Further objects: delivery_saturating (phase 2 alone over 2,048-20,480 random senders,
+plain and target-blocked records), compressed_records (int8, bf16, blocked forms) and
+workloads (32 uneven circuits in autotuned circuit groups; the 4x-scale circuit in
+plain and int8 records).
 
 --impl reference times the CPU oracle itself on the same workload (rank 0 only).
 Under torchrun with N > 1, every rank simulates its own circuit (replicas: the
