@@ -89,8 +89,9 @@ constexpr int kBlockAvgWidth = 512;          // sets the number of in-degree quo
 constexpr int kBlockAlign = 32;              // block boundaries are multiples of 32
 constexpr int kBlockQuad = 4;                // (row, block) segments are whole quads of records
 constexpr int kBlockedThreads = 1024;
-constexpr int kBlockedBatch = 2048;          // senders staged per pass
-constexpr int kBlockedWindow = 8192;        // quads of a pass mapped to their segments at once
+constexpr int kBlockedBatch = 4096;          // senders staged per pass
+constexpr int kBlockedWindow = 8192;         // quads of a pass whose record-array index is tabled at once
+constexpr int kBlockedBinDelays = 32;        // delays summed in shared memory (longer: ring reductions)
 constexpr int kBlockedRounds = 4;            // quads in flight per lane (32 per round and warp)
 constexpr int64_t kBlockedAggregateMin = 64; // fewer senders: reduce straight into the ring
 inline int max_target_blocks(int64_t n)

@@ -670,28 +670,34 @@ __global__ void __launch_bounds__(kStepMaxThreads, 2) k_prime(const StepArgs a)
 // the segment that lands in its block (row_ptr[s] + seg[s][p] .. + seg[s][p + 1]); a
 // segment is a whole number of aligned quads of records (zero-weight padding).  Per
 // pass the CTA stages up to kBlockedBatch senders' segments (first quad, quad count and
-// the exclusive prefix of the counts), which makes the pass one stream of quads.  The
-// stream is taken in windows of kBlockedWindow quads; for a window every quad's segment
-// is written into a shared table, after which the quads are independent work: warp w
-// takes rounds w, w + 16, ... of 32 consecutive quads, kBlockedRounds rounds at a time,
-// issuing all their loads (8 bytes of records, 16 of weights per quad) before adding
-// any.  With many senders the weights are summed per (delay, local target) in shared
-// memory and each nonzero sum is added to its ring entry once at the end; only this CTA
-// writes these ring columns during the launch, so that final add is a plain
-// read-modify-write.  With few senders the weights go straight to the ring as
-// reductions.  Integer addition makes both orders give the same ring.
+// the exclusive prefix of the counts) in shared memory, which makes the pass one stream
+// of quads.  The
+// stream is taken in windows of kBlockedWindow quads; for a window the record-array
+// index of every quad is written into a shared table, after which the quads are
+// independent work: warp w takes rounds w, w + 32, ... of 32 consecutive quads,
+// kBlockedRounds rounds at a time, issuing all their loads (8 bytes of records, 16 of
+// weights per quad) before adding any.
+// With many senders the weights of delays up to kBlockedBinDelays are summed per (delay,
+// local target) in shared memory and each nonzero sum is added to its ring entry once at
+// the end; only this CTA writes these ring columns during the launch, so that final add
+// is a plain read-modify-write.  Longer delays (about 1 % of the microcircuit's events)
+// and, with few senders, all weights go straight to the ring as reductions; they land
+// in other ring rows than the plain adds.  Integer addition makes every order give the
+// same ring.
 // ---------------------------------------------------------------------------------
 
 constexpr int kBlockedWarps = kBlockedThreads / 32;
 // dynamic shared memory of k_deliver_blocked, in bytes from its start
-constexpr size_t kBlockedOffSegQ = sizeof(int32_t) * kDMax * kBlockMaxWidth;         // bins [64][768]
+constexpr size_t kBlockedOffSegQ = sizeof(int32_t) * (kBlockedBinDelays + 1) * kBlockMaxWidth;  // bins
 constexpr size_t kBlockedOffPfx = kBlockedOffSegQ + sizeof(uint32_t) * kBlockedBatch;  // first quad per sender
-constexpr size_t kBlockedOffWarp = kBlockedOffPfx + sizeof(int32_t) * kBlockedBatch;   // quad prefix per sender
-constexpr size_t kBlockedOffSegOf = kBlockedOffWarp + sizeof(int32_t) * kBlockedWarps; // scan scratch
-constexpr size_t kBlockedSmemBytes = kBlockedOffSegOf + sizeof(uint16_t) * kBlockedWindow;
+constexpr size_t kBlockedOffNq = kBlockedOffPfx + sizeof(int32_t) * kBlockedBatch;     // quad prefix per sender
+constexpr size_t kBlockedOffWarp = kBlockedOffNq + sizeof(int32_t) * kBlockedBatch;    // quads per sender
+constexpr size_t kBlockedOffQidx = kBlockedOffWarp + sizeof(int32_t) * kBlockedWarps;  // scan scratch
+constexpr size_t kBlockedSmemBytes = kBlockedOffQidx + sizeof(uint32_t) * kBlockedWindow;
 static_assert(kBlockedSmemBytes <= 232448, "blocked delivery: shared memory above the 227 KB opt-in limit");
-static_assert(sizeof(uint16_t) * kBlockedWindow >= sizeof(int32_t) * kBlockedThreads, "scan output must fit the table");
-static_assert(kBlockedBatch % kBlockedThreads == 0 && kBlockedBatch <= 65536, "staged senders per thread / table");
+static_assert(kBlockedWindow >= kBlockedThreads, "the scan output must fit the window table");
+static_assert(kBlockedBatch % kBlockedThreads == 0, "staged senders per thread");
+static_assert(kBlockedBinDelays >= 1 && kBlockedBinDelays < kDMax && kBlockMaxWidth % 4 == 0, "bins");
 
 template <bool kAggregate>
 __device__ __forceinline__ void blocked_apply(const StepArgs &a, int32_t *bins, int64_t t, int32_t base, uint32_t rec,
@@ -700,7 +706,7 @@ __device__ __forceinline__ void blocked_apply(const StepArgs &a, int32_t *bins, 
     if (w == 0) return;  // padding (adding zero changes nothing)
     const int d = static_cast<int>(rec >> kBlockLocalBits);
     const int lt = static_cast<int>(rec & ((1u << kBlockLocalBits) - 1));
-    if (kAggregate) atomicAdd(bins + d * kBlockMaxWidth + lt, w);
+    if (kAggregate && d <= kBlockedBinDelays) atomicAdd(bins + d * kBlockMaxWidth + lt, w);
     else red_add_s32(a.ring + ((t + d) & kDMask) * a.npad + base + lt, w);
 }
 
@@ -731,11 +737,10 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *out,
     return warp_sums[kBlockedWarps - 1];
 }
 
-// Quads [w0, w1) of the staged stream; seg_of[e - w0] is the segment of quad e.
+// Quads [w0, w1) of the staged stream; qidx[e - w0] is quad e's index in the record arrays.
 template <bool kAggregate>
-__device__ __forceinline__ void blocked_window(const StepArgs &a, int32_t *bins, const uint32_t *seg_q,
-                                               const int32_t *pfx, const uint16_t *seg_of, int32_t w0, int32_t w1,
-                                               int64_t t, int32_t base)
+__device__ __forceinline__ void blocked_window(const StepArgs &a, int32_t *bins, const uint32_t *qidx, int32_t w0,
+                                               int32_t w1, int64_t t, int32_t base)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint2 *recq = reinterpret_cast<const uint2 *>(a.blk_rec);
@@ -749,8 +754,7 @@ __device__ __forceinline__ void blocked_window(const StepArgs &a, int32_t *bins,
         for (int k = 0; k < kBlockedRounds; ++k) {
             const int32_t e = e0 + 32 * (warp + kBlockedWarps * k) + lane;
             if (e < w1) {
-                const int j = seg_of[e - w0];
-                const int64_t q = static_cast<int64_t>(seg_q[j]) + (e - pfx[j]);
+                const uint32_t q = qidx[e - w0];
                 rec[k] = __ldcs(recq + q);
                 w[k] = __ldcs(wq + q);
             }
@@ -771,11 +775,12 @@ __global__ void __launch_bounds__(kBlockedThreads, 1)
 {
     extern __shared__ int4 smem4[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(smem4);
-    int32_t *bins = reinterpret_cast<int32_t *>(sm);                          // [64][kBlockMaxWidth]
+    int32_t *bins = reinterpret_cast<int32_t *>(sm);                          // [kBlockedBinDelays + 1][768]
     uint32_t *seg_q = reinterpret_cast<uint32_t *>(sm + kBlockedOffSegQ);     // [kBlockedBatch]
     int32_t *pfx = reinterpret_cast<int32_t *>(sm + kBlockedOffPfx);          // [kBlockedBatch]
+    int32_t *seg_nq = reinterpret_cast<int32_t *>(sm + kBlockedOffNq);        // [kBlockedBatch]
     int32_t *warp_sums = reinterpret_cast<int32_t *>(sm + kBlockedOffWarp);   // [kBlockedWarps]
-    uint16_t *seg_of = reinterpret_cast<uint16_t *>(sm + kBlockedOffSegOf);   // [kBlockedWindow]
+    uint32_t *qidx = reinterpret_cast<uint32_t *>(sm + kBlockedOffQidx);      // [kBlockedWindow]
 
     int64_t t;
     const int32_t *spk;
@@ -805,71 +810,61 @@ __global__ void __launch_bounds__(kBlockedThreads, 1)
     constexpr int kPer = kBlockedBatch / kBlockedThreads;  // senders staged per thread
 
     if (aggregate)
-        for (int j = tid; j < kDMax * kBlockMaxWidth / 4; j += kBlockedThreads) smem4[j] = make_int4(0, 0, 0, 0);
+        for (int j = tid; j < (kBlockedBinDelays + 1) * kBlockMaxWidth / 4; j += kBlockedThreads)
+            smem4[j] = make_int4(0, 0, 0, 0);
 
-    // thread tid stages senders tid * kPer .. + kPer of every pass (consecutive, for the
-    // scan); the ids of the next pass are loaded while the current pass streams
-    int32_t ids[kPer];
-#pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-        const int64_t j = static_cast<int64_t>(tid) * kPer + i;
-        ids[i] = j < nspk ? __ldcg(spk + j) : 0;
-    }
     for (int64_t b0 = 0; b0 < nspk; b0 += kBlockedBatch) {
         const int nb = static_cast<int>(nspk - b0 < kBlockedBatch ? nspk - b0 : kBlockedBatch);
-        int32_t nq[kPer];
+        // thread tid stages senders tid * kPer .. + kPer (consecutive, for the scan)
         int32_t mine = 0;
 #pragma unroll
         for (int i = 0; i < kPer; ++i) {
             const int j = tid * kPer + i;
-            nq[i] = 0;
+            int32_t nq = 0;
             if (j < nb) {
-                const int32_t s = ids[i];
+                const int32_t s = __ldcg(spk + b0 + j);
                 const uint16_t *sg = a.blk_seg + static_cast<int64_t>(s) * stride + p;
                 const int32_t o0 = __ldg(sg), o1 = __ldg(sg + 1);
                 seg_q[j] = static_cast<uint32_t>((__ldg(a.row_ptr + s) + o0) / kBlockQuad);
-                nq[i] = (o1 - o0) / kBlockQuad;
+                nq = (o1 - o0) / kBlockQuad;
             }
-            mine += nq[i];
+            seg_nq[j] = nq;
+            mine += nq;
         }
         // the window table is idle here: it holds the scan's per-thread output
-        int32_t *scan_out = reinterpret_cast<int32_t *>(seg_of);
+        int32_t *scan_out = reinterpret_cast<int32_t *>(qidx);
         const int32_t total = block_exclusive_scan(mine, scan_out, warp_sums);
         {
             int32_t run = scan_out[tid];
 #pragma unroll
             for (int i = 0; i < kPer; ++i) {
                 pfx[tid * kPer + i] = run;
-                run += nq[i];
+                run += seg_nq[tid * kPer + i];
             }
         }
         __syncthreads();
-#pragma unroll
-        for (int i = 0; i < kPer; ++i) {
-            const int64_t j = b0 + kBlockedBatch + static_cast<int64_t>(tid) * kPer + i;
-            ids[i] = j < nspk ? __ldcg(spk + j) : 0;
-        }
         for (int32_t w0 = 0; w0 < total; w0 += kBlockedWindow) {
             const int32_t w1 = total - w0 < kBlockedWindow ? total : w0 + kBlockedWindow;
-            // segment of every quad of the window
+            // record-array index of every quad of the window
 #pragma unroll
             for (int i = 0; i < kPer; ++i) {
                 const int j = tid * kPer + i;
                 if (j >= nb) break;
-                const int32_t lo = max(pfx[j], w0), hi = min(pfx[j] + nq[i], w1);
-                for (int32_t e = lo; e < hi; ++e) seg_of[e - w0] = static_cast<uint16_t>(j);
+                const int32_t lo = max(pfx[j], w0), hi = min(pfx[j] + seg_nq[j], w1);
+                const uint32_t q0 = seg_q[j] - static_cast<uint32_t>(pfx[j]);
+                for (int32_t e = lo; e < hi; ++e) qidx[e - w0] = q0 + static_cast<uint32_t>(e);
             }
             __syncthreads();
-            if (aggregate) blocked_window<true>(a, bins, seg_q, pfx, seg_of, w0, w1, t, base);
-            else blocked_window<false>(a, bins, seg_q, pfx, seg_of, w0, w1, t, base);
+            if (aggregate) blocked_window<true>(a, bins, qidx, w0, w1, t, base);
+            else blocked_window<false>(a, bins, qidx, w0, w1, t, base);
             __syncthreads();  // the table is rebuilt for the next window
         }
     }
     if (!aggregate) return;
-    // add the sums of delays 1..63 to their ring rows; width is a multiple of 4 except
-    // for the last block, whose extra columns lie inside the padded ring row (sum 0)
+    // add the sums of delays 1..kBlockedBinDelays to their ring rows; width is a multiple
+    // of 4 except for the last block, whose extra columns lie inside the padded ring row
     const int w4 = (width + 3) >> 2;
-    for (int q = tid; q < (kDMax - 1) * w4; q += kBlockedThreads) {
+    for (int q = tid; q < kBlockedBinDelays * w4; q += kBlockedThreads) {
         const int d = 1 + q / w4;
         const int c4 = q - (d - 1) * w4;
         const int4 v = smem4[(d * kBlockMaxWidth) / 4 + c4];
