@@ -89,7 +89,7 @@ constexpr int kBlockAvgWidth = 512;          // sets the number of in-degree quo
 constexpr int kBlockAlign = 32;              // block boundaries are multiples of 32
 constexpr int kBlockQuad = 4;                // (row, block) segments are whole quads of records
 constexpr int kBlockedThreads = 1024;
-constexpr int kBlockedBatch = 4096;          // senders staged per pass
+constexpr int kBlockedBatch = 2048;          // senders staged per pass
 constexpr int kBlockedWindow = 8192;         // quads of a pass whose record-array index is tabled at once
 constexpr int kBlockedBinDelays = 32;        // delays summed in shared memory (longer: ring reductions)
 constexpr int kBlockedRounds = 4;            // quads in flight per lane (32 per round and warp)
