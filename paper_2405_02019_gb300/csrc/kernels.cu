@@ -11,15 +11,23 @@
 // compacted warp by warp (one atomic per warp with spikes) into the raster, which is
 // also the step's spike queue.
 // Phase 2 (Listing push2 of §3.1): every queued spiker's row (sorted by delay, §3.5)
-// is cut into 256-synapse chunks; a warp streams a chunk with 16-byte loads and adds
-// each weight into W[(t + d) mod 64][target] with a fire-and-forget int32 reduction,
-// so the order of delivery cannot change the result.
+// is cut into runs of 256-synapse chunks; a warp streams a chunk with 16-byte loads and
+// adds each weight into W[(t + d) mod 64][target] with a fire-and-forget int32
+// reduction, so the order of delivery cannot change the result.
 //
-// Two engines run these phases:
-//   k_update + k_deliver -- one kernel per phase, replayed from a CUDA graph;
+// Three engines run these phases (every one gives the same raster):
+//   k_step               -- pipelined (default): one kernel per step delivers step t's
+//                           spikes while it finishes step t's update and decides step
+//                           t+1's spikes (a spike at s depends only on spikes <= s-2);
+//                           replayed from a CUDA graph with programmatic launch;
+//   k_update + k_deliver -- one kernel per phase, replayed from a CUDA graph (batches
+//                           may run in circuit groups: k_update takes a neuron range);
 //   k_persistent         -- one cooperative launch for a batch of steps, the phases
 //                           separated by grid-wide barriers whose spin-waits are
 //                           bounded (on timeout the kernel records an error and exits).
+// k_deliver_list delivers a given sender list (measurement and tests); blocked records
+// (target-blocked rows) have their own phase 2, k_deliver_blocked, at the end of this
+// file.
 //
 // No FMA in the neuron arithmetic: __fmul_rn / __fadd_rn round every product and sum
 // on its own, which is what makes the raster reproducible bit for bit.
