@@ -52,11 +52,17 @@ METRIC = "synaptic events/s and real-time factor (full microcircuit, 1 GB300), %
 
 
 def _kernel_sources_hash() -> str:
+    """Hash of the kernel sources' code lines (comment-only and blank lines ignored)."""
     import hashlib
 
     csrc = os.path.join(ROOT, "paper_2405_02019_gb300", "csrc")
-    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("kernels.cu", "internal.hpp"))
-    return hashlib.sha256(src).hexdigest()[:16]
+    lines = []
+    for f in ("kernels.cu", "internal.hpp"):
+        for line in open(os.path.join(csrc, f), encoding="utf-8"):
+            code = line.strip()
+            if code and not code.startswith("//"):
+                lines.append(code)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
 
 
 def _recorded_traffic(kernel: str):
