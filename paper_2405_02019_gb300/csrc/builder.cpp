@@ -549,7 +549,7 @@ bool pack_blocked(HostNetwork &net, int nthreads, int num_sms, std::string &why)
     // padded segment lengths give the row lengths
     net.seg.assign(static_cast<size_t>(n) * (B + 1), 0);
     std::vector<int64_t> rp(n + 1, 0);
-    bool too_long = false;
+    std::atomic<bool> too_long{false};
     parallel_for(nthreads, n, [&](int, int64_t lo, int64_t hi) {
         std::vector<int64_t> cnt(B);
         for (int64_t i = lo; i < hi; ++i) {
@@ -560,7 +560,7 @@ bool pack_blocked(HostNetwork &net, int nthreads, int num_sms, std::string &why)
             for (int b = 0; b < B; ++b) {
                 sg[b] = static_cast<uint16_t>(run);
                 run += (cnt[b] + kBlockQuad - 1) / kBlockQuad * kBlockQuad;
-                if (run > 65535) too_long = true;
+                if (run > 65535) too_long.store(true, std::memory_order_relaxed);
             }
             sg[B] = static_cast<uint16_t>(run);
             rp[i + 1] = run;

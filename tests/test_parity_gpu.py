@@ -784,6 +784,42 @@ def test_blocked_hand_placed_spike_arrival(t1, d):
     net.close()
 
 
+def test_blocked_checkpoint_and_profiling_path(model, tiny):
+    """Blocked records through a checkpoint, a resume after diverging steps and the
+    kernel-by-kernel profiling path: the oracle's raster and state."""
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=BLK,
+                      steps_per_graph=64)
+    net.step(150)
+    blob = net.save_state()
+    first = net.read_spikes()
+    net.step(77)
+    net.load_state(blob)
+    net.profile_steps(50)
+    net.step(100)
+    g_t, g_i = net.read_spikes()
+    g_t = np.concatenate([first[0], g_t])
+    g_i = np.concatenate([first[1], g_i])
+    sim = oracle.Sim(model, onet, wl.seed)
+    o_t, o_i = sim.run(300)
+    assert np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
+    _assert_same_state(net, sim)
+    net.close()
+
+
+def test_blocked_rejects_rows_beyond_16_bit_offsets():
+    """Segment offsets are 16-bit: a row of more than 65,535 (padded) synapses is refused."""
+    m = workload.microcircuit_model()
+    n = 40
+    L = 70000
+    custom = dict(pre=[0] * L, post=list(np.arange(L) % n), w_fx=[1000] * L, delay=[1] * L,
+                  u0=np.zeros(n, np.float32), pop_offsets=[0] + [n] * 8)
+    with pytest.raises(snn.SnnError):
+        snn.Network(m, custom=custom, record_format=BLK)
+    net = snn.Network(m, custom=custom)  # plain records take it
+    net.close()
+
+
 def test_blocked_rejects_other_engines_and_batches(model):
     for eng in (PIPE, PERSIST):
         with pytest.raises(snn.SnnError):
