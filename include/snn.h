@@ -282,6 +282,18 @@ int snn_step_n(snn_net *net, int64_t n_steps, void *cuda_stream);
  * persistent-engine barrier timed out, SNN_ECUDA. */
 int snn_read_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t capacity, int64_t *n_written);
 
+/* Overlapped reads: like snn_read_spikes, but waits only for the steps enqueued before
+ * the most recent snn_step_n call and returns spikes of those steps; the most recent
+ * call's steps may still be running.  A loop of { snn_step_n; snn_collect_spikes } thus
+ * moves one batch of spikes to the host while the GPU computes the next; a final
+ * snn_read_spikes returns the rest.  Spikes are returned once, by whichever call reads
+ * them first, ordered by (step, neuron).  With steps == neurons == NULL it only reports
+ * the number available.  When the device raster is more than a quarter full it waits
+ * for every enqueued step (as snn_read_spikes), since the raster is only reset while the
+ * device is idle: raster_capacity should hold three calls' spikes.  Errors: as
+ * snn_read_spikes; a pending device error is reported. */
+int snn_collect_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t capacity, int64_t *n_written);
+
 /* Waits for the enqueued steps and returns the mean firing rate (Hz) of each
  * population over steps [t_begin, t_end) (§4.1's rate statistic), from all spikes
  * recorded so far (pooled over the circuits of a batch).  pop_rates_hz has n_pops entries; neuron_counts (n_neurons

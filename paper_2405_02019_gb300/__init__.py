@@ -132,20 +132,23 @@ def snn_step_n(handle: int, n_steps: int, stream: int) -> None:
     _check(load().snn_step_n(C.c_void_p(handle), int(n_steps), C.c_void_p(stream)), "snn_step_n")
 
 
-def snn_read_spikes(handle: int, allow_overflow: bool = False):
-    """All unread spikes as (steps int64[k], neurons int32[k]), ordered by (step, neuron)."""
+def snn_read_spikes(handle: int, allow_overflow: bool = False, collect: bool = False):
+    """All unread spikes as (steps int64[k], neurons int32[k]), ordered by (step, neuron);
+    with collect=True only those of the calls before the latest snn_step_n
+    (snn_collect_spikes, which does not wait for the latest call)."""
     lib = load()
+    fn, name = (lib.snn_collect_spikes, "snn_collect_spikes") if collect else (lib.snn_read_spikes, "snn_read_spikes")
     n = C.c_int64()
-    code = lib.snn_read_spikes(C.c_void_p(handle), None, None, 0, C.byref(n))
+    code = fn(C.c_void_p(handle), None, None, 0, C.byref(n))
     if code and not (allow_overflow and code == SNN_EOVERFLOW):
-        _check(code, "snn_read_spikes")
+        _check(code, name)
     steps = np.empty(n.value, np.int64)
     neurons = np.empty(n.value, np.int32)
     got = C.c_int64()
-    code = lib.snn_read_spikes(C.c_void_p(handle), C.c_void_p(_ptr(steps) if n.value else 0),
-                               C.c_void_p(_ptr(neurons) if n.value else 0), n.value, C.byref(got))
+    code = fn(C.c_void_p(handle), C.c_void_p(_ptr(steps) if n.value else 0),
+              C.c_void_p(_ptr(neurons) if n.value else 0), n.value, C.byref(got))
     if code and not (allow_overflow and code == SNN_EOVERFLOW):
-        _check(code, "snn_read_spikes")
+        _check(code, name)
     return steps[: got.value], neurons[: got.value]
 
 
@@ -229,6 +232,11 @@ class Network:
 
     def read_spikes(self, allow_overflow: bool = False):
         return snn_read_spikes(self._handle, allow_overflow)
+
+    def collect_spikes(self):
+        """Spikes of the steps enqueued before the latest step() call, without waiting for
+        that call (snn_collect_spikes): overlaps the host read with the GPU's next batch."""
+        return snn_read_spikes(self._handle, False, collect=True)
 
     def read_rates(self, t_begin: int, t_end: int):
         return snn_read_rates(self._handle, t_begin, t_end, self.n_pops, self.n_neurons)

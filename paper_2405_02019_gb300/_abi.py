@@ -127,6 +127,7 @@ PROTOTYPES = {
     "snn_get_circuits": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "snn_set_schedule": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32]),
     "snn_set_circuit_groups": (C.c_int, [C.c_void_p, C.c_int32]),
+    "snn_collect_spikes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "snn_save_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64, C.POINTER(C.c_uint64)]),
     "snn_load_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint64]),
     "snn_deliver_spikes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_void_p]),

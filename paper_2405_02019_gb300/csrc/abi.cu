@@ -76,6 +76,18 @@ struct snn_net {
     int64_t events_read = 0;
     int32_t *pin_nrn = nullptr, *pin_t = nullptr;
     int64_t pin_cap = 0;
+    // overlapped reads: every snn_step_n ends by copying the device raster cursor into
+    // snap_cursor[call mod kSnaps] (pinned) and recording snap_ev there; raster_read is
+    // the device raster index up to which spikes are already in the host history
+    static constexpr int kSnaps = 4;
+    uint32_t *snap_cursor = nullptr;
+    cudaEvent_t snap_ev[kSnaps] = {};
+    int64_t snap_t[kSnaps] = {};   // steps enqueued at each snapshot
+    int64_t n_snaps = 0;           // snapshots recorded
+    int64_t snaps_valid_from = 0;  // earlier snapshots predate the last cursor reset
+    int64_t raster_read = 0;
+    int64_t collected_t = 0;       // spikes of steps below this are in the host history
+    cudaStream_t copy_stream = nullptr;
     // graph engine, batches: circuits per group (0 = one group) and each group's update
     // arguments and grid; empty when the whole index space updates in one launch
     int32_t circuits_per_group = 0;
@@ -209,7 +221,72 @@ int wait_done(snn_net *net)
     return SNN_OK;
 }
 
-// Move the device raster to the host history and reset the device cursor.
+// Raster entries [lo, hi) of the device raster into the host history, ordered by
+// (step, neuron), through the handle's copy stream (the steps that wrote them are done).
+int append_raster(snn_net *net, int64_t lo, int64_t hi)
+{
+    const int64_t cnt = hi - lo;
+    if (cnt <= 0) return SNN_OK;
+    if (cnt > net->pin_cap) {
+        if (net->pin_nrn) cudaFreeHost(net->pin_nrn);
+        if (net->pin_t) cudaFreeHost(net->pin_t);
+        net->pin_nrn = net->pin_t = nullptr;
+        net->pin_cap = 0;
+        const int64_t want = std::max<int64_t>(cnt, 1 << 16);
+        SNN_CUDA_TRY(cudaMallocHost(&net->pin_nrn, sizeof(int32_t) * want));
+        SNN_CUDA_TRY(cudaMallocHost(&net->pin_t, sizeof(int32_t) * want));
+        net->pin_cap = want;
+    }
+    const int32_t *dn = reinterpret_cast<const int32_t *>(net->arena + net->L.rast_nrn) + lo;
+    const int32_t *dt = reinterpret_cast<const int32_t *>(net->arena + net->L.rast_t) + lo;
+    SNN_CUDA_TRY(cudaMemcpyAsync(net->pin_nrn, dn, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, net->copy_stream));
+    SNN_CUDA_TRY(cudaMemcpyAsync(net->pin_t, dt, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost, net->copy_stream));
+    SNN_CUDA_TRY(cudaStreamSynchronize(net->copy_stream));
+    std::vector<int64_t> key(cnt);
+    bool steps_in_order = true;
+    for (int64_t j = 0; j < cnt; ++j) {
+        key[j] = (static_cast<int64_t>(net->pin_t[j]) << 32) | static_cast<uint32_t>(net->pin_nrn[j]);
+        if (j > 0 && net->pin_t[j] < net->pin_t[j - 1]) steps_in_order = false;
+    }
+    if (steps_in_order) {
+        // one step's spikes are contiguous (a few dozen at full scale): order each run
+        for (int64_t r0 = 0; r0 < cnt;) {
+            int64_t r1 = r0 + 1;
+            while (r1 < cnt && net->pin_t[r1] == net->pin_t[r0]) ++r1;
+            if (r1 - r0 > 64) {
+                std::sort(key.begin() + r0, key.begin() + r1);
+            } else {
+                for (int64_t j = r0 + 1; j < r1; ++j) {
+                    const int64_t v = key[j];
+                    int64_t m = j;
+                    while (m > r0 && key[m - 1] > v) {
+                        key[m] = key[m - 1];
+                        --m;
+                    }
+                    key[m] = v;
+                }
+            }
+            r0 = r1;
+        }
+    } else {
+        std::sort(key.begin(), key.end());  // circuit groups write runs of steps group by group
+    }
+    // the range covers whole steps after every step already in the history (a snapshot
+    // ends an snn_step_n call), so appending keeps the history ordered
+    const size_t base = net->hist_t.size();
+    net->hist_t.resize(base + cnt);
+    net->hist_i.resize(base + cnt);
+    for (int64_t j = 0; j < cnt; ++j) {
+        net->hist_t[base + j] = static_cast<int32_t>(key[j] >> 32);
+        const int32_t i = static_cast<int32_t>(key[j] & 0xFFFFFFFFll);
+        net->hist_i[base + j] = i;
+        net->events_read += net->out_degree[i];
+    }
+    return SNN_OK;
+}
+
+// Waits for every enqueued step, moves the rest of the device raster to the host
+// history and resets the device cursor.
 int drain(snn_net *net)
 {
     int rc = wait_done(net);
@@ -217,46 +294,40 @@ int drain(snn_net *net)
     snn::Ctl ctl;
     SNN_CUDA_TRY(cudaMemcpy(&ctl, net->arena + net->L.ctl, sizeof(ctl), cudaMemcpyDeviceToHost));
     net->device_error |= ctl.err;
-    const int64_t cap = net->L.rast_cap;
-    const int64_t cnt = std::min<int64_t>(ctl.cursor, cap);
-    if (cnt > 0) {
-        if (cnt > net->pin_cap) {
-            if (net->pin_nrn) cudaFreeHost(net->pin_nrn);
-            if (net->pin_t) cudaFreeHost(net->pin_t);
-            net->pin_nrn = net->pin_t = nullptr;
-            net->pin_cap = 0;
-            const int64_t want = std::max<int64_t>(cnt, 1 << 16);
-            SNN_CUDA_TRY(cudaMallocHost(&net->pin_nrn, sizeof(int32_t) * want));
-            SNN_CUDA_TRY(cudaMallocHost(&net->pin_t, sizeof(int32_t) * want));
-            net->pin_cap = want;
-        }
-        SNN_CUDA_TRY(cudaMemcpy(net->pin_nrn, net->arena + net->L.rast_nrn, sizeof(int32_t) * cnt,
-                                cudaMemcpyDeviceToHost));
-        SNN_CUDA_TRY(cudaMemcpy(net->pin_t, net->arena + net->L.rast_t, sizeof(int32_t) * cnt,
-                                cudaMemcpyDeviceToHost));
-        std::vector<int64_t> key(cnt);
-        for (int64_t j = 0; j < cnt; ++j)
-            key[j] = (static_cast<int64_t>(net->pin_t[j]) << 32) | static_cast<uint32_t>(net->pin_nrn[j]);
-        std::sort(key.begin(), key.end());
-        const size_t base = net->hist_t.size();
-        net->hist_t.resize(base + cnt);
-        net->hist_i.resize(base + cnt);
-        for (int64_t j = 0; j < cnt; ++j) {
-            net->hist_t[base + j] = static_cast<int32_t>(key[j] >> 32);
-            const int32_t i = static_cast<int32_t>(key[j] & 0xFFFFFFFFll);
-            net->hist_i[base + j] = i;
-            net->events_read += net->out_degree[i];
-        }
-    }
+    const int64_t cnt = std::min<int64_t>(ctl.cursor, net->L.rast_cap);
+    rc = append_raster(net, std::min(net->raster_read, cnt), cnt);
+    if (rc) return rc;
     if (ctl.cursor != 0) {
         uint32_t zero[3] = {0, 0, 0};  // cursor, step_begin[0], step_begin[1]
         SNN_CUDA_TRY(cudaMemcpy(net->arena + net->L.ctl + offsetof(snn::Ctl, cursor), zero, sizeof(zero),
                                 cudaMemcpyHostToDevice));
     }
+    net->raster_read = 0;
+    net->snaps_valid_from = net->n_snaps;  // their cursors refer to the raster before the reset
+    net->collected_t = net->t;
     if (net->device_error & snn::kErrTimeout)
         return fail(SNN_ETIMEOUT, "a grid barrier of the persistent engine timed out");
     if (net->device_error & snn::kErrRaster)
         return fail(SNN_EOVERFLOW, "device raster filled before it was read; raise raster_capacity");
+    return SNN_OK;
+}
+
+// Moves the spikes of the calls before the latest snn_step_n into the host history
+// without waiting for the latest call.  Falls back to drain() when the device raster is
+// more than a quarter full: the cursor is only reset while the device is idle, and up to
+// two more calls' spikes are written before the next chance.
+int collect(snn_net *net)
+{
+    const int64_t j = net->n_snaps - 2;
+    if (j < 0 || j < net->snaps_valid_from) return SNN_OK;
+    const int slot = static_cast<int>(j % snn_net::kSnaps);
+    SNN_CUDA_TRY(cudaEventSynchronize(net->snap_ev[slot]));
+    const int64_t cur = net->snap_cursor[slot];
+    if (cur > net->L.rast_cap / 4) return drain(net);
+    const int rc = append_raster(net, net->raster_read, std::max(net->raster_read, cur));
+    if (rc) return rc;
+    net->raster_read = std::max(net->raster_read, cur);
+    net->collected_t = std::max(net->collected_t, net->snap_t[slot]);
     return SNN_OK;
 }
 
@@ -517,6 +588,13 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         rc = (net->engine == SNN_ENGINE_GRAPH || net->engine == SNN_ENGINE_PIPELINED) ? capture_graph(net) : SNN_OK;
         if (rc == SNN_OK && cudaEventCreateWithFlags(&net->ev_done, cudaEventDisableTiming) != cudaSuccess)
             rc = fail(SNN_ECUDA, "event create");
+        for (int k = 0; k < snn_net::kSnaps && rc == SNN_OK; ++k)
+            if (cudaEventCreateWithFlags(&net->snap_ev[k], cudaEventDisableTiming) != cudaSuccess)
+                rc = fail(SNN_ECUDA, "event create");
+        if (rc == SNN_OK && cudaMallocHost(&net->snap_cursor, sizeof(uint32_t) * snn_net::kSnaps) != cudaSuccess)
+            rc = fail(SNN_ECUDA, "pinned snapshot slots");
+        if (rc == SNN_OK && cudaStreamCreateWithFlags(&net->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+            rc = fail(SNN_ECUDA, "copy stream");
         if (rc != SNN_OK) {
             snn_destroy(net);
             return rc;
@@ -561,6 +639,13 @@ int snn_step_n(snn_net *net, int64_t n_steps, void *cuda_stream)
     SNN_CUDA_TRY(cudaEventRecord(net->ev_done, st));
     net->ev_recorded = true;
     net->t += n_steps;
+    // where the raster ends after these steps, for snn_collect_spikes
+    const int slot = static_cast<int>(net->n_snaps % snn_net::kSnaps);
+    SNN_CUDA_TRY(cudaMemcpyAsync(net->snap_cursor + slot, net->arena + net->L.ctl + offsetof(snn::Ctl, cursor),
+                                 sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    SNN_CUDA_TRY(cudaEventRecord(net->snap_ev[slot], st));
+    net->snap_t[slot] = net->t;
+    net->n_snaps += 1;
     return SNN_OK;
 }
 
@@ -621,15 +706,14 @@ int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *
     return SNN_OK;
 }
 
-int snn_read_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t capacity, int64_t *n_written)
+namespace {
+
+// Copies history entries of steps below t_done, from the read position on.
+int read_history(snn_net *net, int64_t t_done, int64_t *steps, int32_t *neurons, int64_t capacity,
+                 int64_t *n_written, int rc)
 {
-    if (!net || !n_written) return fail(SNN_EINVAL, "null argument");
-    *n_written = 0;
-    int rc = drain(net);
-    // the pipelined engine has already decided (and recorded) the next step's spikes:
-    // return only spikes of completed steps
     const int64_t done_end =
-        std::lower_bound(net->hist_t.begin(), net->hist_t.end(), static_cast<int32_t>(std::min<int64_t>(net->t, INT32_MAX))) -
+        std::lower_bound(net->hist_t.begin(), net->hist_t.end(), static_cast<int32_t>(std::min<int64_t>(t_done, INT32_MAX))) -
         net->hist_t.begin();
     const int64_t avail = std::max<int64_t>(0, done_end - net->read_pos);
     if (!steps && !neurons) {
@@ -645,6 +729,27 @@ int snn_read_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t capa
     net->read_pos += m;
     *n_written = m;
     return rc;
+}
+
+}  // namespace
+
+int snn_read_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t capacity, int64_t *n_written)
+{
+    if (!net || !n_written) return fail(SNN_EINVAL, "null argument");
+    *n_written = 0;
+    const int rc = drain(net);
+    // only spikes of completed steps (the pipelined engine has already decided the next
+    // step's spikes, but keeps them in its queue)
+    return read_history(net, net->t, steps, neurons, capacity, n_written, rc);
+}
+
+int snn_collect_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t capacity, int64_t *n_written)
+{
+    if (!net || !n_written) return fail(SNN_EINVAL, "null argument");
+    *n_written = 0;
+    if (net->device_error) return drain(net);  // report it now
+    const int rc = collect(net);
+    return read_history(net, net->collected_t, steps, neurons, capacity, n_written, rc);
 }
 
 int snn_read_rates(snn_net *net, int64_t t_begin, int64_t t_end, double *pop_rates_hz, int32_t *neuron_counts)
@@ -821,6 +926,9 @@ int snn_load_state(snn_net *net, const void *host_buf, uint64_t bytes)
     net->hist_t.clear();
     net->hist_i.clear();
     net->read_pos = 0;
+    net->raster_read = 0;
+    net->snaps_valid_from = net->n_snaps;
+    net->collected_t = h.t;
     net->events_read = 0;
     net->device_error = 0;
     return SNN_OK;
@@ -913,6 +1021,10 @@ void snn_destroy(snn_net *net)
     if (net->graph) cudaGraphDestroy(net->graph);
     if (net->capture_stream) cudaStreamDestroy(net->capture_stream);
     if (net->ev_done) cudaEventDestroy(net->ev_done);
+    for (int k = 0; k < snn_net::kSnaps; ++k)
+        if (net->snap_ev[k]) cudaEventDestroy(net->snap_ev[k]);
+    if (net->snap_cursor) cudaFreeHost(net->snap_cursor);
+    if (net->copy_stream) cudaStreamDestroy(net->copy_stream);
     if (net->pin_nrn) cudaFreeHost(net->pin_nrn);
     if (net->pin_t) cudaFreeHost(net->pin_t);
     delete net;

@@ -168,6 +168,61 @@ def test_incremental_reads_and_rates(model, tiny, engine):
     net.close()
 
 
+def _collect_run(net, calls, overlapped=True):
+    """step(n); collect_spikes() for every n, then a blocking read; returns the raster.
+    overlapped: no collect may fall back to waiting (the raster is large enough), so each
+    returns steps of earlier calls only."""
+    parts, t = [], 0
+    for n in calls:
+        net.step(n)
+        st, si = net.collect_spikes()
+        assert len(st) == 0 or st.max() < (t if overlapped else t + n)
+        assert np.all(np.diff(st) >= 0)
+        parts.append((st, si))
+        t += n
+    parts.append(net.read_spikes())
+    g_t = np.concatenate([p[0] for p in parts])
+    g_i = np.concatenate([p[1] for p in parts])
+    order = np.lexsort((g_i, g_t))
+    assert np.array_equal(order, np.arange(len(g_t)))  # ordered by (step, neuron) overall
+    return g_t, g_i
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_collect_overlapped_reads(model, tiny, engine):
+    """Overlapped reads (snn_collect_spikes after every step call, uneven call sizes,
+    graph replays and remainders) return the oracle's raster, each spike once."""
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, steps_per_graph=64,
+                      engine=engine)
+    calls = [1, 7, 120, 372, 64, 100, 136]
+    g_t, g_i = _collect_run(net, calls)
+    o_t, o_i = oracle.Sim(model, onet, wl.seed).run(sum(calls))
+    assert np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
+    net.close()
+
+
+def test_collect_small_raster_and_circuit_groups(model, tiny):
+    """A raster that holds about four calls' spikes (collect falls back to waiting reads),
+    and circuit groups (a call's raster is not in step order)."""
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, steps_per_graph=64,
+                      raster_capacity=10000)
+    g_t, g_i = _collect_run(net, [100] * 8, overlapped=False)
+    o_t, o_i = oracle.Sim(model, onet, wl.seed).run(800)
+    assert np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
+    net.close()
+    ref = snn.Network(model, circuits=BATCH, steps_per_graph=64, engine=GRAPH)
+    ref.step(300)
+    r_t, r_i = ref.read_spikes()
+    ref.close()
+    net = snn.Network(model, circuits=BATCH, steps_per_graph=64, engine=GRAPH)
+    net.set_circuit_groups(2)
+    g_t, g_i = _collect_run(net, [64, 100, 36, 100])
+    assert np.array_equal(g_t, r_t) and np.array_equal(g_i, r_i)
+    net.close()
+
+
 @pytest.mark.parametrize("engine", ENGINES)
 def test_profile_steps_same_dynamics(model, tiny, engine):
     """The kernel-by-kernel timing path computes the same steps as either engine, and
