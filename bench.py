@@ -47,7 +47,6 @@ TICKS_PER_STEP = 1024
 UPDATE_BYTES_PER_NEURON = 26   # U r/w 8 + I r/w 8 + R r/w 2 + ring slot read + clear 8
 EVENT_BYTES = 13               # tgt 4 + w 4 + delay 1 read + 4-byte ring reduction
 SPIKE_BYTES = 20               # row_ptr pair 16 + queue entry 4
-BLOCKED_EVENT_BYTES = 6        # blocked records: uint16 local target | delay + int32 weight
 WORKLOAD = "pd_full"
 METRIC = "synaptic events/s and real-time factor (full microcircuit, 1 GB300), % HBM roofline"
 
@@ -440,11 +439,12 @@ def run_gpu(args):
 
     # compressed synapse records on the same workload: step time and saturating delivery
     forms = {}
+    blocked_formats = (snn.RECORD_BLOCKED6, snn.RECORD_BLOCKED4)
     for fname, fmt in (("int8_pair", snn.RECORD_PACKED_I8), ("bf16", snn.RECORD_PACKED_BF16),
-                       ("blocked6", snn.RECORD_BLOCKED6)):
+                       ("blocked6", snn.RECORD_BLOCKED6), ("blocked4", snn.RECORD_BLOCKED4)):
         if fname not in args.forms:
             continue
-        feng = snn.ENGINE_DEFAULT if fmt == snn.RECORD_BLOCKED6 else engine
+        feng = snn.ENGINE_DEFAULT if fmt in blocked_formats else engine
         fnet = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, seed, steps_per_graph=tps,
                            raster_capacity=1 << 25, device=dev, engine=feng, record_format=fmt)
         fnet.step(args.warmup * tps)
@@ -463,7 +463,7 @@ def run_gpu(args):
         fev = fnet.info().events_read - fe0
         fsat = []
         finfo = fnet.info()
-        blocked = fmt == snn.RECORD_BLOCKED6
+        blocked = fmt in blocked_formats
         for nsp in (args.saturating if blocked else args.saturating[-1:]):
             ms_l, ev_l, nnz_l = [], [], []
             ring = fnet.device_view("ring", torch.int32, 64 * int(fnet.layout().n_neurons_padded)) if blocked else None
@@ -489,12 +489,12 @@ def run_gpu(args):
             pt = {"spikers": nsp, "events": ev_avg, "ms": ms_avg, "events_per_s": ev_avg / (ms_avg * 1e-3),
                   "speedup_vs_plain": float(plain_ms[0] / ms_avg) if plain_ms else None}
             if blocked:
-                # the blocked kernel's own algorithmic bytes: 6 B records per event; per
+                # the blocked kernel's own algorithmic bytes: its record bytes per event; per
                 # sender its list entry, row start and block-table row; 8 B (read + write)
                 # per ring entry it updates
                 nnz = float(np.mean(nnz_l))
                 nb = finfo.target_blocks
-                nbytes = BLOCKED_EVENT_BYTES * ev_avg + (12 + 2 * (nb + 1)) * nsp + 8 * nnz
+                nbytes = finfo.bytes_per_synapse * ev_avg + (12 + 2 * (nb + 1)) * nsp + 8 * nnz
                 pt.update({"ring_entries_updated": nnz, "bytes": nbytes, "gbs": nbytes / (ms_avg * 1e-3) / 1e9,
                            "frac": nbytes / (ms_avg * 1e-3) / 1e9 / peak,
                            "plain_equivalent_gbs": (EVENT_BYTES * ev_avg + SPIKE_BYTES * nsp) / (ms_avg * 1e-3) / 1e9})
@@ -623,7 +623,10 @@ def run_gpu(args):
                                              "note": "one CTA per target block, sums in shared memory; frac on "
                                                      "its own bytes (6 B per event, sender index, 8 B per ring "
                                                      "entry updated)",
-                                             "points": forms.get("blocked6", {}).get("delivery_saturating")}},
+                                             "points": forms.get("blocked6", {}).get("delivery_saturating")},
+                                "blocked4": {"kernel": "k_deliver_blocked",
+                                             "note": "the same with bfloat16 weights (4 B per event)",
+                                             "points": forms.get("blocked4", {}).get("delivery_saturating")}},
         "clocks": clk.summary(), "build_s": build_s,
         "paper_context": {"fpga_best_rtf": 0.79, "hardware": "Intel Agilex 7 FPGA (horiz/multi/s)"},
     }
@@ -662,7 +665,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--saturating", type=int, nargs="*", default=[2048, 8192, 20480])
     ap.add_argument("--saturating-reps", type=int, default=5)
-    ap.add_argument("--forms", nargs="*", default=["int8_pair", "bf16", "blocked6"])
+    ap.add_argument("--forms", nargs="*", default=["int8_pair", "bf16", "blocked6", "blocked4"])
     ap.add_argument("--extra", nargs="*", default=["batched", "x4"])
     ap.add_argument("--batched-steps", type=int, default=20480)
     ap.add_argument("--x4-steps", type=int, default=10240)

@@ -160,6 +160,10 @@ typedef struct snn_circuit {
  *                           int32 weight: 6 bytes.  Delivery runs one CTA per block, which
  *                           sums the block's events in shared memory before it adds them
  *                           to the ring.  One circuit only; the engine is the graph engine.
+ *   SNN_RECORD_BLOCKED4:    the same target-blocked rows with the weight as the bfloat16
+ *                           current of SNN_RECORD_PACKED_BF16: every quad of a segment is
+ *                           one 16-byte unit (four uint16 records, then four bfloat16
+ *                           weights), 4 bytes per synapse.  Same rules as BLOCKED6.
  * Packed formats hold up to 2^20 neurons.  The dynamics are the plain ones applied to
  * the read-back weights (unchanged for SNN_RECORD_BLOCKED6); accumulation stays int32.
  */
@@ -167,6 +171,7 @@ typedef struct snn_circuit {
 #define SNN_RECORD_PACKED_I8 1
 #define SNN_RECORD_PACKED_BF16 2
 #define SNN_RECORD_BLOCKED6 3
+#define SNN_RECORD_BLOCKED4 4
 typedef struct snn_spec {
     uint32_t abi_version; /* must be SNN_ABI_VERSION */
     int32_t scale_n_permille;
@@ -205,7 +210,8 @@ typedef struct snn_sizes {
  * that deliver nothing); plain records: syn_tgt, syn_w int32[n_synapses_padded],
  * syn_delay uint8[...]; packed records: syn_tgt holds the uint32 words, syn_w the
  * int8 codes or bfloat16 currents, syn_delay is unused; blocked records: row_ptr holds
- * unpadded row offsets, syn_tgt the uint16 records, syn_w the int32 weights, syn_delay
+ * row offsets of quad-padded block segments, syn_tgt the uint16 records (BLOCKED4: the
+ * 16-byte quads of records and bfloat16 weights), syn_w the int32 weights (BLOCKED6), syn_delay
  * the uint16 table [n_neurons][target_blocks + 1] of each row's block starts relative
  * to its row start, and blocks the int32 block boundaries [target_blocks + 1];
  * rast_neuron, rast_step int32[raster_capacity]. */

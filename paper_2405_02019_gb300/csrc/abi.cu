@@ -100,7 +100,7 @@ namespace {
 // Phase 2 of graph-engine step t_base + k: blocked records have their own kernel.
 void launch_phase2(const snn_net *net, int k, cudaStream_t st)
 {
-    if (net->format == SNN_RECORD_BLOCKED6) snn::launch_deliver_blocked(net->args, nullptr, 0, 0, k, st);
+    if (snn::is_blocked(net->format)) snn::launch_deliver_blocked(net->args, nullptr, 0, 0, k, st);
     else snn::launch_deliver(net->args, k, net->deliver_grid, st);
 }
 
@@ -461,6 +461,15 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
                     "tgt");
             cuda_ok(cudaMemcpyAsync(A + L.syn_w, hn.w.data(), 4 * net->n_syn_padded, cudaMemcpyHostToDevice, st), "w");
             cuda_ok(cudaMemcpyAsync(A + L.syn_d, hn.d.data(), net->n_syn_padded, cudaMemcpyHostToDevice, st), "d");
+        } else if (hn.format == SNN_RECORD_BLOCKED4) {
+            if (net->n_syn_padded > 0)
+                cuda_ok(cudaMemcpyAsync(A + L.syn_tgt, hn.word.data(), 4 * net->n_syn_padded, cudaMemcpyHostToDevice,
+                                        st),
+                        "record quads");
+            cuda_ok(cudaMemcpyAsync(A + L.syn_d, hn.seg.data(), 2 * hn.seg.size(), cudaMemcpyHostToDevice, st),
+                    "block table");
+            cuda_ok(cudaMemcpyAsync(A + L.blocks, hn.blk.data(), 4 * hn.blk.size(), cudaMemcpyHostToDevice, st),
+                    "blocks");
         } else if (hn.format == SNN_RECORD_BLOCKED6) {
             if (net->n_syn_padded > 0) {
                 cuda_ok(cudaMemcpyAsync(A + L.syn_tgt, hn.rec16.data(), 2 * net->n_syn_padded, cudaMemcpyHostToDevice,
@@ -511,7 +520,7 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         a.blk_rec = reinterpret_cast<const uint16_t *>(A + L.syn_tgt);
         a.blk_seg = reinterpret_cast<const uint16_t *>(A + L.syn_d);
         a.blk_off = reinterpret_cast<const int32_t *>(A + L.blocks);
-        a.n_blocks = hn.format == SNN_RECORD_BLOCKED6 ? static_cast<int32_t>(hn.blk.size()) - 1 : 0;
+        a.n_blocks = snn::is_blocked(hn.format) ? static_cast<int32_t>(hn.blk.size()) - 1 : 0;
         a.p11 = net->c.p11f;
         a.p21 = net->c.p21f;
         a.p22 = net->c.p22f;
@@ -536,9 +545,9 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         net->deliver_grid = spec->deliver_blocks > 0 ? spec->deliver_blocks : 2 * net->num_sms;
         net->steps_per_graph = spec->steps_per_graph > 0 ? spec->steps_per_graph : 1000;
         net->engine = spec->engine != SNN_ENGINE_DEFAULT     ? spec->engine
-                      : net->format == SNN_RECORD_BLOCKED6 ? SNN_ENGINE_GRAPH
+                      : snn::is_blocked(net->format)       ? SNN_ENGINE_GRAPH
                                                            : SNN_ENGINE_PIPELINED;
-        if (net->format == SNN_RECORD_BLOCKED6 && snn::prepare_blocked_kernel() != 0) {
+        if (snn::is_blocked(net->format) && snn::prepare_blocked_kernel() != 0) {
             snn_destroy(net);
             return fail(SNN_ECUDA, "shared memory opt-in of the blocked delivery kernel failed");
         }
@@ -1002,7 +1011,7 @@ int snn_deliver_spikes(snn_net *net, const int32_t *spikers, int64_t n_spikers, 
     if (!net || (n_spikers > 0 && !spikers)) return fail(SNN_EINVAL, "null argument");
     if (n_spikers < 0 || t < 0 || blocks < 0) return fail(SNN_EINVAL, "negative argument");
     if (n_spikers == 0) return SNN_OK;
-    if (net->format == SNN_RECORD_BLOCKED6) {
+    if (snn::is_blocked(net->format)) {
         snn::launch_deliver_blocked(net->args, spikers, n_spikers, t, 0, cuda_stream);
         SNN_CUDA_TRY(cudaGetLastError());
         return SNN_OK;

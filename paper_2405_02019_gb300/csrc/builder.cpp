@@ -215,12 +215,12 @@ bool validate_spec(const snn_spec &spec, std::string &why)
     if (spec.steps_per_graph < 0 || spec.steps_per_graph > 100000) return fail("steps_per_graph out of [0, 100000]");
     if (spec.deliver_blocks < 0 || spec.deliver_blocks > 65535) return fail("deliver_blocks out of range");
     if (spec.engine < SNN_ENGINE_DEFAULT || spec.engine > SNN_ENGINE_PIPELINED) return fail("unknown engine");
-    if (spec.record_format < SNN_RECORD_PLAIN9 || spec.record_format > SNN_RECORD_BLOCKED6)
+    if (spec.record_format < SNN_RECORD_PLAIN9 || spec.record_format > SNN_RECORD_BLOCKED4)
         return fail("unknown record_format");
     if ((spec.record_format == SNN_RECORD_PACKED_I8 || spec.record_format == SNN_RECORD_PACKED_BF16) &&
         count_neurons(spec) > kPackedMaxNeurons)
         return fail("packed records hold at most 2^20 neurons");
-    if (spec.record_format == SNN_RECORD_BLOCKED6) {
+    if (is_blocked(spec.record_format)) {
         if (spec.n_circuits > 0) return fail("blocked records take one circuit");
         if (spec.engine == SNN_ENGINE_PERSISTENT || spec.engine == SNN_ENGINE_PIPELINED)
             return fail("blocked records run on the graph engine");
@@ -295,19 +295,25 @@ Layout make_layout(const snn_spec &spec)
     L.row_ptr = o; o = up(o + 8 * (n + 5));  // 4 spare entries: quads read row_ptr[i0 .. i0+4]
     const int fmt = spec.record_format;
     const uint64_t wbytes = fmt == SNN_RECORD_PACKED_I8 ? 1 : fmt == SNN_RECORD_PACKED_BF16 ? 2 : 4;
-    if (fmt == SNN_RECORD_BLOCKED6) {
-        // rows of quad-padded block segments: uint16 records, int32 weights, the per-row
-        // block table (a nonempty segment gains at most kBlockQuad - 1 pad entries)
+    if (is_blocked(fmt)) {
+        // rows of quad-padded block segments (a nonempty segment gains at most
+        // kBlockQuad - 1 pad entries): BLOCKED6 keeps uint16 records and int32 weights,
+        // BLOCKED4 16-byte quads of records and bfloat16 weights; then the per-row block table
         L.syn_padded_max = s + (kBlockQuad - 1) * std::min<int64_t>(s, n * int64_t{max_target_blocks(n)});
-        L.syn_tgt = o; o = up(o + 2 * L.syn_padded_max + 16);
-        L.syn_w = o; o = up(o + 4 * L.syn_padded_max + 16);
+        if (fmt == SNN_RECORD_BLOCKED6) {
+            L.syn_tgt = o; o = up(o + 2 * L.syn_padded_max + 16);
+            L.syn_w = o; o = up(o + 4 * L.syn_padded_max + 16);
+        } else {
+            L.syn_tgt = o; o = up(o + 4 * L.syn_padded_max + 16);
+            L.syn_w = o; o = up(o + 16);
+        }
         L.syn_d = o; o = up(o + 2 * uint64_t(n) * (max_target_blocks(n) + 1) + 16);
     } else {
         L.syn_tgt = o; o = up(o + 4 * L.syn_padded_max);
         L.syn_w = o; o = up(o + wbytes * L.syn_padded_max + 16);
         L.syn_d = o; o = up(o + (fmt == SNN_RECORD_PLAIN9 ? L.syn_padded_max : 0) + 16);
     }
-    L.blocks = o; o = up(o + 4 * (fmt == SNN_RECORD_BLOCKED6 ? max_target_blocks(n) + 1 : 1));
+    L.blocks = o; o = up(o + 4 * (is_blocked(fmt) ? max_target_blocks(n) + 1 : 1));
     L.rast_nrn = o; o = up(o + 4 * L.rast_cap);
     L.rast_t = o; o = up(o + 4 * L.rast_cap);
     L.U2 = o; o = up(o + 4 * L.npad);
@@ -588,10 +594,29 @@ bool pack_blocked(HostNetwork &net, int nthreads, int num_sms, std::string &why)
         }
     });
     net.row_ptr = std::move(rp);
-    net.w = std::move(w);
     net.n_syn_padded = S;
     std::vector<int32_t>().swap(net.tgt);
     std::vector<uint8_t>().swap(net.d);
+    if (net.format == SNN_RECORD_BLOCKED4) {
+        // quad q: words 4q, 4q+1 hold records 4q..4q+3, words 4q+2, 4q+3 their bfloat16
+        // currents (round to nearest even, the SNN_RECORD_PACKED_BF16 weights)
+        net.word.assign(S, 0);
+        parallel_for(nthreads, S / kBlockQuad, [&](int, int64_t q0, int64_t q1) {
+            for (int64_t q = q0; q < q1; ++q) {
+                const int64_t e = q * kBlockQuad;
+                uint16_t h[4];
+                for (int k = 0; k < 4; ++k) h[k] = to_bf16_even(static_cast<float>(w[e + k]) * (1.0f / 4096.0f));
+                net.word[e] = uint32_t{net.rec16[e]} | uint32_t{net.rec16[e + 1]} << 16;
+                net.word[e + 1] = uint32_t{net.rec16[e + 2]} | uint32_t{net.rec16[e + 3]} << 16;
+                net.word[e + 2] = uint32_t{h[0]} | uint32_t{h[1]} << 16;
+                net.word[e + 3] = uint32_t{h[2]} | uint32_t{h[3]} << 16;
+            }
+        });
+        std::vector<uint16_t>().swap(net.rec16);
+        std::vector<int32_t>().swap(net.w);
+    } else {
+        net.w = std::move(w);
+    }
     return true;
 }
 
@@ -798,7 +823,7 @@ bool build_one(const snn_spec &spec, const Constants &c, HostNetwork &net, std::
     for (int b = 0; b < m.n_pops; ++b)
         for (int64_t i = net.pop_off[b]; i < net.pop_off[b + 1]; ++i) net.pop_id[i] = static_cast<uint8_t>(b);
     net.format = spec.record_format;
-    if (net.format == SNN_RECORD_BLOCKED6) return pack_blocked(net, nthreads, num_sms, why);
+    if (is_blocked(net.format)) return pack_blocked(net, nthreads, num_sms, why);
     if (net.format != SNN_RECORD_PLAIN9) pack_records(net, spec.model.n_pops, nthreads);
     return true;
 }

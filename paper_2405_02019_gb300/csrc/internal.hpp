@@ -79,8 +79,12 @@ constexpr uint32_t kWordPad = 1u << 31;
 constexpr int64_t kPackedMaxNeurons = int64_t{1} << kWordTargetBits;
 inline int record_bytes(int format)
 {
-    return format == SNN_RECORD_PACKED_I8 ? 5 : format == SNN_RECORD_PACKED_BF16 || format == SNN_RECORD_BLOCKED6 ? 6 : 9;
+    return format == SNN_RECORD_PACKED_I8                                         ? 5
+           : format == SNN_RECORD_PACKED_BF16 || format == SNN_RECORD_BLOCKED6 ? 6
+           : format == SNN_RECORD_BLOCKED4                                      ? 4
+                                                                                : 9;
 }
+inline bool is_blocked(int format) { return format == SNN_RECORD_BLOCKED6 || format == SNN_RECORD_BLOCKED4; }
 
 // Blocked records: target blocks and the delivery kernel that owns one block per CTA.
 constexpr int kBlockLocalBits = 10;          // record = local target | delay << 10

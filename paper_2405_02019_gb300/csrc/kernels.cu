@@ -683,8 +683,9 @@ __global__ void __launch_bounds__(kStepMaxThreads, 2) k_prime(const StepArgs a)
 // stream is taken in windows of kBlockedWindow quads; for a window the record-array
 // index of every quad is written into a shared table, after which the quads are
 // independent work: warp w takes rounds w, w + 32, ... of 32 consecutive quads,
-// kBlockedRounds rounds at a time, issuing all their loads (8 bytes of records, 16 of
-// weights per quad) before adding any.
+// kBlockedRounds rounds at a time, issuing all their loads (per quad 8 bytes of records
+// and 16 of int32 weights, or one 16-byte unit of records and bfloat16 weights) before
+// adding any.
 // With many senders the weights of delays up to kBlockedBinDelays are summed per (delay,
 // local target) in shared memory and each nonzero sum is added to its ring entry once at
 // the end; only this CTA writes these ring columns during the launch, so that final add
@@ -745,14 +746,23 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *out,
     return warp_sums[kBlockedWarps - 1];
 }
 
-// Quads [w0, w1) of the staged stream; qidx[e - w0] is quad e's index in the record arrays.
-template <bool kAggregate>
+// bfloat16 current (pA) -> 2^-12 pA, as the SNN_RECORD_PACKED_BF16 read-back
+__device__ __forceinline__ int32_t bf16_fx(uint32_t h)
+{
+    return __float2int_rn(__fmul_rn(__uint_as_float((h & 0xFFFFu) << 16), 4096.0f));
+}
+
+// Quads [w0, w1) of the staged stream; qidx[e - w0] is quad e's index in the record
+// arrays: BLOCKED6 reads 8 bytes of records and 16 of int32 weights per quad, BLOCKED4
+// one 16-byte unit of records and bfloat16 weights.
+template <bool kAggregate, int FMT>
 __device__ __forceinline__ void blocked_window(const StepArgs &a, int32_t *bins, const uint32_t *qidx, int32_t w0,
                                                int32_t w1, int64_t t, int32_t base)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint2 *recq = reinterpret_cast<const uint2 *>(a.blk_rec);
     const int4 *wq = reinterpret_cast<const int4 *>(a.syn_w);
+    const uint4 *q16 = reinterpret_cast<const uint4 *>(a.blk_rec);
     // round k of a step is quads e0 + 32 * (warp + kBlockedWarps * k) + lane: the warps
     // of the CTA interleave, so that a window's rounds spread evenly over them
     for (int32_t e0 = w0; e0 < w1; e0 += kBlockedThreads * kBlockedRounds) {
@@ -763,21 +773,36 @@ __device__ __forceinline__ void blocked_window(const StepArgs &a, int32_t *bins,
             const int32_t e = e0 + 32 * (warp + kBlockedWarps * k) + lane;
             if (e < w1) {
                 const uint32_t q = qidx[e - w0];
-                rec[k] = __ldcs(recq + q);
-                w[k] = __ldcs(wq + q);
+                if (FMT == SNN_RECORD_BLOCKED4) {
+                    const uint4 v = __ldcs(q16 + q);
+                    rec[k] = make_uint2(v.x, v.y);
+                    w[k] = make_int4(static_cast<int32_t>(v.z), static_cast<int32_t>(v.w), 0, 0);  // decoded below
+                } else {
+                    rec[k] = __ldcs(recq + q);
+                    w[k] = __ldcs(wq + q);
+                }
             }
         }
 #pragma unroll
         for (int k = 0; k < kBlockedRounds; ++k) {
             if (e0 + 32 * (warp + kBlockedWarps * k) + lane >= w1) continue;
-            blocked_apply<kAggregate>(a, bins, t, base, rec[k].x & 0xffffu, w[k].x);
-            blocked_apply<kAggregate>(a, bins, t, base, rec[k].x >> 16, w[k].y);
-            blocked_apply<kAggregate>(a, bins, t, base, rec[k].y & 0xffffu, w[k].z);
-            blocked_apply<kAggregate>(a, bins, t, base, rec[k].y >> 16, w[k].w);
+            int32_t w0v = w[k].x, w1v = w[k].y, w2v = w[k].z, w3v = w[k].w;
+            if (FMT == SNN_RECORD_BLOCKED4) {
+                const uint32_t h01 = static_cast<uint32_t>(w[k].x), h23 = static_cast<uint32_t>(w[k].y);
+                w0v = bf16_fx(h01);
+                w1v = bf16_fx(h01 >> 16);
+                w2v = bf16_fx(h23);
+                w3v = bf16_fx(h23 >> 16);
+            }
+            blocked_apply<kAggregate>(a, bins, t, base, rec[k].x & 0xffffu, w0v);
+            blocked_apply<kAggregate>(a, bins, t, base, rec[k].x >> 16, w1v);
+            blocked_apply<kAggregate>(a, bins, t, base, rec[k].y & 0xffffu, w2v);
+            blocked_apply<kAggregate>(a, bins, t, base, rec[k].y >> 16, w3v);
         }
     }
 }
 
+template <int FMT>
 __global__ void __launch_bounds__(kBlockedThreads, 1)
     k_deliver_blocked(const StepArgs a, const int32_t *list, int64_t n_list, int64_t t_list, int k)
 {
@@ -863,8 +888,8 @@ __global__ void __launch_bounds__(kBlockedThreads, 1)
                 for (int32_t e = lo; e < hi; ++e) qidx[e - w0] = q0 + static_cast<uint32_t>(e);
             }
             __syncthreads();
-            if (aggregate) blocked_window<true>(a, bins, qidx, w0, w1, t, base);
-            else blocked_window<false>(a, bins, qidx, w0, w1, t, base);
+            if (aggregate) blocked_window<true, FMT>(a, bins, qidx, w0, w1, t, base);
+            else blocked_window<false, FMT>(a, bins, qidx, w0, w1, t, base);
             __syncthreads();  // the table is rebuilt for the next window
         }
     }
@@ -940,14 +965,22 @@ void launch_deliver_list(const StepArgs &a, const int32_t *list, int64_t n, int6
 
 int prepare_blocked_kernel()
 {
-    return static_cast<int>(cudaFuncSetAttribute(k_deliver_blocked, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(kBlockedSmemBytes)));
+    const int bytes = static_cast<int>(kBlockedSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(k_deliver_blocked<SNN_RECORD_BLOCKED6>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_deliver_blocked<SNN_RECORD_BLOCKED4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bytes);
+    return static_cast<int>(e);
 }
 
 void launch_deliver_blocked(const StepArgs &a, const int32_t *list, int64_t n, int64_t t, int k, void *stream)
 {
-    k_deliver_blocked<<<a.n_blocks, kBlockedThreads, kBlockedSmemBytes, static_cast<cudaStream_t>(stream)>>>(a, list, n,
-                                                                                                            t, k);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (a.format == SNN_RECORD_BLOCKED4)
+        k_deliver_blocked<SNN_RECORD_BLOCKED4><<<a.n_blocks, kBlockedThreads, kBlockedSmemBytes, st>>>(a, list, n, t, k);
+    else
+        k_deliver_blocked<SNN_RECORD_BLOCKED6><<<a.n_blocks, kBlockedThreads, kBlockedSmemBytes, st>>>(a, list, n, t, k);
 }
 
 int deliver_list_blocks_per_sm()

@@ -122,10 +122,14 @@ def test_blocked_records_sizes_and_rules(lib):
     # every nonempty (row, block) segment is padded to a whole quad of records
     assert S == plain.n_synapses and blk.n_synapses_padded_max == S + 3 * min(S, n * bmax)
     assert blk.arena_bytes < plain.arena_bytes
-    for engine in (snn.ENGINE_PIPELINED, snn.ENGINE_PERSISTENT):
-        spec = snn._Spec(m, 100, 100, 1, record_format=snn.RECORD_BLOCKED6, engine=engine).spec
-        with pytest.raises(snn.SnnError):
-            snn.snn_query_sizes(spec)
+    b4 = snn.snn_query_sizes(snn._Spec(m, 1000, 1000, 1, record_format=snn.RECORD_BLOCKED4).spec)
+    assert b4.n_synapses_padded_max == blk.n_synapses_padded_max
+    assert b4.arena_bytes < blk.arena_bytes - 2 * S  # 4 instead of 6 bytes per (padded) synapse
+    for fmt in (snn.RECORD_BLOCKED6, snn.RECORD_BLOCKED4):
+        for engine in (snn.ENGINE_PIPELINED, snn.ENGINE_PERSISTENT):
+            spec = snn._Spec(m, 100, 100, 1, record_format=fmt, engine=engine).spec
+            with pytest.raises(snn.SnnError):
+                snn.snn_query_sizes(spec)
     spec = snn._Spec(m, record_format=snn.RECORD_BLOCKED6, circuits=[(100, 100, 1), (200, 200, 2)]).spec
     with pytest.raises(snn.SnnError):
         snn.snn_query_sizes(spec)

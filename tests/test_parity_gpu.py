@@ -663,10 +663,17 @@ BATCH = [(20, 40, 5), (35, 10, 6), (13, 50, 7), (50, 50, 8), (1, 1, 9)]
 BLK = snn.RECORD_BLOCKED6
 
 
+def _bf16_fx(h):
+    """bfloat16 currents (uint16) read back as 2^-12 pA, as the device does."""
+    f = (h.astype(np.uint32) << 16).view(np.float32)
+    return np.rint(f * np.float32(4096.0)).astype(np.int32)
+
+
 def _check_blocked_structure(net, onet, rows=None):
     """Decodes the blocked records in the arena and compares them with the oracle's
     network: every synapse (rows=None) or the given rows exactly plus global sums.
-    Zero weights mark the padding that ends every (row, block) segment on a quad."""
+    Zero weights mark the padding that ends every (row, block) segment on a quad.
+    For BLOCKED4 `onet` must carry the read-back (bfloat16) weights."""
     info = net.info()
     n, B, S = net.n_neurons, info.target_blocks, info.n_synapses
     SP = int(net.layout().n_synapses_padded)
@@ -674,8 +681,13 @@ def _check_blocked_structure(net, onet, rows=None):
     rp = net.device_view("row_ptr", torch.int64, n + 1).cpu().numpy()
     seg = net.device_view("syn_delay", torch.int16, n * (B + 1)).cpu().numpy().view(np.uint16)
     seg = seg.reshape(n, B + 1).astype(np.int64)
-    rec = net.device_view("syn_tgt", torch.int16, SP).cpu().numpy().view(np.uint16)
-    w = net.device_view("syn_w", torch.int32, SP).cpu().numpy()
+    if info.record_format == snn.RECORD_BLOCKED4:
+        quads = net.device_view("syn_tgt", torch.int16, 2 * SP).cpu().numpy().view(np.uint16).reshape(-1, 8)
+        rec = np.ascontiguousarray(quads[:, :4]).reshape(-1)
+        w = _bf16_fx(np.ascontiguousarray(quads[:, 4:]).reshape(-1))
+    else:
+        rec = net.device_view("syn_tgt", torch.int16, SP).cpu().numpy().view(np.uint16)
+        w = net.device_view("syn_w", torch.int32, SP).cpu().numpy()
     assert blk[0] == 0 and blk[-1] == n and np.all(np.diff(blk) > 0)
     assert np.all(blk[1:-1] % 32 == 0) and np.all(np.diff(blk) <= 768)
     lens = np.diff(onet.row_ptr)
@@ -839,6 +851,70 @@ def test_blocked_hand_placed_spike_arrival(t1, d):
     net.close()
 
 
+BLK4 = snn.RECORD_BLOCKED4
+
+
+def test_blocked4_structure_and_raster_tiny(model, tiny):
+    """Blocked records with bfloat16 weights (4 bytes per synapse): the decoded network
+    equals the oracle's with its bfloat16 read-back weights, and 1,000 steps give the
+    raster of the oracle run on those weights and of the packed bf16 form, bit for bit."""
+    wl, onet = tiny
+    qnet = oracle.with_weights(onet, oracle.quantize_bf16(onet.w_fx))
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=BLK4,
+                      steps_per_graph=96)
+    info = net.info()
+    assert info.record_format == BLK4 and info.bytes_per_synapse == 4 and info.engine == GRAPH
+    _check_blocked_structure(net, qnet)
+    net.step(1000)
+    g_t, g_i = net.read_spikes()
+    sim = oracle.Sim(model, qnet, wl.seed)
+    o_t, o_i = sim.run(1000)
+    assert len(o_t) > 0 and np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
+    _assert_same_state(net, sim)
+    net.close()
+    pk = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=snn.RECORD_PACKED_BF16)
+    pk.step(1000)
+    p_t, p_i = pk.read_spikes()
+    assert np.array_equal(p_t, g_t) and np.array_equal(p_i, g_i)
+    pk.close()
+
+
+@pytest.mark.parametrize("nspk", [37, 700, 3000])
+def test_blocked4_deliver_spikes_matches_oracle_network(model, tiny, nspk):
+    wl, onet = tiny
+    qnet = oracle.with_weights(onet, oracle.quantize_bf16(onet.w_fx))
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=BLK4)
+    spikers = np.random.default_rng(200 + nspk).integers(0, onet.n, nspk).astype(np.int32)
+    net.deliver_spikes(torch.from_numpy(spikers).cuda(), 61)
+    torch.cuda.synchronize()
+    npad = int(net.layout().n_neurons_padded)
+    ring = net.device_view("ring", torch.int32, 64 * npad).cpu().numpy().reshape(64, npad).astype(np.int64)
+    assert np.array_equal(ring, _expected_ring(qnet, spikers, 61, npad))
+    net.close()
+
+
+def test_blocked4_long_rows_all_delays():
+    m = workload.microcircuit_model()
+    rng = np.random.default_rng(13)
+    n = 1501
+    pre = list(rng.integers(0, 1500, 30000)) + [7] * 3001
+    post = list(rng.integers(0, n, 30000)) + list(rng.integers(0, n, 3001))
+    w = list(rng.integers(-2_000_000, 2_000_000, 33001))
+    d = list(rng.integers(1, 64, 33001))
+    u0 = rng.uniform(10, 16, n).astype(np.float32)
+    custom = dict(pre=pre, post=post, w_fx=w, delay=d, u0=u0, pop_offsets=[0, 200, 400, 600, 800, 1000, 1200, 1400, n])
+    net = snn.Network(m, custom=custom, steps_per_graph=33, seed=5, record_format=BLK4)
+    onet = oracle.network_from_edges(n, pre, post, w, d, u0, custom["pop_offsets"])
+    qnet = oracle.with_weights(onet, oracle.quantize_bf16(onet.w_fx))
+    sim = oracle.Sim(m, qnet, 5)
+    net.step(300)
+    g = net.read_spikes()
+    o = sim.run(300)
+    assert len(o[0]) > 50 and np.array_equal(g[0], o[0]) and np.array_equal(g[1], o[1])
+    _assert_same_state(net, sim)
+    net.close()
+
+
 def test_blocked_checkpoint_and_profiling_path(model, tiny):
     """Blocked records through a checkpoint, a resume after diverging steps and the
     kernel-by-kernel profiling path: the oracle's raster and state."""
@@ -886,7 +962,8 @@ def test_blocked_rejects_other_engines_and_batches(model):
 def test_blocked_full_scale_parity(model, full):
     """Full microcircuit with blocked records: the structure (boundaries, quotas, every
     synapse), 1,200 steps of raster and state equal to the oracle, and a saturating
-    delivery of 4,096 random senders equal to the ring sums over the oracle's rows."""
+    delivery of 4,096 random senders equal to the ring sums over the oracle's rows (also
+    with bfloat16 weights: the oracle's read-back weights and a sample of decoded rows)."""
     wl, onet = full
     net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=BLK)
     assert net.info().n_synapses == 284_811_022
@@ -899,14 +976,18 @@ def test_blocked_full_scale_parity(model, full):
     assert len(o_t) > 0 and np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
     _assert_same_state(net, sim)
     net.close()
-    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=BLK)
     spikers = np.random.default_rng(7).integers(0, onet.n, 4096).astype(np.int32)
-    net.deliver_spikes(torch.from_numpy(spikers).cuda(), 40)
-    torch.cuda.synchronize()
-    npad = int(net.layout().n_neurons_padded)
-    ring = net.device_view("ring", torch.int32, 64 * npad).cpu().numpy().reshape(64, npad).astype(np.int64)
-    assert np.array_equal(ring, _expected_ring(onet, spikers, 40, npad))
-    net.close()
+    qnet = oracle.with_weights(onet, oracle.quantize_bf16(onet.w_fx))
+    for fmt, ref in ((BLK, onet), (snn.RECORD_BLOCKED4, qnet)):
+        net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=fmt)
+        net.deliver_spikes(torch.from_numpy(spikers).cuda(), 40)
+        torch.cuda.synchronize()
+        npad = int(net.layout().n_neurons_padded)
+        ring = net.device_view("ring", torch.int32, 64 * npad).cpu().numpy().reshape(64, npad).astype(np.int64)
+        assert np.array_equal(ring, _expected_ring(ref, spikers, 40, npad))
+        if fmt == snn.RECORD_BLOCKED4:
+            _check_blocked_structure(net, qnet, rows=np.random.default_rng(4).integers(0, onet.n, 500))
+        net.close()
 
 
 @pytest.mark.parametrize("fmt", [snn.RECORD_PLAIN9, snn.RECORD_PACKED_BF16])
