@@ -625,6 +625,7 @@ def run_gpu(args):
                                                      "entry updated)",
                                              "points": forms.get("blocked6", {}).get("delivery_saturating")},
                                 "blocked4": {"kernel": "k_deliver_blocked",
+                                             "traffic_20480": _recorded_traffic("k_deliver_blocked_bf16"),
                                              "note": "the same with bfloat16 weights (4 B per event)",
                                              "points": forms.get("blocked4", {}).get("delivery_saturating")}},
         "clocks": clk.summary(), "build_s": build_s,
