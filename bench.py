@@ -661,7 +661,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ticks-per-step", type=int, default=TICKS_PER_STEP)
     ap.add_argument("--profile-ticks", type=int, default=2000)
-    ap.add_argument("--cpu-ticks", type=int, default=2000)
+    ap.add_argument("--cpu-ticks", type=int, default=5000)
     ap.add_argument("--reference-ticks", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--saturating", type=int, nargs="*", default=[2048, 8192, 20480])
