@@ -25,7 +25,7 @@ def candidates(net: Network, num_sms: int) -> List[Dict[str, int]]:
     info = net.info()
     if info.engine == ENGINE_PIPELINED:
         return [dict(grid_ctas=g, delivery_warps=w, steps_per_graph=s)
-                for g in (num_sms, 2 * num_sms) for w in (4, 8) for s in (1024,)]
+                for g in (num_sms, 2 * num_sms, 3 * num_sms) for w in (4, 8) for s in (1024,)]
     if info.engine == ENGINE_GRAPH:
         groups = [0] + [g for g in (4, 8, 16) if g < info.n_circuits]
         return [dict(grid_ctas=g, delivery_warps=0, steps_per_graph=s, circuits_per_group=c)

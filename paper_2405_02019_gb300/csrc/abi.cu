@@ -563,12 +563,13 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
         }
         if (net->engine == SNN_ENGINE_PIPELINED) {
             // state "after 0 steps" is buffer 1; the first kernel decides step 0's spikes
-            net->step_grid = snn::step_grid(net->num_sms);
             const int64_t quad_warps = ((net->n + 3) / 4 + 31) / 32;
+            net->step_grid = snn::step_grid(net->num_sms, quad_warps);
             a.neuron_warps = static_cast<int32_t>(
                 std::min<int64_t>(snn::kStepMaxNeuronWarps,
                                   std::max<int64_t>(1, (quad_warps + net->step_grid - 1) / net->step_grid)));
-            a.delivery_warps = snn::kStepDeliverWarps;
+            // a larger grid brings more delivery warps already: fewer per CTA
+            a.delivery_warps = net->step_grid > net->num_sms ? snn::kStepDeliverWarps / 2 : snn::kStepDeliverWarps;
             a.U2 = reinterpret_cast<float *>(A + L.U2);
             a.R2 = A + L.R2;
             a.queue = reinterpret_cast<snn::QueueEntry *>(A + L.queue);

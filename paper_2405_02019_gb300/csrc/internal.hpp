@@ -225,7 +225,7 @@ int launch_persistent(const StepArgs &a, int64_t n_steps, int grid, void *stream
 int launch_step(const StepArgs &a, int k, int ph, int grid, void *stream, bool programmatic = false);
 void launch_prime(const StepArgs &a, int grid, void *stream);         // pipelined: A(0)
 int prepare_step_kernel(const StepArgs &a);                           // dynamic shared memory opt-in
-int step_grid(int num_sms);
+int step_grid(int num_sms, int64_t quad_warps);  // default CTAs of the step kernel
 int step_threads(const StepArgs &a);
 
 }  // namespace snn

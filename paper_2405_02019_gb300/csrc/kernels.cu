@@ -914,7 +914,15 @@ __global__ void __launch_bounds__(kBlockedThreads, 1)
 
 }  // namespace
 
-int step_grid(int num_sms) { return num_sms; }
+// One CTA per SM while its kStepMaxNeuronWarps neuron warps cover the network's groups of
+// 128 neurons in one pass; larger networks get up to three CTAs per SM, so that a neuron
+// warp walks fewer groups one after another (each group is a chain of dependent loads).
+int step_grid(int num_sms, int64_t quad_warps)
+{
+    const int64_t per_pass = static_cast<int64_t>(kStepMaxNeuronWarps) * num_sms;
+    const int64_t mult = std::min<int64_t>(3, std::max<int64_t>(1, (quad_warps + per_pass - 1) / per_pass));
+    return static_cast<int>(mult * num_sms);
+}
 
 int step_threads(const StepArgs &a) { return 32 * (a.neuron_warps + a.delivery_warps); }
 
