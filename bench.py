@@ -566,8 +566,7 @@ def run_gpu(args):
         extra["batched"] = run_workload("32 PD circuits, neuron/in-degree scales U{100..1000} permille, seeds "
                                         "1000+c, 2 s each", circuits=[(w.scale_n_permille, w.scale_k_permille, w.seed)
                                                                       for w in bw],
-                                        n_steps=args.batched_steps, tune=True,
-                                        weng=snn.ENGINE_GRAPH if args.engine == "default" else engine)
+                                        n_steps=args.batched_steps, tune=True)
         extra["batched"]["speedup_vs_single_circuit"] = extra["batched"]["value"] / value
     if "x4" in args.extra:
         wx = workload.WORKLOADS["pd_x4"]

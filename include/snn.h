@@ -251,7 +251,7 @@ typedef struct snn_info {
     int32_t target_blocks;         /* SNN_RECORD_BLOCKED6: number of target blocks (else 0) */
     int32_t i8_base[SNN_MAX_POPS][SNN_MAX_POPS];  /* SNN_RECORD_PACKED_I8 read-back tables [source][target] */
     int32_t i8_step[SNN_MAX_POPS][SNN_MAX_POPS];
-    int32_t circuits_per_group;    /* graph engine, batches: see snn_set_circuit_groups (0 = one group) */
+    int32_t circuits_per_group;    /* batches: see snn_set_circuit_groups (0 = one group) */
     int32_t reserved3;
 } snn_info;
 
@@ -319,15 +319,20 @@ int snn_get_info(const snn_net *net, snn_info *out);
  * Errors: SNN_EINVAL (out of range), SNN_ENOTSUP (persistent engine), SNN_ECUDA. */
 int snn_set_schedule(snn_net *net, int32_t grid_ctas, int32_t delivery_warps, int32_t steps_per_graph);
 
-/* Batched networks on the graph engine: runs the circuits in groups of
+/* Batched networks on the graph or pipelined engine: runs the circuits in groups of
  * `circuits_per_group` consecutive circuits (0, or at least n_circuits, = one group) and
  * re-captures the step graph (waits for enqueued steps first).  Every run of steps
  * (a graph replay, or the steps one snn_step_n launches directly) is taken group by
  * group: the first group's circuits take all the run's steps, then the next group's,
  * and so on.  Circuits never interact, so results do not change; each group's ring and
  * neuron state then stay in L2 through the run (a whole 32-circuit batch's ring is
- * larger than L2).  Errors: SNN_EINVAL (negative), SNN_ENOTSUP (not the graph engine),
- * SNN_ECUDA. */
+ * larger than L2).  On the pipelined engine each group has its own spike queues; the
+ * spikes already decided for the next step move to the new groups' queues (a host
+ * round trip of one count and a few hundred entries per group), so the grouping may
+ * change between any two steps.  A group takes the step grid and delivery warps of
+ * snn_set_schedule where those were set, else the default for its own size.
+ * Errors: SNN_EINVAL (negative), SNN_ENOTSUP (persistent engine), SNN_ESTATE (a device
+ * error is pending), SNN_ECUDA. */
 int snn_set_circuit_groups(snn_net *net, int32_t circuits_per_group);
 
 /* Batched networks: the first neuron and the neuron count of every circuit (host
@@ -359,7 +364,9 @@ int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *
 int snn_save_state(snn_net *net, void *host_buf, uint64_t capacity, uint64_t *written);
 
 /* Restores a blob from snn_save_state into `net` (same spec; checked by shape and
- * engine), including the step counter; the host spike history starts empty.
+ * engine), including the step counter; the host spike history starts empty.  A blob
+ * saved under another circuit grouping (snn_set_circuit_groups) loads into the current
+ * one.
  * Errors: SNN_EINVAL (not a state blob, or another shape/engine), SNN_ECUDA. */
 int snn_load_state(snn_net *net, const void *host_buf, uint64_t bytes);
 

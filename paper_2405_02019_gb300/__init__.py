@@ -264,8 +264,9 @@ class Network:
                                        int(steps_per_graph)), "snn_set_schedule")
 
     def set_circuit_groups(self, circuits_per_group: int) -> None:
-        """Graph engine, batches: run consecutive circuits in groups of this many, one group
-        after another over each run of steps (0 = all at once); results never depend on it."""
+        """Batches (graph or pipelined engine): run consecutive circuits in groups of this
+        many, one group after another over each run of steps (0 = all at once); results
+        never depend on it, and it may change between any two steps."""
         _check(load().snn_set_circuit_groups(C.c_void_p(self._handle), int(circuits_per_group)),
                "snn_set_circuit_groups")
 

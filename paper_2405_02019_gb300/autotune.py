@@ -1,8 +1,8 @@
 """Autotuner of the step kernels' launch schedule.
 
 The schedule -- CTAs of the step kernel, delivery warps per CTA, steps per captured
-graph (pipelined engine), or CTAs of the delivery kernel and, for a batch, circuits
-per group (graph engine) -- changes only speed, never results.  ``autotune`` times candidate schedules on the live
+graph (pipelined engine), or CTAs of the delivery kernel (graph engine), and for a
+batch the circuits per group -- changes only speed, never results.  ``autotune`` times candidate schedules on the live
 network between a checkpoint and its restore (so the dynamics are untouched, but the
 host spike history restarts: read spikes before tuning), keeps the fastest, and
 remembers it in a JSON cache keyed by GPU, network shape, record format and engine.
@@ -23,11 +23,11 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "snn_gb300_sched
 
 def candidates(net: Network, num_sms: int) -> List[Dict[str, int]]:
     info = net.info()
+    groups = [0] + [g for g in (4, 8, 16) if g < info.n_circuits]
     if info.engine == ENGINE_PIPELINED:
-        return [dict(grid_ctas=g, delivery_warps=w, steps_per_graph=s)
-                for g in (num_sms, 2 * num_sms, 3 * num_sms) for w in (4, 8) for s in (1024,)]
+        return [dict(grid_ctas=g, delivery_warps=w, steps_per_graph=s, circuits_per_group=c)
+                for g in (num_sms, 2 * num_sms, 3 * num_sms) for w in (4, 8) for s in (1024,) for c in groups]
     if info.engine == ENGINE_GRAPH:
-        groups = [0] + [g for g in (4, 8, 16) if g < info.n_circuits]
         return [dict(grid_ctas=g, delivery_warps=0, steps_per_graph=s, circuits_per_group=c)
                 for g in (num_sms, 2 * num_sms, 4 * num_sms) for s in (1024,) for c in groups]
     return []

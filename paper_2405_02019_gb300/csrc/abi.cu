@@ -88,11 +88,16 @@ struct snn_net {
     int64_t raster_read = 0;
     int64_t collected_t = 0;       // spikes of steps below this are in the host history
     cudaStream_t copy_stream = nullptr;
-    // graph engine, batches: circuits per group (0 = one group) and each group's update
-    // arguments and grid; empty when the whole index space updates in one launch
+    // batches: circuits per group (0 = one group) and each group's update (graph engine)
+    // or step (pipelined engine) arguments and grid; empty when the whole index space
+    // runs in one launch
     int32_t circuits_per_group = 0;
     std::vector<snn::StepArgs> group_args;
     std::vector<int> group_grid;
+    // pipelined engine: the step grid / delivery warps were set by snn_set_schedule (else
+    // each circuit group takes the default for its size)
+    bool step_grid_set = false;
+    bool delivery_warps_set = false;
 };
 
 namespace {
@@ -104,27 +109,109 @@ void launch_phase2(const snn_net *net, int k, cudaStream_t st)
     else snn::launch_deliver(net->args, k, net->deliver_grid, st);
 }
 
-// Graph engine, batches: consecutive circuits in groups of circuits_per_group, each
-// group updating only its own neuron range.  The groups are independent, so a run of
-// steps may take them one after another: each group's ring and state then stay in L2
-// for the whole run instead of the whole batch's competing for it every step.
+// Pipelined engine: neuron warps per CTA so that `grid` CTAs cover `quad_warps` groups
+// of 128 neurons in as few passes as the CTA allows.
+int32_t step_neuron_warps(int64_t quad_warps, int grid)
+{
+    return static_cast<int32_t>(
+        std::min<int64_t>(snn::kStepMaxNeuronWarps, std::max<int64_t>(1, (quad_warps + grid - 1) / grid)));
+}
+
+// Neuron range [lo, hi) of every circuit group under `cpg` circuits per group (one
+// group, the whole index space, when cpg is 0 or covers every circuit).
+std::vector<std::pair<int64_t, int64_t>> group_ranges(const snn_net *net, int cpg)
+{
+    const int C = static_cast<int>(net->circuits.size());
+    if (cpg <= 0 || cpg >= C) return {{0, net->n}};
+    std::vector<std::pair<int64_t, int64_t>> r;
+    for (int c0 = 0; c0 < C; c0 += cpg) {
+        const int c1 = std::min(C, c0 + cpg);
+        r.push_back({net->circuits[c0].base, net->circuits[c1 - 1].base + net->circuits[c1 - 1].n});
+    }
+    return r;
+}
+
+// Pipelined engine: arena offset of the four queue counts of group g of `n_groups`
+// (the control block's for a single group, else the group's slot of the count array).
+uint64_t queue_count_offset(const snn_net *net, size_t g, size_t n_groups)
+{
+    return n_groups <= 1 ? net->L.ctl + offsetof(snn::Ctl, qcnt) : net->L.qcount + 16 * g;
+}
+
+// Batches: consecutive circuits in groups of circuits_per_group, each group updating
+// (graph engine) or stepping (pipelined engine) only its own neuron range.  The groups
+// are independent, so a run of steps may take them one after another: each group's
+// ring and state then stay in L2 for the whole run instead of the whole batch's
+// competing for it every step.  Circuits start on multiples of 128 neurons, so a group
+// is a whole number of 128-neuron groups.
 void build_groups(snn_net *net)
 {
     net->group_args.clear();
     net->group_grid.clear();
-    const int C = static_cast<int>(net->circuits.size());
-    const int cpg = net->circuits_per_group;
-    if (net->engine != SNN_ENGINE_GRAPH || cpg <= 0 || cpg >= C) return;
-    for (int c0 = 0; c0 < C; c0 += cpg) {
-        const int c1 = std::min(C, c0 + cpg);
-        const int64_t lo = net->circuits[c0].base;  // a multiple of 128
-        const int64_t hi = net->circuits[c1 - 1].base + net->circuits[c1 - 1].n;
+    const auto ranges = group_ranges(net, net->circuits_per_group);
+    if (ranges.size() <= 1) return;
+    if (net->engine != SNN_ENGINE_GRAPH && net->engine != SNN_ENGINE_PIPELINED) return;
+    for (size_t g = 0; g < ranges.size(); ++g) {
+        const int64_t lo = ranges[g].first, hi = ranges[g].second;
         snn::StepArgs a = net->args;
         a.quad_base = lo / 4;
         a.n = hi;
+        int grid = snn::update_grid(hi - lo);
+        if (net->engine == SNN_ENGINE_PIPELINED) {
+            const int64_t qw_end = ((hi + 3) / 4 + 31) / 32;
+            const int64_t qw = qw_end - lo / 128;
+            grid = net->step_grid_set ? net->step_grid : snn::step_grid(net->num_sms, qw);
+            if (!net->delivery_warps_set)
+                a.delivery_warps = grid > net->num_sms ? snn::kStepDeliverWarps / 2 : snn::kStepDeliverWarps;
+            a.neuron_warps = step_neuron_warps(qw, grid);
+            a.quad_warps = static_cast<int32_t>(qw_end);
+            a.queue = net->args.queue + lo;
+            a.queue_cap = hi - lo;
+            a.qcount = reinterpret_cast<uint32_t *>(net->arena + queue_count_offset(net, g, ranges.size()));
+        }
         net->group_args.push_back(a);
-        net->group_grid.push_back(snn::update_grid(hi - lo));
+        net->group_grid.push_back(grid);
     }
+}
+
+// Pipelined engine: moves the spikes pending at a step boundary (queue t mod 4) from the
+// queue layout of `old_cpg` circuits per group to the current one.  Entries keep their
+// content; within a queue their order carries no meaning (a step's raster is ordered on
+// the host, ring sums are integer).
+int regroup_queue(snn_net *net, int old_cpg)
+{
+    const auto from = group_ranges(net, old_cpg);
+    const auto to = group_ranges(net, net->circuits_per_group);
+    const int s = static_cast<int>(net->t & 3);
+    const uint64_t qbase = net->L.queue + sizeof(snn::QueueEntry) * (static_cast<uint64_t>(s) * net->npad);
+    std::vector<snn::QueueEntry> pending;
+    for (size_t g = 0; g < from.size(); ++g) {
+        uint32_t cnt = 0;
+        SNN_CUDA_TRY(cudaMemcpy(&cnt, net->arena + queue_count_offset(net, g, from.size()) + 4 * s, 4,
+                                cudaMemcpyDeviceToHost));
+        if (cnt > static_cast<uint64_t>(from[g].second - from[g].first))
+            return fail(SNN_ESTATE, "pending spike queue is corrupt");
+        const size_t at = pending.size();
+        pending.resize(at + cnt);
+        if (cnt)
+            SNN_CUDA_TRY(cudaMemcpy(pending.data() + at, net->arena + qbase + sizeof(snn::QueueEntry) * from[g].first,
+                                    sizeof(snn::QueueEntry) * cnt, cudaMemcpyDeviceToHost));
+    }
+    for (size_t g = 0; g < to.size(); ++g) {
+        std::vector<snn::QueueEntry> mine;
+        for (const auto &e : pending)
+            if (e.neuron >= to[g].first && e.neuron < to[g].second) mine.push_back(e);
+        if (mine.size() > static_cast<uint64_t>(to[g].second - to[g].first))
+            return fail(SNN_ESTATE, "pending spike queue is corrupt");
+        if (!mine.empty())
+            SNN_CUDA_TRY(cudaMemcpy(net->arena + qbase + sizeof(snn::QueueEntry) * to[g].first, mine.data(),
+                                    sizeof(snn::QueueEntry) * mine.size(), cudaMemcpyHostToDevice));
+        const uint32_t cnt[2] = {static_cast<uint32_t>(mine.size()), 0u};  // queue t mod 4, and the next one
+        const uint64_t off = queue_count_offset(net, g, to.size());
+        SNN_CUDA_TRY(cudaMemcpy(net->arena + off + 4 * s, &cnt[0], 4, cudaMemcpyHostToDevice));
+        SNN_CUDA_TRY(cudaMemcpy(net->arena + off + 4 * ((s + 1) & 3), &cnt[1], 4, cudaMemcpyHostToDevice));
+    }
+    return SNN_OK;
 }
 
 // Graph engine: m steps from the device's t_base, every group in turn, then t_base += m.
@@ -143,15 +230,33 @@ void enqueue_graph_steps(snn_net *net, int64_t m, cudaStream_t st)
     snn::launch_advance(net->args.ctl, m, st);
 }
 
+// Pipelined engine: m step kernels from step t0 (the device's t_base), every circuit
+// group in turn, then t_base += m.  Consecutive kernels of a group may overlap their
+// launch with the previous one (programmatic edges, inside a captured graph); a group's
+// first kernel follows the previous group's resync in plain stream order.
+int enqueue_pipelined_steps(snn_net *net, int64_t m, cudaStream_t st, int64_t t0, bool programmatic)
+{
+    const size_t G = net->group_args.size();
+    for (size_t g = 0; g < std::max<size_t>(G, 1); ++g) {
+        const snn::StepArgs &a = G ? net->group_args[g] : net->args;
+        const int grid = G ? net->group_grid[g] : net->step_grid;
+        for (int64_t k = 0; k < m; ++k) {
+            const int ph = static_cast<int>((t0 + k) % snn::kPhasePeriod);
+            const int e = snn::launch_step(a, static_cast<int>(k), ph, grid, st, programmatic && k > 0);
+            if (e != 0) return fail(SNN_ECUDA, std::string("step launch: ") + cudaGetErrorString(static_cast<cudaError_t>(e)));
+        }
+        if (g + 1 < G) snn::launch_resync(net->args.ctl, st);
+    }
+    snn::launch_advance(net->args.ctl, m, st);
+    return SNN_OK;
+}
+
 // m steps launched one by one, starting at step t0 (the device counter t_base equals t0).
 int launch_steps_direct(snn_net *net, int64_t m, cudaStream_t st, int64_t t0)
 {
     if (net->engine == SNN_ENGINE_PIPELINED) {
-        for (int64_t k = 0; k < m; ++k) {
-            const int ph = static_cast<int>((t0 + k) % snn::kPhasePeriod);
-            snn::launch_step(net->args, static_cast<int>(k), ph, net->step_grid, st);
-        }
-        snn::launch_advance(net->args.ctl, m, st);
+        const int rc = enqueue_pipelined_steps(net, m, st, t0, false);
+        if (rc) return rc;
     } else {
         enqueue_graph_steps(net, m, st);
     }
@@ -177,19 +282,14 @@ int capture_graph(snn_net *net)
     SNN_CUDA_TRY(cudaStreamCreateWithFlags(&net->capture_stream, cudaStreamNonBlocking));
     SNN_CUDA_TRY(cudaStreamBeginCapture(net->capture_stream, cudaStreamCaptureModeThreadLocal));
     if (net->engine == SNN_ENGINE_PIPELINED) {
-        for (int k = 0; k < net->steps_per_graph; ++k) {
-            // replays start on a multiple of the phase period (see snn_step_n); consecutive
-            // step kernels overlap their launch with the previous one (programmatic edges)
-            const int e = snn::launch_step(net->args, k, k % snn::kPhasePeriod, net->step_grid, net->capture_stream,
-                                           /*programmatic=*/k > 0);
-            if (e != 0) {
-                cudaGraph_t g = nullptr;
-                cudaStreamEndCapture(net->capture_stream, &g);
-                if (g) cudaGraphDestroy(g);
-                return fail(SNN_ECUDA, std::string("capture: ") + cudaGetErrorString(static_cast<cudaError_t>(e)));
-            }
+        // replays start on a multiple of the phase period (see snn_step_n)
+        const int rc = enqueue_pipelined_steps(net, net->steps_per_graph, net->capture_stream, 0, true);
+        if (rc != SNN_OK) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(net->capture_stream, &g);
+            if (g) cudaGraphDestroy(g);
+            return rc;
         }
-        snn::launch_advance(net->args.ctl, net->steps_per_graph, net->capture_stream);
     } else {
         enqueue_graph_steps(net, net->steps_per_graph, net->capture_stream);
     }
@@ -565,16 +665,15 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
             // state "after 0 steps" is buffer 1; the first kernel decides step 0's spikes
             const int64_t quad_warps = ((net->n + 3) / 4 + 31) / 32;
             net->step_grid = snn::step_grid(net->num_sms, quad_warps);
-            a.neuron_warps = static_cast<int32_t>(
-                std::min<int64_t>(snn::kStepMaxNeuronWarps,
-                                  std::max<int64_t>(1, (quad_warps + net->step_grid - 1) / net->step_grid)));
+            a.neuron_warps = step_neuron_warps(quad_warps, net->step_grid);
             // a larger grid brings more delivery warps already: fewer per CTA
             a.delivery_warps = net->step_grid > net->num_sms ? snn::kStepDeliverWarps / 2 : snn::kStepDeliverWarps;
             a.U2 = reinterpret_cast<float *>(A + L.U2);
             a.R2 = A + L.R2;
             a.queue = reinterpret_cast<snn::QueueEntry *>(A + L.queue);
             a.quad_warps = static_cast<int32_t>(quad_warps);
-            a.qcount = reinterpret_cast<uint32_t *>(A + L.qcount);
+            a.qcount = reinterpret_cast<uint32_t *>(A + L.ctl + offsetof(snn::Ctl, qcnt));
+            a.queue_cap = net->npad;
             if (snn::prepare_step_kernel(a) != 0) {
                 snn_destroy(net);
                 return fail(SNN_ENOTSUP, "network too large for the pipelined engine's shared memory");
@@ -667,7 +766,8 @@ int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     double su = 0.0, sd = 0.0;
     const int64_t batch = 256;
-    const size_t G = net->engine == SNN_ENGINE_PIPELINED ? 1 : std::max<size_t>(net->group_args.size(), 1);
+    const size_t G = std::max<size_t>(net->group_args.size(), 1);
+    const bool grouped = !net->group_args.empty();
     std::vector<cudaEvent_t> ev(3 * batch * G);
     for (auto &e : ev) SNN_CUDA_TRY(cudaEventCreate(&e));
     int rc = SNN_OK;
@@ -679,10 +779,10 @@ int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *
                 cudaEventRecord(ev[3 * used], st);
                 if (net->engine == SNN_ENGINE_PIPELINED) {
                     const int ph = static_cast<int>((net->t + done + k) % snn::kPhasePeriod);
-                    snn::launch_step(net->args, static_cast<int>(k), ph, net->step_grid, st);
+                    snn::launch_step(grouped ? net->group_args[g] : net->args, static_cast<int>(k), ph,
+                                     grouped ? net->group_grid[g] : net->step_grid, st);
                     cudaEventRecord(ev[3 * used + 1], st);
                 } else {
-                    const bool grouped = !net->group_args.empty();
                     snn::launch_update(grouped ? net->group_args[g] : net->args, static_cast<int>(k),
                                        grouped ? net->group_grid[g] : net->update_grid, st);
                     cudaEventRecord(ev[3 * used + 1], st);
@@ -863,13 +963,15 @@ int snn_get_layout(const snn_net *net, snn_layout *out)
 
 namespace {
 
-constexpr uint64_t kStateMagic = 0x534E4E5354415431ull;  // "SNNSTAT1"
+constexpr uint64_t kStateMagic = 0x534E4E5354415432ull;  // "SNNSTAT2"
 
 struct StateHeader {
     uint64_t magic;
     uint64_t bytes;
     int64_t n, npad, t;
     int32_t engine, n_segments;
+    int32_t circuits_per_group;  // the pending spike queue's layout (pipelined engine)
+    int32_t reserved;
 };
 
 // Device segments that make up the dynamic state, as (arena offset, bytes).
@@ -883,6 +985,7 @@ std::vector<std::pair<uint64_t, uint64_t>> state_segments(const snn_net *net)
         seg.push_back({L.U2, 4 * uint64_t(net->npad)});
         seg.push_back({L.R2, uint64_t(net->npad)});
         seg.push_back({L.queue, 4 * sizeof(snn::QueueEntry) * net->npad});
+        seg.push_back({L.qcount, 16 * uint64_t(net->npad / 128 + 1)});
     }
     return seg;
 }
@@ -900,7 +1003,8 @@ int snn_save_state(snn_net *net, void *host_buf, uint64_t capacity, uint64_t *wr
     if (capacity < total) return fail(SNN_ENOMEM, "state buffer too small");
     int rc = drain(net);  // spikes so far go to the host history; the device raster restarts at 0
     if (rc) return rc;
-    StateHeader h{kStateMagic, total, net->n, net->npad, net->t, net->engine, static_cast<int32_t>(seg.size())};
+    StateHeader h{kStateMagic, total, net->n, net->npad, net->t, net->engine, static_cast<int32_t>(seg.size()),
+                  net->circuits_per_group, 0};
     uint8_t *out = static_cast<uint8_t *>(host_buf);
     std::memcpy(out, &h, sizeof(h));
     uint64_t off = sizeof(h);
@@ -933,6 +1037,11 @@ int snn_load_state(snn_net *net, const void *host_buf, uint64_t bytes)
         off += sg.second;
     }
     net->t = h.t;
+    if (net->engine == SNN_ENGINE_PIPELINED && h.circuits_per_group != net->circuits_per_group) {
+        // saved under another circuit grouping: move the pending spikes to this one's queues
+        rc = regroup_queue(net, h.circuits_per_group);
+        if (rc) return rc;
+    }
     net->hist_t.clear();
     net->hist_i.clear();
     net->read_pos = 0;
@@ -953,15 +1062,17 @@ int snn_set_schedule(snn_net *net, int32_t grid_ctas, int32_t delivery_warps, in
     if (rc) return rc;
     snn::StepArgs &a = net->args;
     if (net->engine == SNN_ENGINE_PIPELINED) {
-        if (grid_ctas > 0) net->step_grid = grid_ctas;
-        if (delivery_warps > 0) {
-            if (delivery_warps + snn::kStepMaxNeuronWarps > snn::kStepMaxThreads / 32)
-                return fail(SNN_EINVAL, "too many delivery warps per CTA");
-            a.delivery_warps = delivery_warps;
+        if (delivery_warps > 0 && delivery_warps + snn::kStepMaxNeuronWarps > snn::kStepMaxThreads / 32)
+            return fail(SNN_EINVAL, "too many delivery warps per CTA");
+        if (grid_ctas > 0) {
+            net->step_grid = grid_ctas;
+            net->step_grid_set = true;
         }
-        const int64_t quad_warps = ((net->n + 3) / 4 + 31) / 32;
-        a.neuron_warps = static_cast<int32_t>(std::min<int64_t>(
-            snn::kStepMaxNeuronWarps, std::max<int64_t>(1, (quad_warps + net->step_grid - 1) / net->step_grid)));
+        if (delivery_warps > 0) {
+            a.delivery_warps = delivery_warps;
+            net->delivery_warps_set = true;
+        }
+        a.neuron_warps = step_neuron_warps(((net->n + 3) / 4 + 31) / 32, net->step_grid);
         if (steps_per_graph > 0)
             net->steps_per_graph = std::max(snn::kPhasePeriod, steps_per_graph / snn::kPhasePeriod * snn::kPhasePeriod);
     } else if (net->engine == SNN_ENGINE_GRAPH) {
@@ -980,11 +1091,20 @@ int snn_set_circuit_groups(snn_net *net, int32_t circuits_per_group)
 {
     if (!net) return fail(SNN_EINVAL, "null network");
     if (circuits_per_group < 0) return fail(SNN_EINVAL, "circuits_per_group < 0");
-    if (net->engine != SNN_ENGINE_GRAPH)
-        return fail(SNN_ENOTSUP, "circuit groups run on the graph engine");
-    const int rc = wait_done(net);
+    if (net->engine != SNN_ENGINE_GRAPH && net->engine != SNN_ENGINE_PIPELINED)
+        return fail(SNN_ENOTSUP, "circuit groups run on the graph and pipelined engines");
+    if (net->device_error) return fail(SNN_ESTATE, "a previous device error is pending");
+    int rc = wait_done(net);
     if (rc) return rc;
+    const int32_t old = net->circuits_per_group;
     net->circuits_per_group = circuits_per_group >= static_cast<int32_t>(net->circuits.size()) ? 0 : circuits_per_group;
+    if (net->engine == SNN_ENGINE_PIPELINED && net->circuits_per_group != old) {
+        rc = regroup_queue(net, old);
+        if (rc) {
+            net->circuits_per_group = old;
+            return rc;
+        }
+    }
     build_groups(net);
     return recapture(net);
 }

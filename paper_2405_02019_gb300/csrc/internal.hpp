@@ -130,11 +130,11 @@ struct StepArgs {
     int32_t neuron_warps;         // pipelined engine: neuron warps per CTA
     float *U2;                    // pipelined engine: second U / R buffers (state after A(s) in buffer s mod 2)
     uint8_t *R2;
-    QueueEntry *queue;            // pipelined engine: 4 queues of npad entries
+    QueueEntry *queue;            // pipelined engine: 4 queues, entry j of queue s at queue[s * npad + j]
     int64_t pop_off[SNN_MAX_POPS + 1];  // population offsets (read from the launch arguments)
     int32_t n_pops;
-    int32_t quad_warps;           // pipelined engine: groups of 128 neurons (one queue region each)
-    uint32_t *qcount;             // pipelined engine: spikes per group, [4][quad_warps]
+    int32_t quad_warps;           // pipelined engine: end of the launch's groups of 128 neurons
+    uint32_t *qcount;             // pipelined engine: spikes in each of the 4 queues (Ctl::qcnt, or a circuit group's)
     int32_t format;               // SNN_RECORD_*
     int32_t n_circuits;
     int32_t delivery_warps;       // pipelined engine: delivery warps per CTA
@@ -147,7 +147,8 @@ struct StepArgs {
     const int32_t *blk_off;       // blocked records: block boundaries [n_blocks + 1]
     int32_t n_blocks;
     int32_t pad4;
-    int64_t quad_base;            // graph engine: first quad the update kernel covers (n = end neuron)
+    int64_t quad_base;            // first quad the update (or step) launch covers, n its end neuron
+    int64_t queue_cap;            // pipelined engine: entries of each queue (a circuit group's neurons)
 };
 
 // Host constants of one model (§2.2).

@@ -401,9 +401,12 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_persistent(const StepArg
 // the same as the two-phase engines.  U and R after A(s) live in buffer s mod 2 (the
 // state after s steps is in buffer (s-1) mod 2).
 //
-// Spike queue of step s (buffer s mod 4, count Ctl::qcnt[s mod 4]): a warp with
+// Spike queue of step s (buffer s mod 4, count qcount[s mod 4]): a warp with
 // spikers reserves room with one atomic and writes their entries (row bounds were
-// loaded with the neuron state).  The rows are prefetched into L2 for the next
+// loaded with the neuron state).  A batch in circuit groups runs one launch per group
+// and step; the group's launch covers only its own groups of 128 neurons, and its
+// queues and counts are its own (queue region from the group's first neuron, counts
+// in the group's slot of the count array), so the groups' kernels are independent.  The rows are prefetched into L2 for the next
 // kernel.  A delivery warp loads the step's spike count and the entry of its first
 // item in the same round trip, then the synapses; the warp delivering chunk 0 of spike
 // j records it at raster position base + j, the raster base advancing once per step
@@ -545,7 +548,7 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, i
     const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     if (total == 0) return;
     uint32_t base = 0;
-    if (lane == 31) base = atomicAdd(&a.ctl->qcnt[phn & 3], static_cast<uint32_t>(total));
+    if (lane == 31) base = atomicAdd(&a.qcount[phn & 3], static_cast<uint32_t>(total));
     base = __shfl_sync(0xFFFFFFFFu, base, 31);
     if (cnt == 0) return;
     QueueEntry *region = a.queue + (phn & 3) * a.npad + base;
@@ -588,14 +591,13 @@ __device__ __forceinline__ void pipe_deliver_fmt(const StepArgs &a, const int64_
     const int lane = threadIdx.x & 31;
     const QueueEntry *qbuf = a.queue + (ph & 3) * a.npad;
     const int64_t cpr = a.chunks_per_row;
-    const int64_t npad = a.npad;
     // items are (spike, run of `per` chunks); when every item is one chunk (few spikes) the
     // entry `first` loaded before n arrived belongs to this warp's first item
     const int64_t ipj = items_per_spike(cpr, n, ndw);
     const int64_t per = (cpr + ipj - 1) / ipj;
     for (int64_t it = dw;; it += ndw) {
         const int64_t j = it / ipj;
-        if (j >= npad || j >= n) break;
+        if (j >= a.queue_cap || j >= n) break;
         const int4 raw = (it == dw && ipj == cpr) ? first : __ldcg(reinterpret_cast<const int4 *>(qbuf + j));
         const int64_t part = it - j * ipj;
         if (part == 0 && lane == 0) {
@@ -617,17 +619,17 @@ __device__ __forceinline__ void pipe_deliver(const StepArgs &a, const int64_t &t
                                              int64_t ndw, bool wait_first)
 {
     if (wait_first) wait_previous_grid();
-    const uint32_t n = __ldcg(&a.ctl->qcnt[ph & 3]);
+    const uint32_t n = __ldcg(&a.qcount[ph & 3]);
     const uint32_t rbase = __ldcg(&a.ctl->step_begin[t & 1]);
     // speculative: the entry of this warp's first item under one chunk per item, issued
     // alongside the count so both arrive in one round trip
     const int64_t j0 = dw / a.chunks_per_row;
-    const int4 first = j0 < a.npad ? __ldcg(reinterpret_cast<const int4 *>(a.queue + (ph & 3) * a.npad + j0))
+    const int4 first = j0 < a.queue_cap ? __ldcg(reinterpret_cast<const int4 *>(a.queue + (ph & 3) * a.npad + j0))
                                    : make_int4(0, 0, 0, 0);
     if (leader) {
         a.ctl->step_begin[(t + 1) & 1] = rbase + n;
         a.ctl->cursor = rbase + n;
-        a.ctl->qcnt[(ph + 2) & 3] = 0;  // the queue the next kernel fills after this one
+        a.qcount[(ph + 2) & 3] = 0;  // the queue the next kernel fills after this one
         if (static_cast<uint64_t>(rbase) + n > a.rast_cap) atomicOr(&a.ctl->err, kErrRaster);
     }
     if (a.format == SNN_RECORD_PACKED_I8) pipe_deliver_fmt<SNN_RECORD_PACKED_I8>(a, t, ph, dw, ndw, n, rbase, first);
@@ -646,7 +648,8 @@ __global__ void __launch_bounds__(kStepMaxThreads, 2) k_step(const StepArgs a, c
         const int64_t nquads = (a.n + 3) / 4;
         const int64_t nw = static_cast<int64_t>(a.neuron_warps) * gridDim.x;
         bool first = true;
-        for (int64_t g = static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < a.quad_warps; g += nw) {
+        for (int64_t g = (a.quad_base >> 5) + static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < a.quad_warps;
+             g += nw) {
             pipe_quad(a, t, ph, g, g * 32 + (threadIdx.x & 31) < nquads, true, first);
             first = false;
         }
@@ -666,7 +669,7 @@ __global__ void __launch_bounds__(kStepMaxThreads, 2) k_prime(const StepArgs a)
     const int64_t nquads = (a.n + 3) / 4;
     const int64_t nw = static_cast<int64_t>(a.neuron_warps) * gridDim.x;
     const int64_t t = -1;
-    for (int64_t g = static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < a.quad_warps; g += nw)
+    for (int64_t g = (a.quad_base >> 5) + static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < a.quad_warps; g += nw)
         pipe_quad(a, t, -1, g, g * 32 + (threadIdx.x & 31) < nquads, false, false);
 }
 

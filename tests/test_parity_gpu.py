@@ -1024,30 +1024,36 @@ def test_batched_circuits_equal_standalone_runs(model, engine, fmt):
     net.close()
 
 
+@pytest.mark.parametrize("engine", [GRAPH, PIPE])
 @pytest.mark.parametrize("cpg", [1, 2, 3])
-def test_circuit_groups_equal_one_launch(model, cpg):
-    """Graph engine: circuits taken in groups (each group through a whole run of steps
-    before the next) give the raster and state of the ungrouped batch, across graph
-    replays, directly launched remainders, the profiling path, a checkpoint and a change
-    of grouping."""
-    ref = snn.Network(model, circuits=BATCH, steps_per_graph=64, engine=GRAPH)
+def test_circuit_groups_equal_one_launch(model, engine, cpg):
+    """Circuits taken in groups (each group through a whole run of steps before the next)
+    give the raster and state of the ungrouped batch, across graph replays, directly
+    launched remainders, the profiling path, changes of grouping between steps and a
+    checkpoint loaded under another grouping than it was saved with (on the pipelined
+    engine the spikes pending for the next step move between the groups' queues)."""
+    ref = snn.Network(model, circuits=BATCH, steps_per_graph=64, engine=engine)
     ref.step(300)
     r_t, r_i = ref.read_spikes()
     rU, rI, rR = _state(ref)
     ref.close()
-    net = snn.Network(model, circuits=BATCH, steps_per_graph=64, engine=GRAPH)
+    other = 0 if cpg > 1 else 2
+    net = snn.Network(model, circuits=BATCH, steps_per_graph=64, engine=engine)
     net.set_circuit_groups(cpg)
     assert net.info().circuits_per_group == (cpg if cpg < len(BATCH) else 0)
     net.step(100)   # one replay and 36 direct steps
     blob = net.save_state()
     part = net.read_spikes()
     net.step(77)
-    net.load_state(blob)  # back to step 100; the host history restarts there
-    net.set_circuit_groups(0 if cpg > 1 else 2)
+    net.set_circuit_groups(other)
+    net.load_state(blob)  # back to step 100 under the other grouping; the host history restarts there
     net.step(50)
     net.set_circuit_groups(cpg)
-    net.step(100)
-    net.profile_steps(50)  # the kernel-by-kernel path takes the groups too
+    net.step(20)
+    net.set_circuit_groups(other)
+    net.step(86)    # 22 direct steps, then one replay from step 192
+    net.set_circuit_groups(cpg)
+    net.profile_steps(44)  # the kernel-by-kernel path takes the groups too
     g_t, g_i = net.read_spikes()
     g_t = np.concatenate([part[0], g_t])
     g_i = np.concatenate([part[1], g_i])
@@ -1059,8 +1065,26 @@ def test_circuit_groups_equal_one_launch(model, cpg):
     net.close()
 
 
-def test_circuit_groups_need_the_graph_engine(model):
-    net = snn.Network(model, circuits=BATCH, engine=PIPE)
+def test_pipelined_circuit_groups_equal_standalone_runs(model):
+    """Pipelined engine in circuit groups of two: every circuit's slice of the raster
+    equals the oracle run of that circuit alone."""
+    net = snn.Network(model, circuits=BATCH, steps_per_graph=64, engine=PIPE)
+    net.set_circuit_groups(2)
+    base, n = net.circuits()
+    steps = 200
+    net.step(steps)
+    g_t, g_i = net.read_spikes()
+    for c, (sn, sk, seed) in enumerate(BATCH):
+        onet = oracle.build_network(model, sn, sk, seed)
+        o_t, o_i = oracle.Sim(model, onet, seed).run(steps)
+        sel = (g_i >= base[c]) & (g_i < base[c] + n[c])
+        assert np.array_equal(g_t[sel], o_t), c
+        assert np.array_equal(g_i[sel] - base[c], o_i), c
+    net.close()
+
+
+def test_circuit_groups_not_on_the_persistent_engine(model):
+    net = snn.Network(model, circuits=BATCH, engine=PERSIST)
     with pytest.raises(snn.SnnError):
         net.set_circuit_groups(2)
     net.close()
