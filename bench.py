@@ -394,11 +394,12 @@ def run_gpu(args):
     elif info.engine == snn.ENGINE_PERSISTENT:
         # one cooperative launch per bench step: all of its steps' algorithmic bytes over its duration
         per_launch = tps * (upd_bytes + (EVENT_BYTES * events + SPIKE_BYTES * spikes) / (args.steps * tps))
-        kernels["k_persistent"] = {"avg_us": secs_max * 1e6 / args.steps, "bytes_per_launch": per_launch,
-                                   "gbs": per_launch / (secs_max / args.steps) / 1e9, "share": 1.0,
-                                   "steps_per_launch": tps}
-        kernels["k_update"]["note"] = kernels["k_deliver"]["note"] = (
-            "graph-engine kernels timed one launch at a time for the per-phase split")
+        kernels = {"k_persistent": {"avg_us": secs_max * 1e6 / args.steps, "bytes_per_launch": per_launch,
+                                    "gbs": per_launch / (secs_max / args.steps) / 1e9, "share": 1.0,
+                                    "steps_per_launch": tps, "us_per_step": secs_max * 1e6 / (args.steps * tps),
+                                    "isolated_k_step_avg_us": ms_u / prof_ticks * 1e3,
+                                    "note": "isolated_k_step_avg_us: the same step as one k_step launch, "
+                                            "bracketed with CUDA events (launch latency included)"}}
         dom = "k_persistent"
     else:
         dom = "k_update" if ms_u >= ms_d else "k_deliver"

@@ -131,8 +131,9 @@ typedef struct snn_circuit {
  *       update and decides step t+1's spikes;
  *     SNN_ENGINE_GRAPH: the two phases of Listing push2 as two kernels per step,
  *       replayed from a CUDA graph;
- *     SNN_ENGINE_PERSISTENT: one cooperative launch per batch of steps, the two
- *       phases separated by bounded grid-wide barriers.
+ *     SNN_ENGINE_PERSISTENT: the pipelined engine's schedule in one cooperative
+ *       launch per batch of steps, one bounded grid-wide barrier per step in place
+ *       of the kernel boundary.
  */
 #define SNN_ENGINE_DEFAULT 0
 #define SNN_ENGINE_GRAPH 1

@@ -651,17 +651,8 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
             snn_destroy(net);
             return fail(SNN_ECUDA, "shared memory opt-in of the blocked delivery kernel failed");
         }
-        if (net->engine == SNN_ENGINE_PERSISTENT) {
-            int coop = 0;
-            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, net->device);
-            const int per_sm = coop ? snn::persistent_blocks_per_sm() : 0;
-            if (per_sm < 1) {
-                snn_destroy(net);
-                return fail(SNN_ENOTSUP, "cooperative launch of the persistent engine is not available");
-            }
-            net->persistent_grid = net->num_sms;  // one CTA per SM (all co-resident)
-        }
-        if (net->engine == SNN_ENGINE_PIPELINED) {
+        if (net->engine == SNN_ENGINE_PIPELINED || net->engine == SNN_ENGINE_PERSISTENT) {
+            // the persistent engine runs the pipelined schedule on the same state
             // state "after 0 steps" is buffer 1; the first kernel decides step 0's spikes
             const int64_t quad_warps = ((net->n + 3) / 4 + 31) / 32;
             net->step_grid = snn::step_grid(net->num_sms, quad_warps);
@@ -692,6 +683,23 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
             if (rc != SNN_OK) {
                 snn_destroy(net);
                 return rc;
+            }
+        }
+        if (net->engine == SNN_ENGINE_PERSISTENT) {
+            // every CTA of the cooperative launch must be resident at once
+            int coop = 0;
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, net->device);
+            const int per_sm = coop ? snn::persistent_blocks_per_sm(a) : 0;
+            if (per_sm < 1) {
+                snn_destroy(net);
+                return fail(SNN_ENOTSUP, "cooperative launch of the persistent engine is not available");
+            }
+            net->persistent_grid = std::min(net->step_grid, per_sm * net->num_sms);
+            net->step_grid = net->persistent_grid;
+            a.neuron_warps = step_neuron_warps(a.quad_warps, net->persistent_grid);
+            if (snn::persistent_blocks_per_sm(a) * net->num_sms < net->persistent_grid) {
+                snn_destroy(net);
+                return fail(SNN_ENOTSUP, "the persistent engine's grid does not fit on the GPU at once");
             }
         }
         rc = (net->engine == SNN_ENGINE_GRAPH || net->engine == SNN_ENGINE_PIPELINED) ? capture_graph(net) : SNN_OK;
@@ -777,7 +785,7 @@ int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *
         for (size_t g = 0; g < G; ++g) {
             for (int64_t k = 0; k < m; ++k, ++used) {
                 cudaEventRecord(ev[3 * used], st);
-                if (net->engine == SNN_ENGINE_PIPELINED) {
+                if (net->engine == SNN_ENGINE_PIPELINED || net->engine == SNN_ENGINE_PERSISTENT) {
                     const int ph = static_cast<int>((net->t + done + k) % snn::kPhasePeriod);
                     snn::launch_step(grouped ? net->group_args[g] : net->args, static_cast<int>(k), ph,
                                      grouped ? net->group_grid[g] : net->step_grid, st);
@@ -929,8 +937,9 @@ int snn_get_info(const snn_net *net, snn_info *out)
     out->record_format = net->format;
     out->bytes_per_synapse = snn::record_bytes(net->format);
     out->n_circuits = static_cast<int32_t>(net->circuits.size());
-    out->schedule_ctas = net->engine == SNN_ENGINE_PIPELINED ? net->step_grid : net->deliver_grid;
-    out->schedule_delivery_warps = net->engine == SNN_ENGINE_PIPELINED ? net->args.delivery_warps : 0;
+    const bool step_kernel = net->engine == SNN_ENGINE_PIPELINED || net->engine == SNN_ENGINE_PERSISTENT;
+    out->schedule_ctas = step_kernel ? net->step_grid : net->deliver_grid;
+    out->schedule_delivery_warps = step_kernel ? net->args.delivery_warps : 0;
     out->target_blocks = net->args.n_blocks;
     out->circuits_per_group = net->circuits_per_group;
     std::memcpy(out->i8_base, net->i8_base, sizeof(out->i8_base));
@@ -944,7 +953,8 @@ int snn_get_layout(const snn_net *net, snn_layout *out)
     const snn::Layout &L = net->L;
     out->ctl = L.ctl;
     out->params = L.tables;
-    const bool second = net->engine == SNN_ENGINE_PIPELINED && ((net->t - 1) & 1);
+    const bool second = (net->engine == SNN_ENGINE_PIPELINED || net->engine == SNN_ENGINE_PERSISTENT) &&
+                        ((net->t - 1) & 1);
     out->U = second ? L.U2 : L.U;
     out->I = L.I;
     out->R = second ? L.R2 : L.R;
@@ -981,7 +991,7 @@ std::vector<std::pair<uint64_t, uint64_t>> state_segments(const snn_net *net)
     std::vector<std::pair<uint64_t, uint64_t>> seg = {
         {L.ctl, sizeof(snn::Ctl)}, {L.U, 4 * uint64_t(net->npad)}, {L.I, 4 * uint64_t(net->npad)},
         {L.R, uint64_t(net->npad)}, {L.ring, 4 * uint64_t(snn::kDMax) * net->npad}};
-    if (net->engine == SNN_ENGINE_PIPELINED) {
+    if (net->engine == SNN_ENGINE_PIPELINED || net->engine == SNN_ENGINE_PERSISTENT) {
         seg.push_back({L.U2, 4 * uint64_t(net->npad)});
         seg.push_back({L.R2, uint64_t(net->npad)});
         seg.push_back({L.queue, 4 * sizeof(snn::QueueEntry) * net->npad});

@@ -17,7 +17,6 @@ constexpr int kRowAlign = 4;                 // synapse rows padded to whole int
 constexpr int kChunk = 256;                  // synapses per delivery work item (32 lanes x 2 quads)
 constexpr int kUpdateThreads = 128;          // 4 neurons per thread
 constexpr int kDeliverThreads = 256;
-constexpr int kPersistThreads = 512;         // one CTA per SM in the persistent engine
 constexpr int kStepDeliverWarps = 8;         // delivery warps per CTA of the pipelined step kernel
 constexpr int kStepMaxThreads = 384;            // neuron warps (<= 4) + delivery warps per CTA
 constexpr int kStepMaxNeuronWarps = 4;
@@ -219,7 +218,7 @@ int prepare_blocked_kernel();
 void launch_deliver_blocked(const StepArgs &a, const int32_t *list, int64_t n, int64_t t, int k, void *stream);
 int deliver_list_blocks_per_sm();
 int update_grid(int64_t n);  // CTAs of k_update for n neurons
-int persistent_blocks_per_sm();
+int persistent_blocks_per_sm(const StepArgs &a);
 int launch_persistent(const StepArgs &a, int64_t n_steps, int grid, void *stream);
 // pipelined: B(t), A(t+1), D(t); ph = t mod 64.  With `programmatic`, the launch may
 // begin while the previous kernel in the stream still runs (it waits inside).

@@ -19,12 +19,14 @@
 //   k_step               -- pipelined (default): one kernel per step delivers step t's
 //                           spikes while it finishes step t's update and decides step
 //                           t+1's spikes (a spike at s depends only on spikes <= s-2);
-//                           replayed from a CUDA graph with programmatic launch;
+//                           replayed from a CUDA graph with programmatic launch
+//                           (batches may run in circuit groups);
 //   k_update + k_deliver -- one kernel per phase, replayed from a CUDA graph (batches
 //                           may run in circuit groups: k_update takes a neuron range);
-//   k_persistent         -- one cooperative launch for a batch of steps, the phases
-//                           separated by grid-wide barriers whose spin-waits are
-//                           bounded (on timeout the kernel records an error and exits).
+//   k_persistent         -- the pipelined schedule in one cooperative launch for a
+//                           batch of steps, one grid-wide barrier per step whose
+//                           spin-wait is bounded (on timeout the kernel records an
+//                           error and exits).
 // k_deliver_list delivers a given sender list (measurement and tests); blocked records
 // (target-blocked rows) have their own phase 2, k_deliver_blocked, at the end of this
 // file.
@@ -352,41 +354,6 @@ __device__ __forceinline__ bool grid_barrier(const StepArgs &a, Ctl *ctl, uint32
     return s_ok != 0;
 }
 
-__global__ void __launch_bounds__(kPersistThreads, 1) k_persistent(const StepArgs a, const int64_t n_steps)
-{
-    __shared__ SharedTables s;
-    stage_tables(a, s);
-    Ctl *ctl = a.ctl;
-    const int64_t t0 = ctl->t_base;
-    uint32_t begin = ctl->step_begin[t0 & 1];
-    const int64_t nquads = (a.n + 3) / 4;
-    const int64_t quad_warps = (nquads + 31) / 32;
-    const int64_t warp = spread_warp();
-    const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    uint32_t nbar = 0;
-    for (int64_t st = 0; st < n_steps; ++st) {
-        const int64_t t = t0 + st;
-        // phase 1: warp g updates quads 32g .. 32g+31 (coalesced), warps spread over SMs
-        for (int64_t g = warp; g < quad_warps; g += nwarps) {
-            const int64_t q = g * 32 + lane;
-            int32_t spk[4] = {0, 0, 0, 0};
-            if (q < nquads) update_quad(a, s, t, q, spk);
-            append_spikes(a, t, q * 4, spk);
-        }
-        if (!grid_barrier(a, ctl, ++nbar)) return;
-        const uint32_t cur = ld_acquire_u32(&ctl->cursor);
-        const uint32_t end = cur < a.rast_cap ? cur : a.rast_cap;
-        deliver_list(a, t, a.rast_nrn + begin, end > begin ? static_cast<int64_t>(end - begin) : 0, warp, nwarps);
-        begin = cur;
-        if (!grid_barrier(a, ctl, ++nbar)) return;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctl->t_base = t0 + n_steps;
-        ctl->step_begin[(t0 + n_steps) & 1] = begin;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Pipelined engine: one kernel per step.
 //
@@ -671,6 +638,36 @@ __global__ void __launch_bounds__(kStepMaxThreads, 2) k_prime(const StepArgs a)
     const int64_t t = -1;
     for (int64_t g = (a.quad_base >> 5) + static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < a.quad_warps; g += nw)
         pipe_quad(a, t, -1, g, g * 32 + (threadIdx.x & 31) < nquads, false, false);
+}
+
+// Persistent engine: the pipelined schedule in one cooperative launch for a run of
+// steps.  Iteration t does what the step kernel K_t does (neuron warps: B(t) then
+// A(t+1); delivery warps: D(t)); one bounded grid barrier between iterations stands in
+// for the kernel boundary, which orders D(t)'s ring sums and A(t+1)'s queue before
+// iteration t+1 reads them.  Every warp keeps its neuron groups for the whole launch.
+__global__ void __launch_bounds__(kStepMaxThreads, 1) k_persistent(const StepArgs a, const int64_t n_steps)
+{
+    Ctl *ctl = a.ctl;
+    const int64_t t0 = ctl->t_base;
+    const int wib = threadIdx.x >> 5;
+    const int64_t nquads = (a.n + 3) / 4;
+    const int64_t nw = static_cast<int64_t>(a.neuron_warps) * gridDim.x;
+    const int dwarps = static_cast<int>(blockDim.x >> 5) - a.neuron_warps;
+    const bool leader = blockIdx.x == 0 && threadIdx.x == 32 * a.neuron_warps;
+    const int64_t dw = static_cast<int64_t>(wib - a.neuron_warps) * gridDim.x + blockIdx.x;
+    uint32_t nbar = 0;
+    for (int64_t st = 0; st < n_steps; ++st) {
+        const int64_t t = t0 + st;
+        const int ph = static_cast<int>(t & (kPhasePeriod - 1));
+        if (wib < a.neuron_warps) {
+            for (int64_t g = static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < a.quad_warps; g += nw)
+                pipe_quad(a, t, ph, g, g * 32 + (threadIdx.x & 31) < nquads, true, false);
+        } else {
+            pipe_deliver(a, t, ph, leader, dw, static_cast<int64_t>(dwarps) * gridDim.x, false);
+        }
+        if (!grid_barrier(a, ctl, ++nbar)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->t_base = t0 + n_steps;
 }
 
 
@@ -1008,10 +1005,10 @@ void launch_advance(Ctl *ctl, int64_t m, void *stream)
 
 void launch_resync(Ctl *ctl, void *stream) { k_resync<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(ctl); }
 
-int persistent_blocks_per_sm()
+int persistent_blocks_per_sm(const StepArgs &a)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent, kPersistThreads, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent, step_threads(a), 0) != cudaSuccess) return 0;
     return nb;
 }
 
@@ -1021,7 +1018,7 @@ int launch_persistent(const StepArgs &a, int64_t n_steps, int grid, void *stream
     int64_t n = n_steps;
     void *params[] = {&args, &n};
     const cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(k_persistent), dim3(grid),
-                                                      dim3(kPersistThreads), params, 0,
+                                                      dim3(step_threads(a)), params, 0,
                                                       static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? 0 : static_cast<int>(e);
 }
