@@ -511,8 +511,11 @@ def run_gpu(args):
 
     torch.cuda.empty_cache()
 
-    def run_workload(label, circuits=None, wlx=None, fmt=snn.RECORD_PLAIN9, n_steps=None, tune=False, weng=None):
-        """Build, optionally autotune, warm up and time a workload; returns a summary."""
+    def run_workload(label, circuits=None, wlx=None, fmt=snn.RECORD_PLAIN9, n_steps=None, tune=False, weng=None,
+                     region=None):
+        """Build, optionally autotune, warm up and time a workload; returns a summary.  With
+        --profile-region equal to `region`, the timed region is bracketed by
+        cudaProfilerStart/Stop (for ncu --profile-from-start off)."""
         t0 = time.perf_counter()
         weng = engine if weng is None else weng
         if circuits is not None:
@@ -524,7 +527,9 @@ def run_gpu(args):
                                record_format=fmt)
         build = time.perf_counter() - t0
         tuned = None
-        if tune:
+        if tune and args.batched_groups >= 0:
+            xnet.set_circuit_groups(args.batched_groups)  # fixed grouping, default schedule
+        elif tune:
             from paper_2405_02019_gb300 import autotune
 
             tuned = autotune.autotune(xnet, steps=tps, cache_path=None)
@@ -536,9 +541,15 @@ def run_gpu(args):
         torch.cuda.synchronize(dev)
         b0 = torch.cuda.Event(enable_timing=True)
         b1 = torch.cuda.Event(enable_timing=True)
+        prof = region is not None and args.profile_region == region
+        if prof:
+            torch.cuda.profiler.start()
         b0.record(stream)
         xnet.step(nsteps)
         b1.record(stream)
+        if prof:
+            torch.cuda.synchronize(dev)
+            torch.cuda.profiler.stop()
         torch.cuda.synchronize(dev)
         xsecs = b0.elapsed_time(b1) * 1e-3
         xnet.read_spikes()
@@ -567,12 +578,12 @@ def run_gpu(args):
         extra["batched"] = run_workload("32 PD circuits, neuron/in-degree scales U{100..1000} permille, seeds "
                                         "1000+c, 2 s each", circuits=[(w.scale_n_permille, w.scale_k_permille, w.seed)
                                                                       for w in bw],
-                                        n_steps=args.batched_steps, tune=True)
+                                        n_steps=args.batched_steps, tune=True, region="batched")
         extra["batched"]["speedup_vs_single_circuit"] = extra["batched"]["value"] / value
     if "x4" in args.extra:
         wx = workload.WORKLOADS["pd_x4"]
         extra["scaled_up_plain"] = run_workload("pd_x4 plain: 308,676 neurons, full in-degrees", wlx=wx,
-                                                n_steps=args.x4_steps)
+                                                n_steps=args.x4_steps, region="x4")
         extra["scaled_up_int8"] = run_workload("pd_x4 packed int8 records", wlx=wx, fmt=snn.RECORD_PACKED_I8,
                                                n_steps=args.x4_steps)
         extra["scaled_up_int8"]["speedup_vs_plain"] = (extra["scaled_up_int8"]["value"] /
@@ -669,7 +680,11 @@ def main():
     ap.add_argument("--forms", nargs="*", default=["int8_pair", "bf16", "blocked6", "blocked4"])
     ap.add_argument("--extra", nargs="*", default=["batched", "x4"])
     ap.add_argument("--batched-steps", type=int, default=20480)
+    ap.add_argument("--batched-groups", type=int, default=-1,
+                    help="circuits per group for the batched workload instead of autotuning (-1: autotune)")
     ap.add_argument("--x4-steps", type=int, default=10240)
+    ap.add_argument("--profile-region", choices=["none", "batched", "x4"], default="none",
+                    help="bracket that workload's timed region with cudaProfilerStart/Stop")
     ap.add_argument("--form-steps", type=int, default=20)
     ap.add_argument("--engine", default="default", choices=["default", "graph", "persistent", "pipelined"])
     args = ap.parse_args()
