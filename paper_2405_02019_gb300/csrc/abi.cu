@@ -168,6 +168,7 @@ void build_groups(snn_net *net)
             a.queue = net->args.queue + lo;
             a.queue_cap = hi - lo;
             a.qcount = reinterpret_cast<uint32_t *>(net->arena + queue_count_offset(net, g, ranges.size()));
+            a.group_launch = 1;
         }
         net->group_args.push_back(a);
         net->group_grid.push_back(grid);

@@ -137,7 +137,7 @@ struct StepArgs {
     int32_t format;               // SNN_RECORD_*
     int32_t n_circuits;
     int32_t delivery_warps;       // pipelined engine: delivery warps per CTA
-    int32_t pad3;
+    int32_t group_launch;         // pipelined engine: 1 for a circuit group's launch (its own queues and range)
     const uint8_t *pop_id;        // population of every neuron [npad]
     const int32_t *group_circuit; // circuit of every group of 128 neurons [npad / 128]
     const CircuitInfo *circuits;  // [n_circuits]

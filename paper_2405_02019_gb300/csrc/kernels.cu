@@ -408,6 +408,27 @@ __device__ __forceinline__ void allow_next_grid() { asm volatile("griddepcontrol
 // without a quad pass valid = false).  Everything that does not depend on the
 // previous step (row bounds, Poisson thresholds, the Philox block) is done before
 // `wait_first` (if set) waits for the previous kernel.
+// A launch of one circuit group (kGroup) takes its queue counts, queue size and first
+// group of 128 neurons from the arguments; a launch over the whole index space uses the
+// control block's counts, npad entries per queue and group 0.  The two are separate
+// instantiations, so that the whole-network kernel carries none of the group indirection.
+template <bool kGroup>
+__device__ __forceinline__ uint32_t *queue_counts(const StepArgs &a)
+{
+    return kGroup ? a.qcount : a.ctl->qcnt;
+}
+template <bool kGroup>
+__device__ __forceinline__ int64_t queue_entries(const StepArgs &a)
+{
+    return kGroup ? a.queue_cap : a.npad;
+}
+template <bool kGroup>
+__device__ __forceinline__ int64_t first_quad_warp(const StepArgs &a)
+{
+    return kGroup ? (a.quad_base >> 5) : 0;
+}
+
+template <bool kGroup>
 __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, int ph, int64_t g, bool valid,
                                           bool do_b, bool wait_first)
 {
@@ -515,7 +536,7 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, i
     const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     if (total == 0) return;
     uint32_t base = 0;
-    if (lane == 31) base = atomicAdd(&a.qcount[phn & 3], static_cast<uint32_t>(total));
+    if (lane == 31) base = atomicAdd(&queue_counts<kGroup>(a)[phn & 3], static_cast<uint32_t>(total));
     base = __shfl_sync(0xFFFFFFFFu, base, 31);
     if (cnt == 0) return;
     QueueEntry *region = a.queue + (phn & 3) * a.npad + base;
@@ -551,20 +572,21 @@ __device__ __forceinline__ void pipe_quad(const StepArgs &a, const int64_t &t, i
 // D(t), run by the delivery warps: grid-stride over (spike, 256-synapse chunk) items
 // of queue t mod 4.  The count, the raster base and the first item's entry are loaded
 // in one round trip.  The warp taking chunk 0 of spike j records it in the raster.
-template <int FMT>
+template <int FMT, bool kGroup>
 __device__ __forceinline__ void pipe_deliver_fmt(const StepArgs &a, const int64_t &t, int ph, int64_t dw, int64_t ndw,
                                                  uint32_t n, uint32_t rbase, int4 first)
 {
     const int lane = threadIdx.x & 31;
     const QueueEntry *qbuf = a.queue + (ph & 3) * a.npad;
     const int64_t cpr = a.chunks_per_row;
+    const int64_t cap = queue_entries<kGroup>(a);
     // items are (spike, run of `per` chunks); when every item is one chunk (few spikes) the
     // entry `first` loaded before n arrived belongs to this warp's first item
     const int64_t ipj = items_per_spike(cpr, n, ndw);
     const int64_t per = (cpr + ipj - 1) / ipj;
     for (int64_t it = dw;; it += ndw) {
         const int64_t j = it / ipj;
-        if (j >= a.queue_cap || j >= n) break;
+        if (j >= cap || j >= n) break;
         const int4 raw = (it == dw && ipj == cpr) ? first : __ldcg(reinterpret_cast<const int4 *>(qbuf + j));
         const int64_t part = it - j * ipj;
         if (part == 0 && lane == 0) {
@@ -582,30 +604,35 @@ __device__ __forceinline__ void pipe_deliver_fmt(const StepArgs &a, const int64_
     }
 }
 
+template <bool kGroup>
 __device__ __forceinline__ void pipe_deliver(const StepArgs &a, const int64_t &t, int ph, bool leader, int64_t dw,
                                              int64_t ndw, bool wait_first)
 {
     if (wait_first) wait_previous_grid();
-    const uint32_t n = __ldcg(&a.qcount[ph & 3]);
+    const uint32_t n = __ldcg(&queue_counts<kGroup>(a)[ph & 3]);
     const uint32_t rbase = __ldcg(&a.ctl->step_begin[t & 1]);
     // speculative: the entry of this warp's first item under one chunk per item, issued
     // alongside the count so both arrive in one round trip
     const int64_t j0 = dw / a.chunks_per_row;
-    const int4 first = j0 < a.queue_cap ? __ldcg(reinterpret_cast<const int4 *>(a.queue + (ph & 3) * a.npad + j0))
+    const int4 first = j0 < queue_entries<kGroup>(a) ? __ldcg(reinterpret_cast<const int4 *>(a.queue + (ph & 3) * a.npad + j0))
                                    : make_int4(0, 0, 0, 0);
     if (leader) {
         a.ctl->step_begin[(t + 1) & 1] = rbase + n;
         a.ctl->cursor = rbase + n;
-        a.qcount[(ph + 2) & 3] = 0;  // the queue the next kernel fills after this one
+        queue_counts<kGroup>(a)[(ph + 2) & 3] = 0;  // the queue the next kernel fills after this one
         if (static_cast<uint64_t>(rbase) + n > a.rast_cap) atomicOr(&a.ctl->err, kErrRaster);
     }
-    if (a.format == SNN_RECORD_PACKED_I8) pipe_deliver_fmt<SNN_RECORD_PACKED_I8>(a, t, ph, dw, ndw, n, rbase, first);
-    else if (a.format == SNN_RECORD_PACKED_BF16) pipe_deliver_fmt<SNN_RECORD_PACKED_BF16>(a, t, ph, dw, ndw, n, rbase, first);
-    else pipe_deliver_fmt<SNN_RECORD_PLAIN9>(a, t, ph, dw, ndw, n, rbase, first);
+    if (a.format == SNN_RECORD_PACKED_I8)
+        pipe_deliver_fmt<SNN_RECORD_PACKED_I8, kGroup>(a, t, ph, dw, ndw, n, rbase, first);
+    else if (a.format == SNN_RECORD_PACKED_BF16)
+        pipe_deliver_fmt<SNN_RECORD_PACKED_BF16, kGroup>(a, t, ph, dw, ndw, n, rbase, first);
+    else
+        pipe_deliver_fmt<SNN_RECORD_PLAIN9, kGroup>(a, t, ph, dw, ndw, n, rbase, first);
 }
 
 // t_base is read before waiting on the previous kernel: within a graph replay it only
 // changes in the replay's last node, and direct launches are not programmatic.
+template <bool kGroup>
 __global__ void __launch_bounds__(kStepMaxThreads, 2) k_step(const StepArgs a, const int k, const int ph)
 {
     allow_next_grid();
@@ -615,9 +642,9 @@ __global__ void __launch_bounds__(kStepMaxThreads, 2) k_step(const StepArgs a, c
         const int64_t nquads = (a.n + 3) / 4;
         const int64_t nw = static_cast<int64_t>(a.neuron_warps) * gridDim.x;
         bool first = true;
-        for (int64_t g = (a.quad_base >> 5) + static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < a.quad_warps;
-             g += nw) {
-            pipe_quad(a, t, ph, g, g * 32 + (threadIdx.x & 31) < nquads, true, first);
+        for (int64_t g = first_quad_warp<kGroup>(a) + static_cast<int64_t>(wib) * gridDim.x + blockIdx.x;
+             g < a.quad_warps; g += nw) {
+            pipe_quad<kGroup>(a, t, ph, g, g * 32 + (threadIdx.x & 31) < nquads, true, first);
             first = false;
         }
         if (first) wait_previous_grid();
@@ -625,7 +652,7 @@ __global__ void __launch_bounds__(kStepMaxThreads, 2) k_step(const StepArgs a, c
         const int dwarps = static_cast<int>(blockDim.x >> 5) - a.neuron_warps;
         const bool leader = blockIdx.x == 0 && threadIdx.x == 32 * a.neuron_warps;
         const int64_t dw = static_cast<int64_t>(wib - a.neuron_warps) * gridDim.x + blockIdx.x;
-        pipe_deliver(a, t, ph, leader, dw, static_cast<int64_t>(dwarps) * gridDim.x, true);
+        pipe_deliver<kGroup>(a, t, ph, leader, dw, static_cast<int64_t>(dwarps) * gridDim.x, true);
     }
 }
 
@@ -637,7 +664,7 @@ __global__ void __launch_bounds__(kStepMaxThreads, 2) k_prime(const StepArgs a)
     const int64_t nw = static_cast<int64_t>(a.neuron_warps) * gridDim.x;
     const int64_t t = -1;
     for (int64_t g = (a.quad_base >> 5) + static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < a.quad_warps; g += nw)
-        pipe_quad(a, t, -1, g, g * 32 + (threadIdx.x & 31) < nquads, false, false);
+        pipe_quad<true>(a, t, -1, g, g * 32 + (threadIdx.x & 31) < nquads, false, false);
 }
 
 // Persistent engine: the pipelined schedule in one cooperative launch for a run of
@@ -661,9 +688,9 @@ __global__ void __launch_bounds__(kStepMaxThreads, 1) k_persistent(const StepArg
         const int ph = static_cast<int>(t & (kPhasePeriod - 1));
         if (wib < a.neuron_warps) {
             for (int64_t g = static_cast<int64_t>(wib) * gridDim.x + blockIdx.x; g < a.quad_warps; g += nw)
-                pipe_quad(a, t, ph, g, g * 32 + (threadIdx.x & 31) < nquads, true, false);
+                pipe_quad<false>(a, t, ph, g, g * 32 + (threadIdx.x & 31) < nquads, true, false);
         } else {
-            pipe_deliver(a, t, ph, leader, dw, static_cast<int64_t>(dwarps) * gridDim.x, false);
+            pipe_deliver<false>(a, t, ph, leader, dw, static_cast<int64_t>(dwarps) * gridDim.x, false);
         }
         if (!grid_barrier(a, ctl, ++nbar)) return;
     }
@@ -942,7 +969,8 @@ int launch_step(const StepArgs &a, int k, int ph, int grid, void *stream, bool p
     attr[0].val.programmaticStreamSerializationAllowed = programmatic ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return static_cast<int>(cudaLaunchKernelEx(&cfg, k_step, a, k, ph));
+    if (a.group_launch) return static_cast<int>(cudaLaunchKernelEx(&cfg, k_step<true>, a, k, ph));
+    return static_cast<int>(cudaLaunchKernelEx(&cfg, k_step<false>, a, k, ph));
 }
 
 void launch_prime(const StepArgs &a, int grid, void *stream)
