@@ -1127,3 +1127,28 @@ def test_autotune_keeps_dynamics(model, tiny, tmp_path):
     res2 = autotune.autotune(net, steps=256, cache_path=str(tmp_path / "sched.json"))
     assert res2["schedule"] == res["schedule"]
     net.close()
+
+
+def test_autotune_on_a_batch_keeps_dynamics(model):
+    """Pipelined batch: the autotuner tries circuit groupings between a checkpoint and its
+    restore (which moves the pending spikes between queue layouts); every circuit's raster
+    still equals its standalone oracle run."""
+    from paper_2405_02019_gb300 import autotune
+
+    net = snn.Network(model, circuits=BATCH, steps_per_graph=64, engine=PIPE)
+    net.step(100)
+    first = net.read_spikes()
+    res = autotune.autotune(net, steps=64, cache_path=None)
+    assert {c["schedule"]["circuits_per_group"] for c in res["timings"]} == {0, 4}
+    assert net.info().circuits_per_group == res["schedule"]["circuits_per_group"]
+    net.step(150)
+    second = net.read_spikes()
+    g_t = np.concatenate([first[0], second[0]])
+    g_i = np.concatenate([first[1], second[1]])
+    base, n = net.circuits()
+    for c, (sn, sk, seed) in enumerate(BATCH):
+        o_t, o_i = oracle.Sim(model, oracle.build_network(model, sn, sk, seed), seed).run(250)
+        sel = (g_i >= base[c]) & (g_i < base[c] + n[c])
+        assert np.array_equal(g_t[sel], o_t), c
+        assert np.array_equal(g_i[sel] - base[c], o_i), c
+    net.close()
