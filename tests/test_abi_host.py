@@ -135,3 +135,38 @@ def test_blocked_records_sizes_and_rules(lib):
         snn.snn_query_sizes(spec)
     spec = snn._Spec(m, 100, 100, 1, record_format=snn.RECORD_BLOCKED6, engine=snn.ENGINE_GRAPH).spec
     assert snn.snn_query_sizes(spec).n_neurons == 7718
+
+
+def test_null_handle_is_rejected_before_any_device_work(lib):
+    """Every entry point that takes a network handle refuses a null one with SNN_EINVAL
+    (no device call is made, so this runs without a GPU)."""
+    i64 = C.c_int64(0)
+    u64 = C.c_uint64(0)
+    d = C.c_double(0)
+    info = _abi.snn_info()
+    layout = _abi.snn_layout()
+    buf = (C.c_int64 * 4)()
+    calls = {
+        "snn_step_n": lambda: lib.snn_step_n(None, 1, None),
+        "snn_read_spikes": lambda: lib.snn_read_spikes(None, None, None, 0, C.byref(i64)),
+        "snn_collect_spikes": lambda: lib.snn_collect_spikes(None, None, None, 0, C.byref(i64)),
+        "snn_read_rates": lambda: lib.snn_read_rates(None, 0, 10, buf, None),
+        "snn_get_info": lambda: lib.snn_get_info(None, C.byref(info)),
+        "snn_get_layout": lambda: lib.snn_get_layout(None, C.byref(layout)),
+        "snn_profile_steps": lambda: lib.snn_profile_steps(None, 1, None, C.byref(d), C.byref(d)),
+        "snn_get_out_degrees": lambda: lib.snn_get_out_degrees(None, buf),
+        "snn_get_circuits": lambda: lib.snn_get_circuits(None, buf, buf),
+        "snn_set_schedule": lambda: lib.snn_set_schedule(None, 152, 8, 1024),
+        "snn_set_circuit_groups": lambda: lib.snn_set_circuit_groups(None, 2),
+        "snn_save_state": lambda: lib.snn_save_state(None, None, 0, C.byref(u64)),
+        "snn_load_state": lambda: lib.snn_load_state(None, buf, 32),
+        "snn_deliver_spikes": lambda: lib.snn_deliver_spikes(None, buf, 1, 0, 0, None),
+        "snn_step_static": lambda: lib.snn_step_static(None, None, 1, 0, None),
+    }
+    for name, call in calls.items():
+        assert call() == _abi.SNN_EINVAL, name
+        assert b"null" in lib.snn_last_error(), name
+    lib.snn_destroy(None)  # a no-op
+    # every declared entry point that takes a handle is covered above
+    takes_handle = {n for n, (_, args) in _abi.PROTOTYPES.items() if args and args[0] is C.c_void_p}
+    assert takes_handle - {"snn_destroy"} == set(calls), takes_handle ^ set(calls)
