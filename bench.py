@@ -8,6 +8,8 @@ one JSON line.
   value     recurrent synaptic events/s (sum of the spikers' out-degrees / seconds),
             device-timed with CUDA events around snn_step_n graph replays
   rtf       real-time factor = wall time / biological time (§4.2)
+  events_incl_thalamic  value plus the thalamic drive's expected input events
+            (N_b K_ext,b nu_th per biological second, over the same wall time)
   e2e       the same metric through the public API with the raster read back to
             host memory every bench step (snn_step_n + snn_collect_spikes, which
             reads the previous bench step's spikes while the GPU runs this one)
@@ -75,6 +77,15 @@ def _recorded_traffic(kernel: str):
     if d.get("kernels_sha256_16") != _kernel_sources_hash() or kernel not in d:
         return None
     return d[kernel].get("dram_bytes_per_launch")
+
+
+def thalamic_events_per_bio_s(model, pop_offsets) -> float:
+    """Expected thalamic input events per biological second: every neuron of population
+    b receives K_ext,b independent Poisson inputs at nu_th (§2.2).  The step loop draws
+    their per-step sums from counter-based Poisson streams, so they are not counted on
+    the device; this is their expectation."""
+    n = np.diff(np.asarray(list(pop_offsets)[: model.n_pops + 1], dtype=np.int64))
+    return float((n * np.asarray(model.k_ext[: model.n_pops], dtype=np.float64) * model.nu_th_hz).sum())
 
 
 def _peaks():
@@ -339,6 +350,7 @@ def run_gpu(args):
     value = events_all / secs_max
     bio_s = args.steps * tps * model.dt_ms * 1e-3
     rtf = secs_max / bio_s
+    thal_bio = thalamic_events_per_bio_s(model, inf.pop_offsets)
 
     # end to end through the public API: step + raster read into host memory per bench step
     _barrier(ws)
@@ -612,6 +624,11 @@ def run_gpu(args):
                    "deliver_blocks": info.deliver_blocks, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (2.56 GB synapse store); ring and neuron state are L2-resident by design"},
         "rtf": rtf, "realtime_x": 1.0 / rtf, "spikes_per_tick": spikes / (args.steps * tps),
+        "events_incl_thalamic": {
+            "value": value + ws * thal_bio * bio_s / secs_max, "unit": "synaptic events/s",
+            "thalamic_per_bio_second": thal_bio,
+            "note": "recurrent events counted on the device plus the thalamic drive's expected events "
+                    "(sum over populations of N_b K_ext,b nu_th per biological second)"},
         "events_per_tick": events / (args.steps * tps),
         "e2e": {"value": e2e_value, "unit": "synaptic events/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": d2h / args.steps,
