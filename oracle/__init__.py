@@ -9,7 +9,7 @@ Functions mirror the paper's steps:
   pop_sizes / pair_count      -- Table params2 sizes, the N_pre N_post p count (§2.2)
   build_network               -- synapse sampling with replacement, grouped by sender (§2.2, §3.5)
   initial_u                   -- u_init Gaussians (Table params2)
-  poisson_table / draws       -- thalamic Poisson drive (§2.2)
+  poisson_table / poisson_count_at / draws -- thalamic Poisson drive (§2.2)
   lif_trace                   -- one neuron under a given input (Listing push, Eqs. mem/psc/ref)
   Sim.run                     -- the full deferred-push step loop (Listings push, push2; §3.2 ring)
   SimMT.run                   -- the same loop on host threads that own target ranges (cpu_mt.c),
@@ -109,6 +109,8 @@ def lib():
         L.or_build.restype = C.c_int
         L.or_initial_u.argtypes = [P(OrModel), C.c_int32, C.c_uint64, vp]
         L.or_poisson_table.argtypes = [P(OrModel), C.c_int32, vp]
+        L.or_poisson_count_at.argtypes = [P(OrModel), C.c_int32, C.c_uint64]
+        L.or_poisson_count_at.restype = C.c_int32
         L.or_poisson_draws.argtypes = [P(OrModel), C.c_uint64, C.c_int32, C.c_int64, C.c_int64,
                                        C.c_int64, vp]
         L.or_lif_trace.argtypes = [P(OrModel), C.c_float, C.c_float, C.c_int32, C.c_int64, vp, vp,
@@ -177,6 +179,11 @@ def poisson_table(m, pop: int) -> np.ndarray:
     out = np.zeros(PKMAX, dtype=np.uint64)
     lib().or_poisson_table(C.byref(_model(m)), pop, _p(out))
     return out
+
+
+def poisson_count_at(m, pop: int, v: int) -> int:
+    """T = #{k : v >= C_k} for a chosen 63-bit v (the inversion step of the draws)."""
+    return int(lib().or_poisson_count_at(C.byref(_model(m)), pop, v))
 
 
 def poisson_draws(m, seed: int, pop: int, t: int, i0: int, n: int) -> np.ndarray:

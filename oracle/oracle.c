@@ -350,6 +350,15 @@ static int32_t or_poisson_count(uint64_t v, const uint64_t C[OR_PKMAX])
     return T;
 }
 
+/* T for a given 63-bit uniform v and population `pop`: the inversion count of the
+ * table above (pins its boundaries without a random draw). */
+int32_t or_poisson_count_at(const or_model *m, int32_t pop, uint64_t v)
+{
+    uint64_t C[OR_PKMAX];
+    or_poisson_table(m, pop, C);
+    return or_poisson_count(v, C);
+}
+
 /* n draws for neurons i0..i0+n-1 (all taken as population `pop`) at step t. */
 void or_poisson_draws(const or_model *m, uint64_t seed, int32_t pop, int64_t t, int64_t i0,
                       int64_t n, int32_t *out)

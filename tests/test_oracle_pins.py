@@ -139,6 +139,7 @@ def test_refractory_clamp_and_isi_closed_form(model):
     spk = np.flatnonzero(tr["spike"])
     assert len(spk) > 5
     for s in spk[:-1]:
+        assert tr["U"][s] == 0.0  # reset on the spike step itself
         assert np.all(tr["U"][s + 1: s + 21] == 0.0)
         assert tr["R"][s] == 20 and tr["R"][s + 20] == 0
         assert tr["U"][s + 21] > 0.0
@@ -148,6 +149,20 @@ def test_refractory_clamp_and_isi_closed_form(model):
     isi = np.diff(spk)
     assert np.all(isi[2:] == 20 + j_star)
     assert np.all(isi >= 21)
+
+
+def test_refractory_clamp_holds_the_reset_value(model):
+    """Eq. ref holds U at u_reset, which need not be the rest potential: with u_reset
+    5 mV below rest, U is -5 mV (relative to rest) from the spike step through the 20
+    refractory steps, and integrates again from there."""
+    m2 = model.replace(u_reset_mV=model.u_rest_mV - 5.0)
+    assert oracle.step_constants(m2)["u_reset"] == np.float32(-5.0)
+    tr = oracle.lif_trace(m2, np.full(3000, int(round(110.0 * 4096)), np.int32))
+    spk = np.flatnonzero(tr["spike"])
+    assert len(spk) > 5
+    for s in spk[:-1]:
+        assert np.all(tr["U"][s: s + 21] == np.float32(-5.0))
+        assert tr["U"][s + 21] > -5.0
 
 
 def _float_with_product(p, target, below=False):
@@ -271,6 +286,21 @@ def test_thalamic_rate_example(model):
 
 
 @pytest.mark.parametrize("pop", range(8))
+def test_poisson_inversion_boundaries(model, pop):
+    """T = #{k : v >= C_k}: a uniform exactly on threshold C_k already counts it (T =
+    k + 1), one below does not (T = k); v = 0 gives 0 and the largest 63-bit value the
+    last count whose threshold is below 2^63."""
+    C = oracle.poisson_table(model, pop)
+    assert oracle.poisson_count_at(model, pop, 0) == 0
+    for k in range(6):
+        assert C[k] < C[k + 1]
+        assert oracle.poisson_count_at(model, pop, int(C[k])) == k + 1
+        assert oracle.poisson_count_at(model, pop, int(C[k]) - 1) == k
+    top = 2**63 - 1
+    assert oracle.poisson_count_at(model, pop, top) == int(np.count_nonzero(C <= top))
+
+
+@pytest.mark.parametrize("pop", range(8))
 def test_poisson_draw_statistics(model, pop):
     n = 400_000
     T = oracle.poisson_draws(model, seed=3, pop=pop, t=11, i0=0, n=n).astype(np.float64)
@@ -382,6 +412,23 @@ def test_weight_distributions(model, tiny_net):
         ks = scipy.stats.kstest(x, scipy.stats.norm(mu, sd).cdf)
         # the fixed-point quantum (1/4096 pA / w_f ~ 4e-7 mV) is far below sd
         assert ks.pvalue > 1e-4, name
+
+
+def test_weights_clip_at_zero_on_their_own_side(model):
+    """A weight drawn past zero is clipped to zero, never flipped in sign: with the SD
+    raised to the full mean (so that clipping is common), excitatory weights stay >= 0,
+    inhibitory ones <= 0, and each side's share of zeros is Phi(-1) within 4 standard
+    errors."""
+    m2 = model.replace(w_sd_mV=[abs(mu) for mu in model.w_mean_mV], overrides=[(2, 0, 0.3, 0.3)])
+    net = oracle.build_network(m2, 50, 50, 3)
+    pre, pp, qp = _pre_post_pops(net)
+    p0 = scipy.stats.norm.cdf(-1.0)
+    for name, sel, sign in (("exc", pp % 2 == 0, 1), ("inh", pp % 2 == 1, -1)):
+        w = net.w_fx[sel]
+        assert np.all(sign * w >= 0), name
+        n = len(w)
+        frac = np.count_nonzero(w == 0) / n
+        assert abs(frac - p0) < 4 * math.sqrt(p0 * (1 - p0) / n), (name, frac, p0)
 
 
 def _discretised_clipped_normal(mu, sd, dt=0.1, dmax=63):
