@@ -273,6 +273,17 @@ int snn_query_sizes(const snn_spec *spec, snn_sizes *out);
 int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_bytes, void *cuda_stream,
                       snn_net **out);
 
+/* Host only (no GPU, no device memory): builds the network of `spec` exactly as
+ * snn_build_network does (§2.2 sampling; the indexed store of §3.5: rows grouped by
+ * sender and sorted by delay) and copies it, without the row padding, into caller
+ * arrays: row_ptr[N + 1] (row i is row_ptr[i] .. row_ptr[i + 1]), post[S] (target
+ * neuron), w_fx[S] (weight, 2^-12 pA units), delay[S] (steps) and u0[N] (initial
+ * potential, mV relative to rest), with N = snn_sizes.n_neurons and S =
+ * snn_sizes.n_synapses.  Any output may be NULL to skip it.  Plain records only.
+ * Errors: SNN_EINVAL (spec, or another record format), SNN_ENOMEM. */
+int snn_export_network(const snn_spec *spec, int64_t *row_ptr, int32_t *post, int32_t *w_fx, uint8_t *delay,
+                       float *u0);
+
 /* Enqueues n_steps steps (Listing push / push2 of §3.1; one step = dt) on
  * `cuda_stream` and returns without waiting.  n_steps = 0 is a no-op.
  * Errors: SNN_EINVAL (n_steps < 0), SNN_ESTATE (after a sticky device error),

@@ -121,6 +121,25 @@ def snn_query_sizes(spec: snn_spec) -> snn_sizes:
     return out
 
 
+def snn_export_network(spec: snn_spec) -> dict:
+    """The network of `spec` built on the host, without a GPU (snn_export_network):
+    row_ptr, post, w_fx, delay and u0 as numpy arrays, rows without their padding."""
+    sz = snn_query_sizes(spec)
+    n, S = int(sz.n_neurons), int(sz.n_synapses)
+    out = {"row_ptr": np.zeros(n + 1, np.int64), "post": np.zeros(S, np.int32), "w_fx": np.zeros(S, np.int32),
+           "delay": np.zeros(S, np.uint8), "u0": np.zeros(n, np.float32)}
+    _check(load().snn_export_network(C.byref(spec), *(C.c_void_p(_ptr(out[k])) for k in
+                                                      ("row_ptr", "post", "w_fx", "delay", "u0"))),
+           "snn_export_network")
+    return out
+
+
+def export_network(model, scale_n: int = 1000, scale_k: int = 1000, seed: int = 1, circuits=None) -> dict:
+    """Host-only build of a microcircuit (or a batch of circuits, as in Network) with the
+    simulator's own builder; see snn_export_network."""
+    return snn_export_network(_Spec(model, scale_n, scale_k, seed, circuits=circuits).spec)
+
+
 def snn_build_network(spec: snn_spec, arena_ptr: int, arena_bytes: int, stream: int) -> int:
     h = C.c_void_p()
     _check(load().snn_build_network(C.byref(spec), C.c_void_p(arena_ptr), arena_bytes, C.c_void_p(stream),

@@ -116,6 +116,8 @@ PROTOTYPES = {
     "snn_query_sizes": (C.c_int, [C.POINTER(snn_spec), C.POINTER(snn_sizes)]),
     "snn_build_network": (C.c_int, [C.POINTER(snn_spec), C.c_void_p, C.c_uint64, C.c_void_p,
                                     C.POINTER(C.c_void_p)]),
+    "snn_export_network": (C.c_int, [C.POINTER(snn_spec), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p]),
     "snn_step_n": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
     "snn_read_spikes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "snn_read_rates": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]),

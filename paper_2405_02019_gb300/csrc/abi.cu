@@ -472,6 +472,42 @@ int snn_query_sizes(const snn_spec *spec, snn_sizes *out)
     return SNN_OK;
 }
 
+int snn_export_network(const snn_spec *spec, int64_t *row_ptr, int32_t *post, int32_t *w_fx, uint8_t *delay,
+                       float *u0)
+{
+    if (!spec) return fail(SNN_EINVAL, "null argument");
+    std::string why;
+    if (!snn::validate_spec(*spec, why)) return fail(SNN_EINVAL, why);
+    if (spec->record_format != SNN_RECORD_PLAIN9) return fail(SNN_EINVAL, "export takes plain records");
+    try {
+        snn::Constants c;
+        snn::compute_constants(spec->model, c);
+        snn::HostNetwork hn;
+        if (!snn::build_host_network(*spec, c, hn, why)) return fail(SNN_EINVAL, why);
+        // the caller sized the arrays by snn_query_sizes
+        int64_t real = 0;
+        for (int64_t i = 0; i < hn.n; ++i) real += hn.out_degree[i];
+        if (hn.n != snn::count_neurons(*spec) || hn.n_syn != snn::count_synapses(*spec) || real != hn.n_syn)
+            return fail(SNN_EINVAL, "built network disagrees with snn_query_sizes");
+        // the padded rows of the indexed store keep their real synapses first
+        int64_t k = 0;
+        if (row_ptr) row_ptr[0] = 0;
+        for (int64_t i = 0; i < hn.n; ++i) {
+            const int64_t a = hn.row_ptr[i];
+            const int64_t len = hn.out_degree[i];
+            if (post) std::memcpy(post + k, hn.tgt.data() + a, sizeof(int32_t) * len);
+            if (w_fx) std::memcpy(w_fx + k, hn.w.data() + a, sizeof(int32_t) * len);
+            if (delay) std::memcpy(delay + k, hn.d.data() + a, len);
+            k += len;
+            if (row_ptr) row_ptr[i + 1] = k;
+        }
+        if (u0) std::memcpy(u0, hn.u0.data(), sizeof(float) * hn.n);
+    } catch (const std::bad_alloc &) {
+        return fail(SNN_ENOMEM, "host allocation failed while building the network");
+    }
+    return SNN_OK;
+}
+
 int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_bytes, void *cuda_stream,
                       snn_net **out)
 {
