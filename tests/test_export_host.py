@@ -57,6 +57,21 @@ def test_export_equals_oracle_network(model, scale):
     assert np.all(d[1:][same_row] >= d[:-1][same_row])
 
 
+def test_export_equals_oracle_when_clipping_is_common(model):
+    """The same comparison under a model whose draws often leave the clipping bounds:
+    weight SD equal to the mean (about 16 % of weights clip at zero) and excitatory
+    delays of 5.5 +- 1.5 ms (a fifth clip at 63 steps), inhibitory ones of 0.2 +- 0.2 ms
+    (most clip at 1 step)."""
+    m2 = model.replace(w_sd_mV=[abs(mu) for mu in model.w_mean_mV], overrides=[(2, 0, 0.3, 0.3)],
+                       d_mean_ms=[5.5 if b % 2 == 0 else 0.2 for b in range(8)],
+                       d_sd_ms=[1.5 if b % 2 == 0 else 0.2 for b in range(8)])
+    net = snn.export_network(m2, 30, 30, 4)
+    onet = oracle.build_network(m2, 30, 30, 4)
+    _assert_same_network(net, onet)
+    assert np.count_nonzero(net["delay"] == 63) > 0.1 * len(net["delay"]) * 0.5
+    assert np.count_nonzero(net["w_fx"] == 0) > 0.1 * len(net["w_fx"])
+
+
 def test_export_of_a_batch_places_each_circuit_alone(model):
     circuits = [(20, 40, 5), (35, 10, 6), (1, 1, 9)]
     net = snn.export_network(model, circuits=circuits)
