@@ -279,8 +279,11 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
  * arrays: row_ptr[N + 1] (row i is row_ptr[i] .. row_ptr[i + 1]), post[S] (target
  * neuron), w_fx[S] (weight, 2^-12 pA units), delay[S] (steps) and u0[N] (initial
  * potential, mV relative to rest), with N = snn_sizes.n_neurons and S =
- * snn_sizes.n_synapses.  Any output may be NULL to skip it.  Plain records only.
- * Errors: SNN_EINVAL (spec, or another record format), SNN_ENOMEM. */
+ * snn_sizes.n_synapses.  Any output may be NULL to skip it.  For the packed formats
+ * (SNN_RECORD_PACKED_I8 / _BF16) the fields are decoded from the packed words and w_fx
+ * is the weight the kernels read back (the per-pair affine code, or the bfloat16
+ * current rounded to 2^-12 pA).  Errors: SNN_EINVAL (spec, or a blocked format),
+ * SNN_ENOMEM. */
 int snn_export_network(const snn_spec *spec, int64_t *row_ptr, int32_t *post, int32_t *w_fx, uint8_t *delay,
                        float *u0);
 

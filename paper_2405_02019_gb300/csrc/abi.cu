@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -478,7 +479,9 @@ int snn_export_network(const snn_spec *spec, int64_t *row_ptr, int32_t *post, in
     if (!spec) return fail(SNN_EINVAL, "null argument");
     std::string why;
     if (!snn::validate_spec(*spec, why)) return fail(SNN_EINVAL, why);
-    if (spec->record_format != SNN_RECORD_PLAIN9) return fail(SNN_EINVAL, "export takes plain records");
+    const int fmt = spec->record_format;
+    if (fmt != SNN_RECORD_PLAIN9 && fmt != SNN_RECORD_PACKED_I8 && fmt != SNN_RECORD_PACKED_BF16)
+        return fail(SNN_EINVAL, "export takes plain or packed records");
     try {
         snn::Constants c;
         snn::compute_constants(spec->model, c);
@@ -495,9 +498,32 @@ int snn_export_network(const snn_spec *spec, int64_t *row_ptr, int32_t *post, in
         for (int64_t i = 0; i < hn.n; ++i) {
             const int64_t a = hn.row_ptr[i];
             const int64_t len = hn.out_degree[i];
-            if (post) std::memcpy(post + k, hn.tgt.data() + a, sizeof(int32_t) * len);
-            if (w_fx) std::memcpy(w_fx + k, hn.w.data() + a, sizeof(int32_t) * len);
-            if (delay) std::memcpy(delay + k, hn.d.data() + a, len);
+            if (fmt == SNN_RECORD_PLAIN9) {
+                if (post) std::memcpy(post + k, hn.tgt.data() + a, sizeof(int32_t) * len);
+                if (w_fx) std::memcpy(w_fx + k, hn.w.data() + a, sizeof(int32_t) * len);
+                if (delay) std::memcpy(delay + k, hn.d.data() + a, len);
+            } else {
+                // packed records: the fields of each word and the weight the kernels read back
+                const int src = hn.pop_id[i];
+                for (int64_t j = 0; j < len; ++j) {
+                    const uint32_t word = hn.word[a + j];
+                    if (post) post[k + j] = static_cast<int32_t>(word & snn::kWordTargetMask);
+                    if (delay) delay[k + j] = static_cast<uint8_t>((word >> snn::kWordDelayShift) & 63u);
+                    if (!w_fx) continue;
+                    if (fmt == SNN_RECORD_PACKED_I8) {
+                        const int tgt = static_cast<int>((word >> snn::kWordPopShift) & 7u);
+                        const int8_t code = static_cast<int8_t>(hn.wbytes[a + j]);
+                        w_fx[k + j] = hn.i8_base[src][tgt] + static_cast<int32_t>(code) * hn.i8_step[src][tgt];
+                    } else {
+                        uint16_t h;
+                        std::memcpy(&h, &hn.wbytes[2 * (a + j)], 2);
+                        const uint32_t bits = static_cast<uint32_t>(h) << 16;
+                        float f;
+                        std::memcpy(&f, &bits, 4);
+                        w_fx[k + j] = static_cast<int32_t>(std::lrintf(f * 4096.0f));  // nearest, ties to even
+                    }
+                }
+            }
             k += len;
             if (row_ptr) row_ptr[i + 1] = k;
         }

@@ -85,9 +85,24 @@ def test_export_of_a_batch_places_each_circuit_alone(model):
         base = nxt
 
 
+@pytest.mark.parametrize("fmt", [snn.RECORD_PACKED_I8, snn.RECORD_PACKED_BF16])
+def test_export_of_packed_records_reads_back_the_oracles_quantised_weights(model, fmt):
+    """Packed records (Z18): targets and delays decode from the packed words unchanged, and
+    the weight the kernels read back equals the oracle's quantiser applied to the oracle's
+    network (int8: per population pair base + code * step; bf16: the round-to-nearest-even
+    bfloat16 current read back as rint(f * 4096))."""
+    onet = oracle.build_network(model, 100, 100, 1)
+    if fmt == snn.RECORD_PACKED_I8:
+        wq = oracle.quantize_i8(onet)[0]
+    else:
+        wq = oracle.quantize_bf16(onet.w_fx)
+    net = snn.snn_export_network(snn._Spec(model, 100, 100, 1, record_format=fmt).spec)
+    _assert_same_network(net, oracle.with_weights(onet, wq))
+
+
 def test_export_refuses_other_formats_and_null(model):
     lib = snn.load()
-    spec = snn._Spec(model, 20, 20, 1, record_format=snn.RECORD_PACKED_BF16).spec
+    spec = snn._Spec(model, 20, 20, 1, record_format=snn.RECORD_BLOCKED6).spec
     assert lib.snn_export_network(C.byref(spec), None, None, None, None, None) == _abi.SNN_EINVAL
     assert lib.snn_export_network(None, None, None, None, None, None) == _abi.SNN_EINVAL
     # all outputs optional
