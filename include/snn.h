@@ -247,8 +247,8 @@ typedef struct snn_info {
     int32_t record_format;         /* SNN_RECORD_* */
     int32_t bytes_per_synapse;     /* device bytes of one synapse record */
     int32_t n_circuits;            /* 1, or the batch size */
-    int32_t schedule_ctas;         /* CTAs of the step (pipelined) or delivery (graph) kernel */
-    int32_t schedule_delivery_warps; /* pipelined engine: delivery warps per CTA */
+    int32_t schedule_ctas;         /* CTAs of the step (pipelined, persistent) or delivery (graph) kernel */
+    int32_t schedule_delivery_warps; /* pipelined and persistent engines: delivery warps per CTA */
     int32_t target_blocks;         /* SNN_RECORD_BLOCKED6: number of target blocks (else 0) */
     int32_t i8_base[SNN_MAX_POPS][SNN_MAX_POPS];  /* SNN_RECORD_PACKED_I8 read-back tables [source][target] */
     int32_t i8_step[SNN_MAX_POPS][SNN_MAX_POPS];
@@ -266,7 +266,8 @@ int snn_query_sizes(const snn_spec *spec, snn_sizes *out);
  * every population pair drawn with replacement, §2.2; rows grouped by sender and
  * sorted by delay, the indexed store of §3.5), uploads it into the caller's device
  * arena on `cuda_stream`, initialises U from the u_init Gaussians, I = R = 0, the
- * ring to zero, and captures the step loop into a CUDA graph.  Returns when the
+ * ring to zero, and captures the step loop into a CUDA graph (graph and pipelined
+ * engines; the persistent engine launches its steps directly).  Returns when the
  * upload is complete.  On success *out owns host-side state; free it with
  * snn_destroy.  Errors: SNN_EINVAL (spec), SNN_ENOMEM (host memory, or arena_bytes
  * below snn_query_sizes' figure), SNN_ECUDA. */
