@@ -105,7 +105,7 @@ def lib():
         L.or_pair_count.restype = C.c_int64
         L.or_total_synapses.argtypes = [P(OrModel), C.c_int32, C.c_int32]
         L.or_total_synapses.restype = C.c_int64
-        L.or_build.argtypes = [P(OrModel), C.c_int32, C.c_int32, C.c_uint64, vp, vp, vp, vp]
+        L.or_build.argtypes = [P(OrModel), C.c_int32, C.c_int32, C.c_uint64, vp, vp, vp, vp, vp]
         L.or_build.restype = C.c_int
         L.or_initial_u.argtypes = [P(OrModel), C.c_int32, C.c_uint64, vp]
         L.or_poisson_table.argtypes = [P(OrModel), C.c_int32, vp]
@@ -120,7 +120,7 @@ def lib():
         L.or_run.restype = C.c_int
         L.or_quantize_i8.argtypes = [C.c_int32, vp, C.c_int64, vp, vp, vp, vp, vp, vp]
         L.or_quantize_bf16.argtypes = [C.c_int64, vp, vp]
-        L.or_run_f64.argtypes = L.or_run.argtypes
+        L.or_run_f64.argtypes = L.or_run.argtypes  # weights double[S] in pA, ring double[DMAX*N]
         L.or_run_f64.restype = C.c_int
         _lib = L
     return _lib
@@ -222,9 +222,12 @@ class Network:
     w_fx: np.ndarray
     delay: np.ndarray
     u0: np.ndarray
+    w_pA: Optional[np.ndarray] = None  # currents in pA before rounding to 2^-12 pA (FP64 loop)
 
 
-def build_network(m, scale_n: int, scale_k: int, seed: int) -> Network:
+def build_network(m, scale_n: int, scale_k: int, seed: int, with_pA: bool = False) -> Network:
+    """with_pA also keeps every synapse's current in pA before its rounding to 2^-12 pA
+    (the FP64 loop's weights)."""
     off = pop_offsets(m, scale_n)
     n = int(off[-1])
     s = total_synapses(m, scale_n, scale_k)
@@ -232,14 +235,18 @@ def build_network(m, scale_n: int, scale_k: int, seed: int) -> Network:
     post = np.zeros(max(s, 1), np.int32)
     w = np.zeros(max(s, 1), np.int32)
     d = np.zeros(max(s, 1), np.uint8)
-    rc = lib().or_build(C.byref(_model(m)), scale_n, scale_k, seed, _p(row_ptr), _p(post), _p(w), _p(d))
+    w_pA = np.zeros(max(s, 1), np.float64) if with_pA else None
+    rc = lib().or_build(C.byref(_model(m)), scale_n, scale_k, seed, _p(row_ptr), _p(post), _p(w), _p(d),
+                        _p(w_pA) if with_pA else None)
     if rc != 0:
         raise MemoryError("oracle network build failed")
-    return Network(n, off, row_ptr, post[:s], w[:s], d[:s], initial_u(m, scale_n, seed))
+    return Network(n, off, row_ptr, post[:s], w[:s], d[:s], initial_u(m, scale_n, seed),
+                   w_pA[:s] if with_pA else None)
 
 
-def network_from_edges(n: int, pre, post, w_fx, delay, u0, pop_off=None) -> Network:
-    """A hand-made network (tests): edges grouped by sender, order kept within a row."""
+def network_from_edges(n: int, pre, post, w_fx, delay, u0, pop_off=None, w_pA=None) -> Network:
+    """A hand-made network (tests): edges grouped by sender, order kept within a row;
+    w_pA optionally gives the FP64 loop's weights in pA (else w_fx / 4096)."""
     pre = np.asarray(pre, np.int64)
     order = np.argsort(pre, kind="stable")
     counts = np.bincount(pre, minlength=n) if len(pre) else np.zeros(n, np.int64)
@@ -250,7 +257,8 @@ def network_from_edges(n: int, pre, post, w_fx, delay, u0, pop_off=None) -> Netw
                    np.ascontiguousarray(np.asarray(post, np.int32)[order]),
                    np.ascontiguousarray(np.asarray(w_fx, np.int32)[order]),
                    np.ascontiguousarray(np.asarray(delay, np.uint8)[order]),
-                   np.ascontiguousarray(np.asarray(u0, np.float32)))
+                   np.ascontiguousarray(np.asarray(u0, np.float32)),
+                   None if w_pA is None else np.ascontiguousarray(np.asarray(w_pA, np.float64)[order]))
 
 
 def quantize_i8(net: "Network", n_pops: int = 8):
@@ -274,14 +282,15 @@ def quantize_bf16(w_fx: np.ndarray) -> np.ndarray:
 
 def with_weights(net: "Network", w_fx: np.ndarray) -> "Network":
     return Network(net.n, net.pop_off, net.row_ptr, net.post, np.ascontiguousarray(w_fx, np.int32), net.delay,
-                   net.u0)
+                   net.u0, net.w_pA)
 
 
 class Sim:
     """State of one circuit under the oracle: U, I (FP32), R (steps), exact ring."""
 
     def __init__(self, m, net: Network, seed: int, fp64: bool = False):
-        """fp64=True runs the same loop with FP64 neuron state and propagators."""
+        """fp64=True runs the same loop in FP64: neuron state, propagators, the weights in
+        pA before rounding (net.w_pA, else w_fx / 4096) and a double ring."""
         self.m, self.net, self.seed = m, net, int(seed)
         self._cm = _model(m)
         self.fp64 = fp64
@@ -290,7 +299,9 @@ class Sim:
         self.U = net.u0.astype(dt)
         self.I = np.zeros(n, dt)
         self.R = np.zeros(n, np.int32)
-        self.W = np.zeros(D_MAX * n, np.int64)
+        self.W = np.zeros(D_MAX * n, np.float64 if fp64 else np.int64)
+        if fp64:
+            self.w_pA = net.w_pA if net.w_pA is not None else net.w_fx.astype(np.float64) / 4096.0
         self.t = 0
         self.status = 0
 
@@ -304,6 +315,8 @@ class Sim:
         net = self.net
         post = net.post if len(net.post) else np.zeros(1, np.int32)
         w = net.w_fx if len(net.w_fx) else np.zeros(1, np.int32)
+        if self.fp64:
+            w = self.w_pA if len(self.w_pA) else np.zeros(1, np.float64)
         d = net.delay if len(net.delay) else np.zeros(1, np.uint8)
         run = lib().or_run_f64 if self.fp64 else lib().or_run
         rc = run(C.byref(self._cm), self.seed, net.n, _p(net.pop_off), _p(net.row_ptr),

@@ -204,12 +204,13 @@ static void or_weight_law(const or_model *m, int a, int b, double *mu, double *s
 /* 0): word 0 picks the source neuron, word 1 the target, words 2-3 give a      */
 /* Box-Muller pair whose cosine branch sets the amplitude and sine branch the   */
 /* delay.  Amplitude in mV is mapped to current with w_f, clipped at zero on    */
-/* the wrong side of its sign, and stored as an integer count of 2^-12 pA.      */
+/* the wrong side of its sign, and stored as an integer count of 2^-12 pA       */
+/* (w_pA, when not NULL, receives the current before that rounding).           */
 /* Delay in ms is rounded to whole steps and clipped to [1, DMAX-1].            */
 /* ------------------------------------------------------------------------ */
 static void or_draw_synapse(const or_model *m, uint64_t seed, double w_f, const int64_t *off,
                             const int64_t *nb, int a, int b, int64_t k,
-                            int32_t *pre, int32_t *post, int32_t *w_fx, uint8_t *dly)
+                            int32_t *pre, int32_t *post, int32_t *w_fx, double *w_pA, uint8_t *dly)
 {
     uint64_t ctr[4] = {(uint64_t)k, (uint64_t)a, (uint64_t)b, 0};
     uint64_t key[2] = {seed, OR_TAG_CONN};
@@ -224,7 +225,9 @@ static void or_draw_synapse(const or_model *m, uint64_t seed, double w_f, const 
     double w_mV = mu + sd * zw;
     if (mu >= 0.0 && w_mV < 0.0) w_mV = 0.0;
     if (mu < 0.0 && w_mV > 0.0) w_mV = 0.0;
-    *w_fx = (int32_t)llround(w_mV * w_f * 4096.0);
+    const double amp_pA = w_mV * w_f;
+    *w_fx = (int32_t)llround(amp_pA * 4096.0);
+    if (w_pA) *w_pA = amp_pA;
     double d_ms = m->d_mean[a] + m->d_sd[a] * zd;
     long long ds = llround(d_ms / m->dt_ms);
     if (ds < 1) ds = 1;
@@ -235,10 +238,12 @@ static void or_draw_synapse(const or_model *m, uint64_t seed, double w_f, const 
 /* Build the network: every synapse of every pair, then grouped by source neuron
  * (a stable counting sort: within a row, synapses keep generation order) so that
  * "syns_from(i)" of Listing push is the contiguous slice row_ptr[i]..row_ptr[i+1]
- * (§3.5).  Outputs are caller-allocated: row_ptr[N+1], post/w_fx/dly[S].
+ * (§3.5).  Outputs are caller-allocated: row_ptr[N+1], post/w_fx/dly[S], and, when
+ * w_pA is not NULL, w_pA[S]: the same synapses' currents in pA before rounding to
+ * 2^-12 pA (the weights of the FP64 reference loop).
  * Returns 0, or -1 on allocation failure. */
 int or_build(const or_model *m, int32_t scale_n, int32_t scale_k, uint64_t seed,
-             int64_t *row_ptr, int32_t *post, int32_t *w_fx, uint8_t *dly)
+             int64_t *row_ptr, int32_t *post, int32_t *w_fx, uint8_t *dly, double *w_pA)
 {
     int64_t nb[OR_MAX_POPS], off[OR_MAX_POPS + 1];
     or_pop_sizes(m, scale_n, nb);
@@ -253,8 +258,9 @@ int or_build(const or_model *m, int32_t scale_n, int32_t scale_k, uint64_t seed,
     int32_t *g_post = (int32_t *)malloc((size_t)(S > 0 ? S : 1) * sizeof(int32_t));
     int32_t *g_w = (int32_t *)malloc((size_t)(S > 0 ? S : 1) * sizeof(int32_t));
     uint8_t *g_d = (uint8_t *)malloc((size_t)(S > 0 ? S : 1));
-    if (!g_pre || !g_post || !g_w || !g_d) {
-        free(g_pre); free(g_post); free(g_w); free(g_d);
+    double *g_a = w_pA ? (double *)malloc((size_t)(S > 0 ? S : 1) * sizeof(double)) : NULL;
+    if (!g_pre || !g_post || !g_w || !g_d || (w_pA && !g_a)) {
+        free(g_pre); free(g_post); free(g_w); free(g_d); free(g_a);
         return -1;
     }
     int64_t s = 0;
@@ -262,7 +268,8 @@ int or_build(const or_model *m, int32_t scale_n, int32_t scale_k, uint64_t seed,
         for (int b = 0; b < m->n_pops; ++b) {
             const int64_t K = or_pair_count(m, scale_n, scale_k, b, a);
             for (int64_t k = 0; k < K; ++k, ++s)
-                or_draw_synapse(m, seed, c[0], off, nb, a, b, k, &g_pre[s], &g_post[s], &g_w[s], &g_d[s]);
+                or_draw_synapse(m, seed, c[0], off, nb, a, b, k, &g_pre[s], &g_post[s], &g_w[s],
+                                g_a ? &g_a[s] : NULL, &g_d[s]);
         }
     /* counting sort by source neuron */
     for (int64_t i = 0; i <= N; ++i) row_ptr[i] = 0;
@@ -270,7 +277,7 @@ int or_build(const or_model *m, int32_t scale_n, int32_t scale_k, uint64_t seed,
     for (int64_t i = 0; i < N; ++i) row_ptr[i + 1] += row_ptr[i];
     int64_t *fill = (int64_t *)malloc((size_t)(N > 0 ? N : 1) * sizeof(int64_t));
     if (!fill) {
-        free(g_pre); free(g_post); free(g_w); free(g_d);
+        free(g_pre); free(g_post); free(g_w); free(g_d); free(g_a);
         return -1;
     }
     for (int64_t i = 0; i < N; ++i) fill[i] = row_ptr[i];
@@ -279,9 +286,10 @@ int or_build(const or_model *m, int32_t scale_n, int32_t scale_k, uint64_t seed,
         post[dst] = g_post[k];
         w_fx[dst] = g_w[k];
         dly[dst] = g_d[k];
+        if (g_a) w_pA[dst] = g_a[k];
     }
     free(fill);
-    free(g_pre); free(g_post); free(g_w); free(g_d);
+    free(g_pre); free(g_post); free(g_w); free(g_d); free(g_a);
     return 0;
 }
 
@@ -573,12 +581,14 @@ void or_quantize_bf16(int64_t S, const int32_t *w_fx, int32_t *w_out)
     }
 }
 
-/* The step loop of or_run with FP64 neuron state and FP64 propagators (the
- * reference for the accuracy of the FP32 and compressed forms).  Synaptic and
- * thalamic input are the same exact integers (2^-12 pA) as in or_run. */
+/* The step loop of or_run in FP64 throughout (the reference for the accuracy of the
+ * FP32 and compressed forms): FP64 neuron state and propagators, synaptic weights
+ * w_pA in pA as drawn (before any rounding to 2^-12 pA), the thalamic amplitude
+ * w_f w_ext in pA, and a double ring W[DMAX*N] that sums the currents in pA.
+ * The spike order, delays and Poisson draws are those of or_run. */
 int or_run_f64(const or_model *m, uint64_t seed, int64_t N, const int64_t *pop_off, const int64_t *row_ptr,
-               const int32_t *post, const int32_t *w_fx, const uint8_t *dly, double *U, double *I, int32_t *R,
-               int64_t *W, int64_t t0, int64_t n_steps, int32_t *rast_t, int32_t *rast_i, int64_t rast_cap,
+               const int32_t *post, const double *w_pA, const uint8_t *dly, double *U, double *I, int32_t *R,
+               double *W, int64_t t0, int64_t n_steps, int32_t *rast_t, int32_t *rast_i, int64_t rast_cap,
                int64_t *n_rast)
 {
     double c[6];
@@ -589,7 +599,7 @@ int or_run_f64(const or_model *m, uint64_t seed, int64_t N, const int64_t *pop_o
     int32_t k2[2];
     or_step_constants(m, f, k2);
     const int32_t t_ref = k2[0];
-    const int64_t w_ext = k2[1];
+    const double w_ext = c[0] * m->w_ext_mV;
     uint64_t C[OR_MAX_POPS][OR_PKMAX];
     for (int b = 0; b < m->n_pops; ++b) or_poisson_table(m, b, C[b]);
     int32_t *queue = (int32_t *)malloc((size_t)(N > 0 ? N : 1) * sizeof(int32_t));
@@ -603,8 +613,8 @@ int or_run_f64(const or_model *m, uint64_t seed, int64_t N, const int64_t *pop_o
         for (int64_t i = 0; i < N; ++i) {
             while (i >= pop_off[b + 1]) ++b;
             const int32_t T = or_poisson_count(or_poisson_uniform(seed, t, i), C[b]);
-            const int64_t in = W[slot * N + i] + (int64_t)T * w_ext;
-            W[slot * N + i] = 0;
+            const double in = W[slot * N + i] + (double)T * w_ext;
+            W[slot * N + i] = 0.0;
             int spike = 0;
             if (R[i] == 0) {
                 double x = p22 * U[i] + p21 * I[i];
@@ -618,7 +628,7 @@ int or_run_f64(const or_model *m, uint64_t seed, int64_t N, const int64_t *pop_o
                 U[i] = u_reset;
                 R[i] -= 1;
             }
-            I[i] = p11 * I[i] + (double)in / 4096.0;
+            I[i] = p11 * I[i] + in;
             if (spike) {
                 queue[nq++] = (int32_t)i;
                 if (nr < rast_cap) {
@@ -632,7 +642,7 @@ int or_run_f64(const or_model *m, uint64_t seed, int64_t N, const int64_t *pop_o
         }
         for (int64_t q = 0; q < nq; ++q) {
             const int64_t s = queue[q];
-            for (int64_t e = row_ptr[s]; e < row_ptr[s + 1]; ++e) W[((t + dly[e]) % OR_DMAX) * N + post[e]] += w_fx[e];
+            for (int64_t e = row_ptr[s]; e < row_ptr[s + 1]; ++e) W[((t + dly[e]) % OR_DMAX) * N + post[e]] += w_pA[e];
         }
     }
     *n_rast = nr;

@@ -556,3 +556,53 @@ def test_fp64_loop_psc_and_psp():
         U.append(sim.U[1])
     k = np.arange(1, 61)
     np.testing.assert_allclose(U, c["gamma"] * (w / 4096.0) * (c["p22"] ** k - c["p11"] ** k), rtol=1e-12)
+
+
+def test_fp64_loop_uses_unrounded_weights_and_currents():
+    """FP64 loop: a weight given in pA that 2^-12 pA cannot represent arrives unrounded,
+    simultaneous arrivals add in pA, and the thalamic input of a step is T w_f w_ext in
+    pA with T the Poisson count of that neuron and step."""
+    m0 = workload.microcircuit_model().replace(k_ext=[0.0] * 8)
+    w_pA = [87.808521234567, -351.23399991]
+    net = oracle.network_from_edges(3, pre=[0, 1], post=[2, 2], w_fx=[359_664, -1_438_654], delay=[2, 2],
+                                    u0=[20.0, 20.0, 0.0], w_pA=w_pA)
+    sim = oracle.Sim(m0, net, seed=1, fp64=True)
+    sim.run(2)
+    assert sim.I[2] == 0.0
+    sim.run(1)
+    assert sim.I[2] == w_pA[0] + w_pA[1]
+    assert sim.I[2] != (359_664 - 1_438_654) / 4096.0
+    m = workload.microcircuit_model()
+    c = oracle.constants(m)
+    one = oracle.network_from_edges(1, pre=[], post=[], w_fx=[], delay=[], u0=[0.0],
+                                    pop_off=[0, 1, 1, 1, 1, 1, 1, 1, 1])
+    sim = oracle.Sim(m, one, seed=5, fp64=True)
+    Is = []
+    for _ in range(40):
+        sim.run(1)
+        Is.append(sim.I[0])
+    T = [int(oracle.poisson_draws(m, 5, 0, t, 0, 1)[0]) for t in range(40)]
+    w_ext = c["w_f"] * m.w_ext_mV
+    exp, cur = [], 0.0
+    for t in range(40):
+        cur = c["p11"] * cur + (0.0 + T[t] * w_ext)
+        exp.append(cur)
+    assert sum(T) > 10
+    assert Is == exp
+
+
+def test_build_keeps_unrounded_currents():
+    """The FP64 loop's weights are the drawn currents before rounding: rounding them to
+    2^-12 pA gives the integer weights bit for bit, excitatory currents are >= 0 and
+    inhibitory ones <= 0, and their scale is pA (the mean excitatory current is
+    w_f * 0.15 mV, about 87.8 pA)."""
+    m = workload.microcircuit_model()
+    net = oracle.build_network(m, 50, 50, 3, with_pA=True)
+    assert np.array_equal(np.rint(net.w_pA * 4096.0).astype(np.int64), net.w_fx.astype(np.int64))
+    pre = np.repeat(np.arange(net.n), np.diff(net.row_ptr))
+    pops = np.searchsorted(net.pop_off, pre, side="right") - 1
+    exc = pops % 2 == 0
+    assert np.all(net.w_pA[exc] >= 0) and np.all(net.w_pA[~exc] <= 0)
+    c = oracle.constants(m)
+    plain = exc & ~((pops == 2) & (np.searchsorted(net.pop_off, net.post, side="right") - 1 == 0))
+    assert abs(net.w_pA[plain].mean() / (c["w_f"] * 0.15) - 1.0) < 0.01
