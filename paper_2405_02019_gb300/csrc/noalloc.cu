@@ -16,7 +16,6 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
-#include <mutex>
 
 #include "../../include/snn.h"
 #include "philox.cuh"
@@ -178,28 +177,23 @@ __global__ void __launch_bounds__(kDeliverWarpsThreads) k_static_deliver(const S
     }
 }
 
-std::mutex g_symbol_mutex;
-void *g_symbol_ptr[64] = {nullptr};
-
 int static_fail(int code, const char *msg)
 {
     snn::set_last_error(msg);
     return code;
 }
 
-// Device address of g_static_scratch on `device` (which must be current), looked up
-// once per device.
-int scratch_address(int device, uint32_t **out)
+// Device address of g_static_scratch on the current device.  In host code the array's
+// name stands for a host-side shadow, not a device address, so the address is looked up
+// here, with the device current, on every call: the lookup is cheap once the library's
+// device code is loaded, and a fresh address cannot go stale when the caller resets the
+// device between calls.
+int scratch_address(uint32_t **out)
 {
-    if (device < 0 || device >= 64) return static_fail(SNN_EINVAL, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_symbol_mutex);
-    if (!g_symbol_ptr[device]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p) return static_fail(SNN_ECUDA, "cudaGetSymbolAddress(g_static_scratch) failed");
-        g_symbol_ptr[device] = p;
-    }
-    *out = static_cast<uint32_t *>(g_symbol_ptr[device]);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) return static_fail(SNN_ECUDA, "cudaGetSymbolAddress(g_static_scratch) failed");
+    *out = static_cast<uint32_t *>(p);
     return SNN_OK;
 }
 
@@ -214,6 +208,9 @@ extern "C" int snn_step_static(const snn_net *net, const snn_static_io *io, uint
     if (t < 0) return static_fail(SNN_EINVAL, "snn_step_static: negative step index");
     snn_info info;
     if (snn_get_info(net, &info) != SNN_OK) return static_fail(SNN_EINVAL, "snn_step_static: bad network handle");
+    if (info.device_error != 0)
+        return static_fail(SNN_ESTATE, "snn_step_static: a device error of this network is pending");
+    if (info.n_neurons < 1) return static_fail(SNN_EINVAL, "snn_step_static: network without neurons");
     if (info.record_format != SNN_RECORD_PLAIN9)
         return static_fail(SNN_ENOTSUP, "snn_step_static: only plain synapse records are supported");
     if (info.n_circuits != 1) return static_fail(SNN_ENOTSUP, "snn_step_static: batched networks are not supported");
@@ -242,7 +239,9 @@ extern "C" int snn_step_static(const snn_net *net, const snn_static_io *io, uint
     StaticArgs a;
     std::memset(&a, 0, sizeof(a));
     uint32_t *scratch = nullptr;
-    int rc = scratch_address(dev, &scratch);
+    int rc = scratch_address(&scratch);
+    if (rc == SNN_OK && cudaPeekAtLastError() != cudaSuccess)
+        rc = static_fail(SNN_ECUDA, "snn_step_static: a CUDA error from earlier work is pending (not cleared)");
     if (rc == SNN_OK) {
         a.row_ptr = io->row_ptr;
         a.syn_tgt = io->syn_tgt;
@@ -275,12 +274,17 @@ extern "C" int snn_step_static(const snn_net *net, const snn_static_io *io, uint
         cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(uint32_t) * kStaticCtlWords, st);
         const int64_t quads = (info.n_neurons + 3) / 4;
         const int ugrid = static_cast<int>((quads + kQuadThreads - 1) / kQuadThreads);
-        if (e == cudaSuccess) {
+        if (e != cudaSuccess) {
+            rc = static_fail(SNN_ECUDA, "snn_step_static: clearing the spike counter failed");
+        } else {
             k_static_update<<<ugrid, kQuadThreads, 0, st>>>(a);
-            k_static_deliver<<<info.deliver_blocks > 0 ? info.deliver_blocks : 1, kDeliverWarpsThreads, 0, st>>>(a);
             e = cudaGetLastError();
+            if (e == cudaSuccess) {
+                k_static_deliver<<<info.deliver_blocks > 0 ? info.deliver_blocks : 1, kDeliverWarpsThreads, 0, st>>>(a);
+                e = cudaGetLastError();
+            }
+            if (e != cudaSuccess) rc = static_fail(SNN_ECUDA, "snn_step_static: launch failed");
         }
-        if (e != cudaSuccess) rc = static_fail(SNN_ECUDA, "snn_step_static: launch failed");
     }
     if (dev != prev) cudaSetDevice(prev);
     return rc;

@@ -116,3 +116,40 @@ def test_too_many_neurons_rejected():
     assert rc == _abi.SNN_EINVAL
     assert b"SNN_STATIC_MAX_NEURONS" in lib.snn_last_error()
     net.close()
+
+
+def test_hundred_static_steps_with_every_delay_match_step_n():
+    """100 consecutive calls on a small network whose delays take every value 1..63:
+    each call's spikes (sorted) and, at the end, U, I, R and the whole 64-row ring equal
+    snn_step_n's; the fixed spike counter is cleared by every call, and contributions
+    wrap around the ring."""
+    m = workload.microcircuit_model()
+    rng = np.random.default_rng(21)
+    n, S = 600, 30000
+    custom = dict(pre=rng.integers(0, n, S), post=rng.integers(0, n, S),
+                  w_fx=rng.integers(-1_500_000, 2_500_000, S), delay=np.tile(np.arange(1, 64), S // 63 + 1)[:S],
+                  u0=rng.uniform(0, 16, n).astype(np.float32), pop_offsets=[0] + [n] * 8)
+    seed = 7
+    ref = snn.Network(m, custom=custom, seed=seed, steps_per_graph=64)
+    dut = snn.Network(m, custom=custom, seed=seed, steps_per_graph=64)
+    lib = snn.load()
+    spikes = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    n_spikes = torch.zeros(1, dtype=torch.int32, device="cuda")
+    io = _io_for(dut, spikes, n_spikes)
+    stream = torch.cuda.current_stream().cuda_stream
+    total = 0
+    for t in range(100):
+        ref.step(1)
+        r_t, r_i = ref.read_spikes()
+        rc = lib.snn_step_static(C.c_void_p(dut._handle), C.byref(io), seed, t, C.c_void_p(stream))
+        assert rc == 0, lib.snn_last_error()
+        torch.cuda.synchronize()
+        k = int(n_spikes.item())
+        assert np.array_equal(np.sort(spikes[:k].cpu().numpy()), r_i), t
+        total += k
+    assert total > 100
+    a, b = _snapshot(ref), _snapshot(dut)
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
+    ref.close()
+    dut.close()
