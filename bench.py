@@ -312,7 +312,11 @@ def run_gpu(args):
     tps = args.ticks_per_step
     t0 = time.perf_counter()
     engine = {"default": snn.ENGINE_DEFAULT, "graph": snn.ENGINE_GRAPH, "persistent": snn.ENGINE_PERSISTENT,
-              "pipelined": snn.ENGINE_PIPELINED}[args.engine]
+              "pipelined": snn.ENGINE_PIPELINED, "resident": snn.ENGINE_RESIDENT}[args.engine]
+    # the compressed forms, batches and the 4x circuit run where the resident engine does not
+    others = snn.ENGINE_DEFAULT if engine == snn.ENGINE_RESIDENT else engine
+    engine_name = {snn.ENGINE_GRAPH: "graph", snn.ENGINE_PERSISTENT: "persistent", snn.ENGINE_PIPELINED: "pipelined",
+                   snn.ENGINE_RESIDENT: "resident"}
     net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, seed, steps_per_graph=tps,
                       raster_capacity=1 << 25, device=dev, engine=engine)
     build_s = time.perf_counter() - t0
@@ -381,7 +385,7 @@ def run_gpu(args):
     upd_bytes = UPDATE_BYTES_PER_NEURON * n
     dlv_bytes = (EVENT_BYTES * pe + SPIKE_BYTES * pspk) / prof_ticks
     upd_gbs = upd_bytes / (ms_u / prof_ticks * 1e-3) / 1e9
-    dlv_gbs = dlv_bytes / (ms_d / prof_ticks * 1e-3) / 1e9
+    dlv_gbs = dlv_bytes / (ms_d / prof_ticks * 1e-3) / 1e9 if ms_d > 0 else 0.0  # resident: one launch, both phases
     peak, peak_kind = _peaks()
     kernels = {
         "k_update": {"avg_us": ms_u / prof_ticks * 1e3, "bytes_per_launch": upd_bytes, "gbs": upd_gbs,
@@ -403,16 +407,22 @@ def run_gpu(args):
                               "note": "avg_us over the timed graph replays; isolated_avg_us brackets single "
                                       "launches with CUDA events (launch latency included)"}}
         dom = "k_step"
-    elif info.engine == snn.ENGINE_PERSISTENT:
+    elif info.engine in (snn.ENGINE_PERSISTENT, snn.ENGINE_RESIDENT):
         # one cooperative launch per bench step: all of its steps' algorithmic bytes over its duration
         per_launch = tps * (upd_bytes + (EVENT_BYTES * events + SPIKE_BYTES * spikes) / (args.steps * tps))
-        kernels = {"k_persistent": {"avg_us": secs_max * 1e6 / args.steps, "bytes_per_launch": per_launch,
-                                    "gbs": per_launch / (secs_max / args.steps) / 1e9, "share": 1.0,
-                                    "steps_per_launch": tps, "us_per_step": secs_max * 1e6 / (args.steps * tps),
-                                    "isolated_k_step_avg_us": ms_u / prof_ticks * 1e3,
-                                    "note": "isolated_k_step_avg_us: the same step as one k_step launch, "
-                                            "bracketed with CUDA events (launch latency included)"}}
-        dom = "k_persistent"
+        dom = "k_persistent" if info.engine == snn.ENGINE_PERSISTENT else "k_resident"
+        kernels = {dom: {"avg_us": secs_max * 1e6 / args.steps, "bytes_per_launch": per_launch,
+                         "gbs": per_launch / (secs_max / args.steps) / 1e9, "share": 1.0,
+                         "steps_per_launch": tps, "us_per_step": secs_max * 1e6 / (args.steps * tps),
+                         "events_per_launch": events / args.steps, "spikes_per_launch": spikes / args.steps}}
+        if info.engine == snn.ENGINE_PERSISTENT:
+            kernels[dom]["isolated_k_step_avg_us"] = ms_u / prof_ticks * 1e3
+            kernels[dom]["note"] = ("isolated_k_step_avg_us: the same step as one k_step launch, bracketed with "
+                                    "CUDA events (launch latency included)")
+        else:
+            kernels[dom]["note"] = ("one cooperative launch per bench step (1,024 steps); its algorithmic bytes "
+                                    "count the ring row and neuron state per neuron-step although the kernel keeps "
+                                    "both on chip; its DRAM traffic is the synapse segments it reads")
     else:
         dom = "k_update" if ms_u >= ms_d else "k_deliver"
     traffic = _recorded_traffic(dom)
@@ -457,7 +467,7 @@ def run_gpu(args):
                        ("blocked6", snn.RECORD_BLOCKED6), ("blocked4", snn.RECORD_BLOCKED4)):
         if fname not in args.forms:
             continue
-        feng = snn.ENGINE_DEFAULT if fmt in blocked_formats else engine
+        feng = snn.ENGINE_DEFAULT if fmt in blocked_formats else others
         fnet = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, seed, steps_per_graph=tps,
                            raster_capacity=1 << 25, device=dev, engine=feng, record_format=fmt)
         fnet.step(args.warmup * tps)
@@ -513,8 +523,7 @@ def run_gpu(args):
                            "plain_equivalent_gbs": (EVENT_BYTES * ev_avg + SPIKE_BYTES * nsp) / (ms_avg * 1e-3) / 1e9})
             fsat.append(pt)
         forms[fname] = {"bytes_per_synapse": finfo.bytes_per_synapse, "value": fev / fsecs,
-                        "engine": {snn.ENGINE_GRAPH: "graph", snn.ENGINE_PERSISTENT: "persistent",
-                                   snn.ENGINE_PIPELINED: "pipelined"}[finfo.engine],
+                        "engine": engine_name[finfo.engine],
                         "unit": "synaptic events/s", "rtf": fsecs / (args.form_steps * tps * model.dt_ms * 1e-3),
                         "steps": args.form_steps * tps, "delivery_saturating": fsat,
                         "note": "raster bit-exact with the oracle on the read-back weights; statistics vs FP64 "
@@ -529,13 +538,13 @@ def run_gpu(args):
         --profile-region equal to `region`, the timed region is bracketed by
         cudaProfilerStart/Stop (for ncu --profile-from-start off)."""
         t0 = time.perf_counter()
-        weng = engine if weng is None else weng
+        weng = others if weng is None else weng
         if circuits is not None:
             xnet = snn.Network(model, circuits=circuits, steps_per_graph=tps, raster_capacity=1 << 27, device=dev,
                                engine=weng, record_format=fmt)
         else:
             xnet = snn.Network(model, wlx.scale_n_permille, wlx.scale_k_permille, wlx.seed + rank,
-                               steps_per_graph=tps, raster_capacity=1 << 27, device=dev, engine=engine,
+                               steps_per_graph=tps, raster_capacity=1 << 27, device=dev, engine=weng,
                                record_format=fmt)
         build = time.perf_counter() - t0
         tuned = None
@@ -567,8 +576,7 @@ def run_gpu(args):
         xnet.read_spikes()
         xi = xnet.info()
         ev = xi.events_read - x0
-        out = {"workload": label, "engine": {snn.ENGINE_GRAPH: "graph", snn.ENGINE_PERSISTENT: "persistent",
-                                             snn.ENGINE_PIPELINED: "pipelined"}[xi.engine],
+        out = {"workload": label, "engine": engine_name[xi.engine],
                "circuits_per_group": int(xi.circuits_per_group),
                "neurons": int(xi.n_neurons), "synapses": int(xi.n_synapses),
                "circuits": int(xi.n_circuits), "bytes_per_synapse": int(xi.bytes_per_synapse),
@@ -619,8 +627,7 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f32/i32", "data": "synthetic (PD microcircuit sampled from the paper's tables)",
         "config": {"workload": f"{wl.name}: 77,169 neurons, 284,811,022 synapses, dt 0.1 ms, seed {wl.seed}+rank",
                    "ticks_per_step": tps, "bio_seconds": bio_s, "steps_per_graph": info.steps_per_graph,
-                   "engine": {snn.ENGINE_GRAPH: "graph", snn.ENGINE_PERSISTENT: "persistent",
-                              snn.ENGINE_PIPELINED: "pipelined"}[info.engine],
+                   "engine": engine_name[info.engine],
                    "deliver_blocks": info.deliver_blocks, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (2.56 GB synapse store); ring and neuron state are L2-resident by design"},
         "rtf": rtf, "realtime_x": 1.0 / rtf, "spikes_per_tick": spikes / (args.steps * tps),
@@ -636,7 +643,7 @@ def run_gpu(args):
                         "every bench step enqueues 1,024 steps (snn_step_n) and moves the previous bench "
                         "step's raster to host memory while they run (snn_collect_spikes); a final "
                         "snn_read_spikes inside the timed region returns the last one"},
-        "gpu_launches": args.steps * {snn.ENGINE_PERSISTENT: 1, snn.ENGINE_PIPELINED: tps + 1,
+        "gpu_launches": args.steps * {snn.ENGINE_PERSISTENT: 1, snn.ENGINE_RESIDENT: 1, snn.ENGINE_PIPELINED: tps + 1,
                                       snn.ENGINE_GRAPH: 2 * tps + 1}[info.engine],
         "roofline": roofline, "kernels": kernels,
         "compressed_records": forms,
@@ -703,7 +710,7 @@ def main():
     ap.add_argument("--profile-region", choices=["none", "batched", "x4"], default="none",
                     help="bracket that workload's timed region with cudaProfilerStart/Stop")
     ap.add_argument("--form-steps", type=int, default=20)
-    ap.add_argument("--engine", default="default", choices=["default", "graph", "persistent", "pipelined"])
+    ap.add_argument("--engine", default="default", choices=["default", "graph", "persistent", "pipelined", "resident"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

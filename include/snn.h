@@ -133,12 +133,25 @@ typedef struct snn_circuit {
  *       replayed from a CUDA graph;
  *     SNN_ENGINE_PERSISTENT: the pipelined engine's schedule in one cooperative
  *       launch per batch of steps, one bounded grid-wide barrier per step in place
- *       of the kernel boundary.
+ *       of the kernel boundary;
+ *     SNN_ENGINE_RESIDENT: all steps of one snn_step_n call in one cooperative launch
+ *       with one CTA per block of consecutive neurons (at most 1024 neurons per SM):
+ *       the CTA keeps its neurons' U, I, R in registers and their columns of the ring
+ *       in shared memory for the whole launch, and adds the synapses that target its
+ *       block (each row is stored grouped by target block, delay order kept within a
+ *       block, with a table of where each block's segment starts: the indexed store of
+ *       §3.5 split by target) with shared-memory integer atomics; CTAs exchange only
+ *       each step's spike list, through per-CTA mailboxes whose words carry the step
+ *       number.  One circuit, SNN_RECORD_PLAIN9 records.  smem_ring_rows (8, 16, 32 or
+ *       64; 0 = as many as fit) caps the ring rows kept in shared memory; delays of
+ *       that many steps or more then go to the ring in global memory.  Every mailbox
+ *       wait is bounded (2 s) and ends, on timeout, with SNN_ETIMEOUT at the next read.
  */
 #define SNN_ENGINE_DEFAULT 0
 #define SNN_ENGINE_GRAPH 1
 #define SNN_ENGINE_PERSISTENT 2
 #define SNN_ENGINE_PIPELINED 3
+#define SNN_ENGINE_RESIDENT 4
 /*
  * record_format: how synapses are stored on the device (§3.5 stores a target, a
  * delay and an FP32 weight; §5.3 proposes fewer bits per weight):
@@ -187,7 +200,7 @@ typedef struct snn_spec {
     snn_model model;
     const snn_custom_net *custom;
     int32_t n_circuits;
-    int32_t reserved;
+    int32_t smem_ring_rows;
     const snn_circuit *circuits;
 } snn_spec;
 
@@ -215,12 +228,18 @@ typedef struct snn_sizes {
  * 16-byte quads of records and bfloat16 weights), syn_w the int32 weights (BLOCKED6), syn_delay
  * the uint16 table [n_neurons][target_blocks + 1] of each row's block starts relative
  * to its row start, and blocks the int32 block boundaries [target_blocks + 1];
- * rast_neuron, rast_step int32[raster_capacity]. */
+ * rast_neuron, rast_step int32[raster_capacity].  Resident engine: plain records, each row
+ * grouped by target block (delay order kept inside a block), blocks the int32 block
+ * boundaries, block_starts the per-row segment table. */
 typedef struct snn_layout {
     uint64_t ctl, U, I, R, ring, row_ptr, syn_tgt, syn_w, syn_delay, rast_neuron, rast_step, params;
     int64_t n_neurons_padded;
     int64_t n_synapses_padded;
     uint64_t blocks;
+    uint64_t block_starts;  /* resident engine: uint32 [target_blocks][n_neurons], for block b and
+                               row i the start of the row's segment of synapses into block b,
+                               relative to the row (low 16 bits), and its length (high 16 bits);
+                               0 for the other engines */
 } snn_layout;
 
 /* Constants and counters of a built network. */
@@ -243,23 +262,26 @@ typedef struct snn_info {
     int32_t steps_per_graph;
     int32_t deliver_blocks;
     uint32_t device_error;         /* sticky device error bits (1 = raster overflow, 2 = barrier timeout) */
-    int32_t engine;                /* SNN_ENGINE_PIPELINED, SNN_ENGINE_GRAPH or SNN_ENGINE_PERSISTENT */
+    int32_t engine;                /* SNN_ENGINE_PIPELINED, _GRAPH, _PERSISTENT or _RESIDENT */
     int32_t record_format;         /* SNN_RECORD_* */
     int32_t bytes_per_synapse;     /* device bytes of one synapse record */
     int32_t n_circuits;            /* 1, or the batch size */
     int32_t schedule_ctas;         /* CTAs of the step (pipelined, persistent) or delivery (graph) kernel */
     int32_t schedule_delivery_warps; /* pipelined and persistent engines: delivery warps per CTA */
-    int32_t target_blocks;         /* SNN_RECORD_BLOCKED6: number of target blocks (else 0) */
+    int32_t target_blocks;         /* blocked records or the resident engine: number of target blocks (else 0) */
     int32_t i8_base[SNN_MAX_POPS][SNN_MAX_POPS];  /* SNN_RECORD_PACKED_I8 read-back tables [source][target] */
     int32_t i8_step[SNN_MAX_POPS][SNN_MAX_POPS];
     int32_t circuits_per_group;    /* batches: see snn_set_circuit_groups (0 = one group) */
     int32_t reserved3;
+    char last_error[256];          /* message of this handle's last failed call ("" if none; truncated) */
 } snn_info;
 
 typedef struct snn_net snn_net;
 
-/* Host only (no GPU needed).  Validates `spec` and fills `out`.
- * Errors: SNN_EINVAL for an invalid spec (message via snn_last_error). */
+/* Host only (no GPU needed).  Validates `spec` and fills `out`: the neuron and synapse
+ * counts of §2.2's sizing rules (population sizes N_b and pair counts N_pre N_post p at
+ * the spec's scales) and the arena bytes of every buffer.  No passage of its own: ABI
+ * helper.  Errors: SNN_EINVAL for an invalid spec (message via snn_last_error). */
 int snn_query_sizes(const snn_spec *spec, snn_sizes *out);
 
 /* Builds the network on the host (constants of §2.2 in FP64; every synapse of
@@ -323,16 +345,20 @@ int snn_collect_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t c
  * Errors: SNN_EINVAL (empty or negative window), SNN_EOVERFLOW, SNN_ECUDA. */
 int snn_read_rates(snn_net *net, int64_t t_begin, int64_t t_end, double *pop_rates_hz, int32_t *neuron_counts);
 
-/* Fills `out` with the network's constants and counters (host only, no wait). */
+/* Fills `out` with the network's constants (the FP64 and FP32 propagators of §2.2, the
+ * thalamic Poisson tables) and counters (host only, no wait).  No passage of its own:
+ * ABI helper.  Errors: SNN_EINVAL (null argument). */
 int snn_get_info(const snn_net *net, snn_info *out);
 
 /* Changes the launch schedule of the step kernels and re-captures the step graph
  * (waits for enqueued steps first): grid_ctas = CTAs of the step kernel (pipelined) or
  * of the delivery kernel (graph engine; SNN_RECORD_BLOCKED6 keeps one CTA per target
  * block), delivery_warps = delivery warps per CTA
- * (pipelined, 1..8), steps_per_graph as in snn_spec; 0 keeps a value.  The schedule
- * never changes results, only speed (see paper_2405_02019_gb300.autotune).
- * Errors: SNN_EINVAL (out of range), SNN_ENOTSUP (persistent engine), SNN_ECUDA. */
+ * (pipelined, 1..8; resident, blocks/32 rounded up .. 8), steps_per_graph as in
+ * snn_spec; 0 keeps a value.  The schedule never changes results, only speed (see
+ * paper_2405_02019_gb300.autotune).
+ * Errors: SNN_EINVAL (out of range), SNN_ENOTSUP (persistent engine; grid_ctas on the
+ * resident engine, which runs one CTA per target block), SNN_ECUDA. */
 int snn_set_schedule(snn_net *net, int32_t grid_ctas, int32_t delivery_warps, int32_t steps_per_graph);
 
 /* Batched networks on the graph or pipelined engine: runs the circuits in groups of
@@ -397,7 +423,8 @@ int snn_load_state(snn_net *net, const void *host_buf, uint64_t bytes);
 int snn_deliver_spikes(snn_net *net, const int32_t *spikers, int64_t n_spikers, int64_t t, int32_t blocks,
                        void *cuda_stream);
 
-/* Releases host-side state (not the caller's arena).  NULL is ignored. */
+/* Releases host-side state (not the caller's arena).  NULL is ignored.  No passage:
+ * ABI helper. */
 void snn_destroy(snn_net *net);
 
 /*
@@ -425,15 +452,22 @@ void snn_destroy(snn_net *net);
  * `seed` is the thalamic stream's seed (the spec's seed for parity with snn_step_n).
  * Enqueued on `cuda_stream`; returns without waiting.
  *
- * The first call on a device looks up the device address of the fixed array
- * (cudaGetSymbolAddress, with that device current); make that first call before any
- * stream capture.  Every call reuses the same array and clears its counter first, so
- * calls whose work overlaps on the GPU (different streams, or different handles at
- * the same time) race and give wrong results: serialise them.
+ * Every call looks up the device address of the fixed array (cudaGetSymbolAddress, with
+ * the buffers' device current); the first call on a device also loads the library's
+ * device code there, so make it before any stream capture.  Every call reuses the same
+ * array and clears its counter first, so calls whose work overlaps on the GPU
+ * (different streams, or different handles at the same time) race and give wrong
+ * results: serialise them.
+ * When io points into the handle's own arena (as snn_get_layout gives it), the handle's
+ * step counter, raster and pending-spike queue do not follow these steps: after
+ * snn_step_static has run on that arena, do not step the handle with snn_step_n nor
+ * save it with snn_save_state (the pipelined engine would deliver its queued spikes
+ * again and recompute a step on state that has moved on).
  * Errors: SNN_EINVAL for more than SNN_STATIC_MAX_NEURONS neurons, a missing or
  * misaligned buffer, a negative t; SNN_ENOTSUP for a network with packed synapse
- * records (this step reads plain records) or a batch of circuits; SNN_ECUDA on a
- * failed CUDA call.
+ * records (this step reads plain records) or a batch of circuits; SNN_ESTATE after a
+ * device error of the network; SNN_ECUDA on a failed CUDA call, or when a CUDA error
+ * of earlier work is pending (it is left for the caller to read).
  */
 #define SNN_STATIC_MAX_NEURONS 131072
 typedef struct snn_static_io {
@@ -452,10 +486,12 @@ typedef struct snn_static_io {
 
 int snn_step_static(const snn_net *net, const snn_static_io *io, uint64_t seed, int64_t t, void *cuda_stream);
 
-/* Static description of a status code. */
+/* Static description of a status code.  No passage: ABI helper. */
 const char *snn_strerror(int code);
 
-/* Message of the calling thread's last failed call ("" if none). */
+/* Message of the calling thread's last failed call ("" if none); the same message is
+ * also kept per handle for calls that take one (snn_info.last_error).  No passage: ABI
+ * helper. */
 const char *snn_last_error(void);
 
 #ifdef __cplusplus

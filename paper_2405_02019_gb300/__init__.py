@@ -17,6 +17,7 @@ import numpy as np
 
 from . import _abi
 from ._abi import (ABI_VERSION, D_MAX, ENGINE_DEFAULT, ENGINE_GRAPH, ENGINE_PERSISTENT, ENGINE_PIPELINED,  # noqa: F401
+                   ENGINE_RESIDENT,
                    RECORD_BLOCKED4, RECORD_BLOCKED6, RECORD_PACKED_BF16, RECORD_PACKED_I8, RECORD_PLAIN9,
                    FX_SHIFT, MAX_POPS, POISSON_KMAX, SNN_EOVERFLOW, SNN_ETIMEOUT, load, snn_info, snn_layout,
                    snn_sizes, snn_spec)
@@ -70,8 +71,10 @@ class _Spec:
     """An snn_spec plus the host arrays it points to (kept alive together)."""
 
     def __init__(self, model, scale_n=1000, scale_k=1000, seed=1, custom=None, steps_per_graph=0,
-                 raster_capacity=0, deliver_blocks=0, n_threads=0, engine=0, record_format=0, circuits=None):
+                 raster_capacity=0, deliver_blocks=0, n_threads=0, engine=0, record_format=0, circuits=None,
+                 smem_ring_rows=0):
         s = snn_spec()
+        s.smem_ring_rows = int(smem_ring_rows)
         s.engine = int(engine)
         s.record_format = int(record_format)
         s.abi_version = ABI_VERSION
@@ -218,14 +221,14 @@ class Network:
 
     def __init__(self, model, scale_n=1000, scale_k=1000, seed=1, custom=None, steps_per_graph=0,
                  raster_capacity=0, deliver_blocks=0, n_threads=0, device=None, engine=ENGINE_DEFAULT,
-                 record_format=RECORD_PLAIN9, circuits=None):
+                 record_format=RECORD_PLAIN9, circuits=None, smem_ring_rows=0):
         import torch
 
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
         self.device = torch.device(device if device is not None else "cuda")
         self._spec = _Spec(model, scale_n, scale_k, seed, custom, steps_per_graph, raster_capacity,
-                           deliver_blocks, n_threads, engine, record_format, circuits)
+                           deliver_blocks, n_threads, engine, record_format, circuits, smem_ring_rows)
         self.sizes = snn_query_sizes(self._spec.spec)
         self.model = model
         with torch.cuda.device(self.device):

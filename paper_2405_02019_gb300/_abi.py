@@ -11,7 +11,7 @@ D_MAX = 64
 FX_SHIFT = 12
 POISSON_KMAX = 24
 ABI_VERSION = 2
-ENGINE_DEFAULT, ENGINE_GRAPH, ENGINE_PERSISTENT, ENGINE_PIPELINED = 0, 1, 2, 3
+ENGINE_DEFAULT, ENGINE_GRAPH, ENGINE_PERSISTENT, ENGINE_PIPELINED, ENGINE_RESIDENT = 0, 1, 2, 3, 4
 RECORD_PLAIN9, RECORD_PACKED_I8, RECORD_PACKED_BF16, RECORD_BLOCKED6, RECORD_BLOCKED4 = 0, 1, 2, 3, 4
 
 STATUS = {0: "SNN_OK", 1: "SNN_EINVAL", 2: "SNN_ENOMEM", 3: "SNN_ECUDA", 4: "SNN_EOVERFLOW",
@@ -58,7 +58,7 @@ class snn_spec(C.Structure):
         ("engine", C.c_int32), ("record_format", C.c_int32),
         ("model", snn_model),
         ("custom", C.POINTER(snn_custom_net)),
-        ("n_circuits", C.c_int32), ("reserved", C.c_int32),
+        ("n_circuits", C.c_int32), ("smem_ring_rows", C.c_int32),
         ("circuits", C.POINTER(snn_circuit)),
     ]
 
@@ -73,7 +73,8 @@ class snn_sizes(C.Structure):
 class snn_layout(C.Structure):
     _fields_ = [(f, C.c_uint64) for f in ("ctl", "U", "I", "R", "ring", "row_ptr", "syn_tgt", "syn_w",
                                           "syn_delay", "rast_neuron", "rast_step", "params")] + [
-        ("n_neurons_padded", C.c_int64), ("n_synapses_padded", C.c_int64), ("blocks", C.c_uint64)]
+        ("n_neurons_padded", C.c_int64), ("n_synapses_padded", C.c_int64), ("blocks", C.c_uint64),
+        ("block_starts", C.c_uint64)]
 
 
 class snn_info(C.Structure):
@@ -94,7 +95,7 @@ class snn_info(C.Structure):
         ("n_circuits", C.c_int32), ("schedule_ctas", C.c_int32), ("schedule_delivery_warps", C.c_int32),
         ("target_blocks", C.c_int32),
         ("i8_base", (C.c_int32 * MAX_POPS) * MAX_POPS), ("i8_step", (C.c_int32 * MAX_POPS) * MAX_POPS),
-        ("circuits_per_group", C.c_int32), ("reserved3", C.c_int32),
+        ("circuits_per_group", C.c_int32), ("reserved3", C.c_int32), ("last_error", C.c_char * 256),
     ]
 
 

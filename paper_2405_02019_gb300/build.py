@@ -18,7 +18,7 @@ OUT = os.path.join(HERE, "libsnn.so")
 BUILD = os.path.join(HERE, "_build")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["builder.cpp", "kernels.cu", "abi.cu", "noalloc.cu"]
+SOURCES = ["builder.cpp", "kernels.cu", "resident.cu", "abi.cu", "noalloc.cu"]
 HEADERS = ["internal.hpp", "philox.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

@@ -20,10 +20,15 @@
 namespace {
 
 thread_local std::string g_last_error;
+// The handle whose entry point this thread is running (a HandleScope sets it): its
+// failures are also recorded on the handle, where snn_get_info reports them.
+thread_local snn_net *g_current = nullptr;
+void record_on_handle(const std::string &msg);
 
 int fail(int code, const std::string &msg)
 {
     g_last_error = msg;
+    record_on_handle(msg);
     return code;
 }
 
@@ -99,7 +104,24 @@ struct snn_net {
     // each circuit group takes the default for its size)
     bool step_grid_set = false;
     bool delivery_warps_set = false;
+    std::string last_error;  // message of this handle's last failed call
 };
+
+namespace {
+
+void record_on_handle(const std::string &msg)
+{
+    if (g_current) g_current->last_error = msg;
+}
+
+// Marks the handle an entry point works on, for the length of the call.
+struct HandleScope {
+    snn_net *prev;
+    explicit HandleScope(const snn_net *net) : prev(g_current) { g_current = const_cast<snn_net *>(net); }
+    ~HandleScope() { g_current = prev; }
+};
+
+}  // namespace
 
 namespace {
 
@@ -279,6 +301,27 @@ int launch_steps_persistent(snn_net *net, int64_t n, cudaStream_t st)
     return SNN_OK;
 }
 
+// Resident engine: every call's steps in cooperative launches of at most
+// kResidentMaxSteps steps; each launch reads the step counter and the raster cursor
+// from the control block at its start and writes them back at its end.  Mailbox words
+// are tagged with the step's rank in its launch, so the mailboxes are zeroed first.
+int launch_steps_resident(snn_net *net, int64_t n, cudaStream_t st)
+{
+    const uint64_t B = net->args.n_blocks;
+    const uint64_t mbox_bytes = 8 * 4 * B * snn::kResidentMboxWords;
+    const uint64_t inbox_bytes = 8 * 4 * B * B * snn::kResidentSlotWords;
+    while (n > 0) {
+        const int64_t m = std::min<int64_t>(n, snn::kResidentMaxSteps);
+        SNN_CUDA_TRY(cudaMemsetAsync(net->arena + net->L.mbox, 0, mbox_bytes, st));
+        SNN_CUDA_TRY(cudaMemsetAsync(net->arena + net->L.inbox, 0, inbox_bytes, st));
+        const int e = snn::launch_resident(net->args, m, st);
+        if (e != 0)
+            return fail(SNN_ECUDA, std::string("cooperative launch: ") + cudaGetErrorString(static_cast<cudaError_t>(e)));
+        n -= m;
+    }
+    return SNN_OK;
+}
+
 int capture_graph(snn_net *net)
 {
     SNN_CUDA_TRY(cudaStreamCreateWithFlags(&net->capture_stream, cudaStreamNonBlocking));
@@ -408,7 +451,7 @@ int drain(snn_net *net)
     net->snaps_valid_from = net->n_snaps;  // their cursors refer to the raster before the reset
     net->collected_t = net->t;
     if (net->device_error & snn::kErrTimeout)
-        return fail(SNN_ETIMEOUT, "a grid barrier of the persistent engine timed out");
+        return fail(SNN_ETIMEOUT, "a bounded device wait (persistent barrier or resident mailbox) timed out");
     if (net->device_error & snn::kErrRaster)
         return fail(SNN_EOVERFLOW, "device raster filled before it was read; raise raster_capacity");
     return SNN_OK;
@@ -748,6 +791,40 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
                 return rc;
             }
         }
+        if (net->engine == SNN_ENGINE_RESIDENT) {
+            const int64_t width = snn::resident_width(net->n, net->num_sms);
+            const int B = static_cast<int>(hn.blk.size()) - 1;
+            int coop = 0;
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, net->device);
+            if (width == 0 || B < 1 || B > net->num_sms) {
+                snn_destroy(net);
+                return fail(SNN_ENOTSUP, "network too large for the resident engine (1024 neurons per SM)");
+            }
+            a.n_blocks = B;
+            a.blk_off = reinterpret_cast<const int32_t *>(A + L.blocks);
+            a.res_segt = reinterpret_cast<const uint32_t *>(A + L.seg);
+            a.mbox = reinterpret_cast<uint64_t *>(A + L.mbox);
+            a.inbox = reinterpret_cast<uint64_t *>(A + L.inbox);
+            a.res_stride = static_cast<int32_t>(width);
+            a.res_rows = snn::resident_rows(static_cast<int>(width), spec->smem_ring_rows);
+            a.neuron_warps = static_cast<int32_t>((width + 127) / 128);
+            a.delivery_warps = std::max(snn::kResidentDeliverWarps, (B + 31) / 32);
+            cuda_ok(cudaMemcpyAsync(A + L.seg, hn.segt.data(), 4 * hn.segt.size(), cudaMemcpyHostToDevice, st),
+                    "segment table");
+            cuda_ok(cudaMemcpyAsync(A + L.blocks, hn.blk.data(), 4 * hn.blk.size(), cudaMemcpyHostToDevice, st),
+                    "blocks");
+            cuda_ok(cudaStreamSynchronize(st), "resident upload");
+            if (rc != SNN_OK) {
+                snn_destroy(net);
+                return rc;
+            }
+            if (a.res_rows == 0 || !coop || snn::prepare_resident_kernel(a) != 0 ||
+                snn::resident_blocks_per_sm(a) < 1) {
+                snn_destroy(net);
+                return fail(SNN_ENOTSUP, "the resident engine's cooperative launch does not fit this GPU");
+            }
+            net->steps_per_graph = spec->steps_per_graph > 0 ? spec->steps_per_graph : 1024;
+        }
         if (net->engine == SNN_ENGINE_PERSISTENT) {
             // every CTA of the cooperative launch must be resident at once
             int coop = 0;
@@ -789,13 +866,15 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
 
 int snn_step_n(snn_net *net, int64_t n_steps, void *cuda_stream)
 {
+    HandleScope scope(net);
     if (!net) return fail(SNN_EINVAL, "null network");
     if (n_steps < 0) return fail(SNN_EINVAL, "n_steps < 0");
     if (net->device_error) return fail(SNN_ESTATE, "a previous device error is pending");
     if (n_steps == 0) return SNN_OK;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    if (net->engine == SNN_ENGINE_PERSISTENT) {
-        const int rc = launch_steps_persistent(net, n_steps, st);
+    if (net->engine == SNN_ENGINE_PERSISTENT || net->engine == SNN_ENGINE_RESIDENT) {
+        const int rc = net->engine == SNN_ENGINE_RESIDENT ? launch_steps_resident(net, n_steps, st)
+                                                          : launch_steps_persistent(net, n_steps, st);
         if (rc) return rc;
     } else {
         int64_t t = net->t, n = n_steps;
@@ -831,10 +910,33 @@ int snn_step_n(snn_net *net, int64_t n_steps, void *cuda_stream)
 
 int snn_profile_steps(snn_net *net, int64_t n_steps, void *cuda_stream, double *ms_update, double *ms_deliver)
 {
+    HandleScope scope(net);
     if (!net) return fail(SNN_EINVAL, "null network");
     if (n_steps < 0) return fail(SNN_EINVAL, "n_steps < 0");
     if (net->device_error) return fail(SNN_ESTATE, "a previous device error is pending");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (net->engine == SNN_ENGINE_RESIDENT) {
+        // one cooperative launch runs both phases of every step: its time goes to ms_update
+        cudaEvent_t e0, e1;
+        SNN_CUDA_TRY(cudaEventCreate(&e0));
+        SNN_CUDA_TRY(cudaEventCreate(&e1));
+        cudaEventRecord(e0, st);
+        int rc = launch_steps_resident(net, n_steps, st);
+        cudaEventRecord(e1, st);
+        float ms = 0.f;
+        if (rc == SNN_OK) {
+            const cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) rc = fail(SNN_ECUDA, std::string("profile: ") + cudaGetErrorString(e));
+            else cudaEventElapsedTime(&ms, e0, e1);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc != SNN_OK) return rc;
+        net->t += n_steps;
+        if (ms_update) *ms_update = ms;
+        if (ms_deliver) *ms_deliver = 0.0;
+        return SNN_OK;
+    }
     double su = 0.0, sd = 0.0;
     const int64_t batch = 256;
     const size_t G = std::max<size_t>(net->group_args.size(), 1);
@@ -916,6 +1018,7 @@ int read_history(snn_net *net, int64_t t_done, int64_t *steps, int32_t *neurons,
 
 int snn_read_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t capacity, int64_t *n_written)
 {
+    HandleScope scope(net);
     if (!net || !n_written) return fail(SNN_EINVAL, "null argument");
     *n_written = 0;
     const int rc = drain(net);
@@ -926,6 +1029,7 @@ int snn_read_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t capa
 
 int snn_collect_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t capacity, int64_t *n_written)
 {
+    HandleScope scope(net);
     if (!net || !n_written) return fail(SNN_EINVAL, "null argument");
     *n_written = 0;
     if (net->device_error) return drain(net);  // report it now
@@ -935,6 +1039,7 @@ int snn_collect_spikes(snn_net *net, int64_t *steps, int32_t *neurons, int64_t c
 
 int snn_read_rates(snn_net *net, int64_t t_begin, int64_t t_end, double *pop_rates_hz, int32_t *neuron_counts)
 {
+    HandleScope scope(net);
     if (!net || !pop_rates_hz) return fail(SNN_EINVAL, "null argument");
     if (t_begin < 0 || t_end <= t_begin) return fail(SNN_EINVAL, "empty or negative window");
     if (t_end > net->t) return fail(SNN_EINVAL, "window ends after the steps enqueued so far");
@@ -1001,10 +1106,12 @@ int snn_get_info(const snn_net *net, snn_info *out)
     out->bytes_per_synapse = snn::record_bytes(net->format);
     out->n_circuits = static_cast<int32_t>(net->circuits.size());
     const bool step_kernel = net->engine == SNN_ENGINE_PIPELINED || net->engine == SNN_ENGINE_PERSISTENT;
-    out->schedule_ctas = step_kernel ? net->step_grid : net->deliver_grid;
-    out->schedule_delivery_warps = step_kernel ? net->args.delivery_warps : 0;
+    const bool resident = net->engine == SNN_ENGINE_RESIDENT;
+    out->schedule_ctas = resident ? net->args.n_blocks : step_kernel ? net->step_grid : net->deliver_grid;
+    out->schedule_delivery_warps = step_kernel || resident ? net->args.delivery_warps : 0;
     out->target_blocks = net->args.n_blocks;
     out->circuits_per_group = net->circuits_per_group;
+    std::strncpy(out->last_error, net->last_error.c_str(), sizeof(out->last_error) - 1);
     std::memcpy(out->i8_base, net->i8_base, sizeof(out->i8_base));
     std::memcpy(out->i8_step, net->i8_step, sizeof(out->i8_step));
     return SNN_OK;
@@ -1031,6 +1138,7 @@ int snn_get_layout(const snn_net *net, snn_layout *out)
     out->n_neurons_padded = net->npad;
     out->n_synapses_padded = net->n_syn_padded;
     out->blocks = L.blocks;
+    out->block_starts = net->engine == SNN_ENGINE_RESIDENT ? L.seg : 0;
     return SNN_OK;
 }
 
@@ -1067,6 +1175,7 @@ std::vector<std::pair<uint64_t, uint64_t>> state_segments(const snn_net *net)
 
 int snn_save_state(snn_net *net, void *host_buf, uint64_t capacity, uint64_t *written)
 {
+    HandleScope scope(net);
     if (!net || !written) return fail(SNN_EINVAL, "null argument");
     const auto seg = state_segments(net);
     uint64_t total = sizeof(StateHeader);
@@ -1090,6 +1199,7 @@ int snn_save_state(snn_net *net, void *host_buf, uint64_t capacity, uint64_t *wr
 
 int snn_load_state(snn_net *net, const void *host_buf, uint64_t bytes)
 {
+    HandleScope scope(net);
     if (!net || !host_buf) return fail(SNN_EINVAL, "null argument");
     if (bytes < sizeof(StateHeader)) return fail(SNN_EINVAL, "state buffer too small");
     StateHeader h;
@@ -1128,6 +1238,7 @@ int snn_load_state(snn_net *net, const void *host_buf, uint64_t bytes)
 
 int snn_set_schedule(snn_net *net, int32_t grid_ctas, int32_t delivery_warps, int32_t steps_per_graph)
 {
+    HandleScope scope(net);
     if (!net) return fail(SNN_EINVAL, "null network");
     if (grid_ctas < 0 || grid_ctas > 65535 || delivery_warps < 0 || steps_per_graph < 0 || steps_per_graph > 100000)
         return fail(SNN_EINVAL, "schedule out of range");
@@ -1151,6 +1262,16 @@ int snn_set_schedule(snn_net *net, int32_t grid_ctas, int32_t delivery_warps, in
     } else if (net->engine == SNN_ENGINE_GRAPH) {
         if (grid_ctas > 0) net->deliver_grid = grid_ctas;
         if (steps_per_graph > 0) net->steps_per_graph = steps_per_graph;
+    } else if (net->engine == SNN_ENGINE_RESIDENT) {
+        // one CTA per target block; the delivery warps must cover one mailbox per lane
+        if (grid_ctas > 0) return fail(SNN_ENOTSUP, "the resident engine runs one CTA per target block");
+        if (delivery_warps > 0) {
+            if (delivery_warps > snn::kResidentDeliverWarps || delivery_warps * 32 < a.n_blocks)
+                return fail(SNN_EINVAL, "resident engine: delivery warps out of [blocks / 32, 8]");
+            a.delivery_warps = delivery_warps;
+        }
+        if (steps_per_graph > 0) net->steps_per_graph = steps_per_graph;
+        return SNN_OK;
     } else {
         if (grid_ctas > 0 || delivery_warps > 0 || steps_per_graph > 0)
             return fail(SNN_ENOTSUP, "the persistent engine has a fixed schedule");
@@ -1162,6 +1283,7 @@ int snn_set_schedule(snn_net *net, int32_t grid_ctas, int32_t delivery_warps, in
 
 int snn_set_circuit_groups(snn_net *net, int32_t circuits_per_group)
 {
+    HandleScope scope(net);
     if (!net) return fail(SNN_EINVAL, "null network");
     if (circuits_per_group < 0) return fail(SNN_EINVAL, "circuits_per_group < 0");
     if (net->engine != SNN_ENGINE_GRAPH && net->engine != SNN_ENGINE_PIPELINED)
@@ -1202,6 +1324,7 @@ int snn_get_out_degrees(const snn_net *net, int32_t *out)
 int snn_deliver_spikes(snn_net *net, const int32_t *spikers, int64_t n_spikers, int64_t t, int32_t blocks,
                        void *cuda_stream)
 {
+    HandleScope scope(net);
     if (!net || (n_spikers > 0 && !spikers)) return fail(SNN_EINVAL, "null argument");
     if (n_spikers < 0 || t < 0 || blocks < 0) return fail(SNN_EINVAL, "negative argument");
     if (n_spikers == 0) return SNN_OK;

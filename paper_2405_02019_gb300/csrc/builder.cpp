@@ -214,7 +214,15 @@ bool validate_spec(const snn_spec &spec, std::string &why)
         return fail("raster_capacity out of [0, 2^31-1]");
     if (spec.steps_per_graph < 0 || spec.steps_per_graph > 100000) return fail("steps_per_graph out of [0, 100000]");
     if (spec.deliver_blocks < 0 || spec.deliver_blocks > 65535) return fail("deliver_blocks out of range");
-    if (spec.engine < SNN_ENGINE_DEFAULT || spec.engine > SNN_ENGINE_PIPELINED) return fail("unknown engine");
+    if (spec.engine < SNN_ENGINE_DEFAULT || spec.engine > SNN_ENGINE_RESIDENT) return fail("unknown engine");
+    if (spec.smem_ring_rows != 0 && spec.smem_ring_rows != 8 && spec.smem_ring_rows != 16 &&
+        spec.smem_ring_rows != 32 && spec.smem_ring_rows != 64)
+        return fail("smem_ring_rows must be 0, 8, 16, 32 or 64");
+    if (spec.engine == SNN_ENGINE_RESIDENT) {
+        if (spec.n_circuits > 0) return fail("the resident engine takes one circuit");
+        if (spec.record_format != SNN_RECORD_PLAIN9) return fail("the resident engine reads plain records");
+        if (count_neurons(spec) > kResidentMaxNeurons) return fail("more neurons than the resident engine holds");
+    }
     if (spec.record_format < SNN_RECORD_PLAIN9 || spec.record_format > SNN_RECORD_BLOCKED4)
         return fail("unknown record_format");
     if ((spec.record_format == SNN_RECORD_PACKED_I8 || spec.record_format == SNN_RECORD_PACKED_BF16) &&
@@ -313,7 +321,14 @@ Layout make_layout(const snn_spec &spec)
         L.syn_w = o; o = up(o + wbytes * L.syn_padded_max + 16);
         L.syn_d = o; o = up(o + (fmt == SNN_RECORD_PLAIN9 ? L.syn_padded_max : 0) + 16);
     }
-    L.blocks = o; o = up(o + 4 * (is_blocked(fmt) ? max_target_blocks(n) + 1 : 1));
+    const bool resident = spec.engine == SNN_ENGINE_RESIDENT;
+    const int64_t res_blocks = resident ? resident_max_blocks(n) : 0;
+    L.blocks = o; o = up(o + 4 * std::max<int64_t>(is_blocked(fmt) ? max_target_blocks(n) + 1 : 1, res_blocks + 1));
+    // resident engine: each block's segment table (uint32 [blocks][n]), the outboxes and
+    // the inbox slots
+    L.seg = o; o = up(o + (resident ? 4 * uint64_t(n) * res_blocks : 0));
+    L.mbox = o; o = up(o + (resident ? 8 * uint64_t{4} * res_blocks * kResidentMboxWords : 0));
+    L.inbox = o; o = up(o + (resident ? 8 * uint64_t{4} * res_blocks * res_blocks * kResidentSlotWords : 0));
     L.rast_nrn = o; o = up(o + 4 * L.rast_cap);
     L.rast_t = o; o = up(o + 4 * L.rast_cap);
     L.U2 = o; o = up(o + 4 * L.npad);
@@ -620,6 +635,52 @@ bool pack_blocked(HostNetwork &net, int nthreads, int num_sms, std::string &why)
     return true;
 }
 
+// Resident engine: targets cut into blocks of `width` consecutive neurons (one CTA each)
+// and every row regrouped by target block, delay order kept inside a block (a stable
+// counting sort by block), so that a CTA reads one contiguous segment of each row.  The
+// row padding stays at the row's end.  segt[b][i] = start | length << 16 of block b's
+// segment in row i (start relative to the row): each CTA reads only its own table row.
+bool group_rows_by_block(HostNetwork &net, int64_t width, int nthreads, std::string &why)
+{
+    const int64_t n = net.n;
+    const int B = static_cast<int>((n + width - 1) / width);
+    net.blk.resize(B + 1);
+    for (int b = 0; b <= B; ++b) net.blk[b] = static_cast<int32_t>(std::min<int64_t>(n, int64_t{b} * width));
+    for (int64_t i = 0; i < n; ++i)
+        if (net.out_degree[i] > 65535) {
+            why = "the resident engine holds rows of at most 65535 synapses";
+            return false;
+        }
+    net.segt.assign(static_cast<size_t>(n) * B, 0);
+    parallel_for(nthreads, n, [&](int, int64_t lo, int64_t hi) {
+        std::vector<int64_t> pos(B + 1);
+        std::vector<int32_t> t2, w2;
+        std::vector<uint8_t> d2;
+        for (int64_t i = lo; i < hi; ++i) {
+            const int64_t rs = net.row_ptr[i], len = net.out_degree[i];
+            std::fill(pos.begin(), pos.end(), 0);
+            for (int64_t s = rs; s < rs + len; ++s) ++pos[net.tgt[s] / width + 1];
+            for (int b = 0; b < B; ++b) pos[b + 1] += pos[b];
+            for (int b = 0; b < B; ++b)
+                net.segt[static_cast<size_t>(b) * n + i] =
+                    static_cast<uint32_t>(pos[b]) | static_cast<uint32_t>(pos[b + 1] - pos[b]) << 16;
+            t2.resize(len);
+            w2.resize(len);
+            d2.resize(len);
+            for (int64_t s = rs; s < rs + len; ++s) {
+                const int64_t dst = pos[net.tgt[s] / width]++;
+                t2[dst] = net.tgt[s];
+                w2[dst] = net.w[s];
+                d2[dst] = net.d[s];
+            }
+            std::copy(t2.begin(), t2.end(), net.tgt.begin() + rs);
+            std::copy(w2.begin(), w2.end(), net.w.begin() + rs);
+            std::copy(d2.begin(), d2.end(), net.d.begin() + rs);
+        }
+    });
+    return true;
+}
+
 bool build_one(const snn_spec &spec, const Constants &c, HostNetwork &net, std::string &why, int num_sms);
 }
 
@@ -628,6 +689,14 @@ bool build_host_network(const snn_spec &spec, const Constants &c, HostNetwork &n
     if (spec.n_circuits <= 0) {
         if (!build_one(spec, c, net, why, num_sms)) return false;
         net.circuits = {CircuitInfo{0, net.n, spec.seed, 0}};
+        if (spec.engine == SNN_ENGINE_RESIDENT && num_sms > 0) {
+            const int64_t width = resident_width(net.n, num_sms);
+            if (width == 0) {
+                why = "more neurons than the resident engine holds on this GPU (1024 per SM)";
+                return false;
+            }
+            if (!group_rows_by_block(net, width, resolve_threads(spec.n_threads), why)) return false;
+        }
         return true;
     }
     // a batch: every circuit built alone (in plain records), placed at a 128-aligned base

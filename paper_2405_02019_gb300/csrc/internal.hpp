@@ -1,6 +1,7 @@
 // Internal declarations shared by the host builder, the kernels and the ABI layer.
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -102,6 +103,24 @@ inline int max_target_blocks(int64_t n)
     return static_cast<int>((n + kBlockAvgWidth - 1) / kBlockAvgWidth + n / (kBlockMaxWidth - kBlockAlign) + 2);
 }
 
+// Resident engine: one cooperative CTA per target block of consecutive neurons, which
+// keeps its neurons' state in registers and its columns of the ring in shared memory
+// for a whole launch; spikes cross between CTAs through inbox slots (one per reader and
+// sender) and, beyond three spikes of a block in one step, the sender's outbox.
+constexpr int kResidentMaxWidth = 1024;      // neurons per block (8 neuron warps x 128)
+constexpr int kResidentMaxBlocks = 256;      // blocks (CTAs, at most one per SM)
+constexpr int kResidentAlign = 32;           // block boundaries are multiples of 32
+constexpr int kResidentDeliverWarps = 8;     // delivery warps per CTA (default)
+constexpr int kResidentMboxWords = kResidentMaxWidth + 2;  // u64 words of one outbox: header, entries, pad
+constexpr int kResidentSlotWords = 4;        // u64 words of one inbox slot: header and three entries
+constexpr int64_t kResidentMaxSteps = int64_t{1} << 19;     // steps per launch (mailbox tags count them)
+constexpr int kResidentGather = 1024;        // spikes of a step staged in shared memory per pass
+constexpr int64_t kResidentMaxNeurons = int64_t{kResidentMaxBlocks} * kResidentMaxWidth;
+inline int resident_max_blocks(int64_t n)
+{
+    return static_cast<int>(std::min<int64_t>(kResidentMaxBlocks, (n + kResidentAlign - 1) / kResidentAlign));
+}
+
 // Kernel arguments (by value; small).
 struct StepArgs {
     Ctl *ctl;
@@ -148,6 +167,11 @@ struct StepArgs {
     int32_t pad4;
     int64_t quad_base;            // first quad the update (or step) launch covers, n its end neuron
     int64_t queue_cap;            // pipelined engine: entries of each queue (a circuit group's neurons)
+    uint64_t *mbox;               // resident engine: outboxes [4][n_blocks][kResidentMboxWords]
+    uint64_t *inbox;              // resident engine: inbox slots [4][n_blocks (reader)][n_blocks (sender)][4]
+    const uint32_t *res_segt;     // resident engine: [n_blocks][n] segment start | length << 16 within a row
+    int32_t res_rows;             // resident engine: ring rows kept in shared memory (power of two, 8..64)
+    int32_t res_stride;           // resident engine: shared ring row stride (widest block, multiple of 32)
 };
 
 // Host constants of one model (§2.2).
@@ -183,12 +207,13 @@ struct HostNetwork {
     std::vector<int32_t> blk;      // blocked records: block boundaries
     std::vector<uint16_t> rec16;   // blocked records: local target | delay << 10
     std::vector<uint16_t> seg;     // blocked records: [n][blocks + 1] block starts per row
+    std::vector<uint32_t> segt;    // resident engine: [blocks][n] segment start | length << 16 within each row
 };
 
 // Arena layout for a spec.
 struct Layout {
     uint64_t ctl, tables, U, I, R, ring, row_ptr, syn_tgt, syn_w, syn_d, rast_nrn, rast_t, U2, R2, queue, qcount, pop_id,
-        group_circuit, circuits, blocks, total;
+        group_circuit, circuits, blocks, seg, mbox, inbox, total;
     int64_t npad, syn_padded_max, rast_cap;
 };
 
@@ -227,5 +252,18 @@ void launch_prime(const StepArgs &a, int grid, void *stream);         // pipelin
 int prepare_step_kernel(const StepArgs &a);                           // dynamic shared memory opt-in
 int step_grid(int num_sms, int64_t quad_warps);  // default CTAs of the step kernel
 int step_threads(const StepArgs &a);
+
+// resident.cu
+// Block width of the resident engine for n neurons on num_sms SMs (a multiple of
+// kResidentAlign; 0 if n does not fit kResidentMaxWidth per SM).
+int64_t resident_width(int64_t n, int num_sms);
+size_t resident_smem_bytes(int rows, int stride);
+// Ring rows in shared memory: the largest power of two in [8, 64] (at most `cap` when
+// cap > 0) whose shared memory fits one CTA; 0 if none fits.
+int resident_rows(int stride, int cap);
+int prepare_resident_kernel(const StepArgs &a);
+int resident_blocks_per_sm(const StepArgs &a);
+// n_steps steps from the device's t_base in one cooperative launch of a.n_blocks CTAs
+int launch_resident(const StepArgs &a, int64_t n_steps, void *stream);
 
 }  // namespace snn

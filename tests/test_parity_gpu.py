@@ -55,7 +55,24 @@ def _device_network(net):
     return rp, tg, w, d
 
 
-def _row_multisets_equal(onet, rp, tg, w, d):
+def _block_bounds(net):
+    """Target-block boundaries of a resident-engine network (None for other engines)."""
+    info = net.info()
+    if info.engine != snn.ENGINE_RESIDENT:
+        return None
+    return net.device_view("blocks", torch.int32, int(info.target_blocks) + 1).cpu().numpy().astype(np.int64)
+
+
+def _assert_row_order(bounds, tg, d, starts, lens):
+    """Rows are delay-sorted (indexed store of §3.5); on the resident engine grouped by
+    target block first, delay-sorted inside each block."""
+    for a, L in zip(starts, lens):
+        seg_d = d[a:a + L].astype(np.int64)
+        key = seg_d if bounds is None else (np.searchsorted(bounds, tg[a:a + L], side="right") - 1) * 64 + seg_d
+        assert np.all(np.diff(key) >= 0)
+
+
+def _row_multisets_equal(onet, rp, tg, w, d, bounds=None):
     n = onet.n
     lens = np.diff(onet.row_ptr)
     plen = np.diff(rp)
@@ -65,10 +82,8 @@ def _row_multisets_equal(onet, rp, tg, w, d):
     assert np.all(w[: rp[-1]][~real] == 0)
     pre_l = np.repeat(np.arange(n), plen)[real]
     tl, wl, dl = tg[: rp[-1]][real], w[: rp[-1]][real], d[: rp[-1]][real]
-    # rows are delay-sorted on the device (indexed store of §3.5)
-    for i in range(0, n, max(1, n // 200)):
-        seg = d[rp[i]: rp[i] + lens[i]]
-        assert np.all(np.diff(seg.astype(int)) >= 0)
+    sample = np.arange(0, n, max(1, n // 200))
+    _assert_row_order(bounds, tg, d, rp[sample], lens[sample])
     pre_o = np.repeat(np.arange(n), lens)
     ko = np.lexsort((onet.w_fx, onet.delay, onet.post, pre_o))
     kl = np.lexsort((wl, dl, tl, pre_l))
@@ -118,11 +133,12 @@ def test_network_identical_tiny(model, tiny):
     net.close()
 
 
-GRAPH, PERSIST, PIPE = snn.ENGINE_GRAPH, snn.ENGINE_PERSISTENT, snn.ENGINE_PIPELINED
-ENGINES = [GRAPH, PERSIST, PIPE]
+GRAPH, PERSIST, PIPE, RES = snn.ENGINE_GRAPH, snn.ENGINE_PERSISTENT, snn.ENGINE_PIPELINED, snn.ENGINE_RESIDENT
+ENGINES = [GRAPH, PERSIST, PIPE, RES]
 
 
-@pytest.mark.parametrize("engine,spg", [(GRAPH, 96), (GRAPH, 1000), (PERSIST, 0), (PIPE, 96), (PIPE, 1000)])
+@pytest.mark.parametrize("engine,spg", [(GRAPH, 96), (GRAPH, 1000), (PERSIST, 0), (PIPE, 96), (PIPE, 1000),
+                                        (RES, 0)])
 def test_raster_bit_exact_tiny(model, tiny, engine, spg):
     """Tiny microcircuit (7,718 neurons, 2.85e6 synapses), 1,000 steps: identical raster
     and final state.  spg=96 mixes graph replays with directly launched remainders."""
@@ -232,7 +248,7 @@ def test_profile_steps_same_dynamics(model, tiny, engine):
                       engine=engine)
     net.step(100)
     mu, md = net.profile_steps(300)
-    assert mu > 0 and md > 0
+    assert mu > 0 and (md > 0 or engine == RES)  # the resident launch runs both phases
     net.step(100)
     g_t, g_i = net.read_spikes()
     o_t, o_i = oracle.Sim(model, onet, wl.seed).run(500)
@@ -361,8 +377,10 @@ def test_raster_overflow_is_reported(model, engine):
     with pytest.raises(snn.SnnError) as e:
         net.read_spikes()
     assert e.value.code == snn.SNN_EOVERFLOW
+    assert b"raster" in net.info().last_error  # also kept on the handle
     with pytest.raises(snn.SnnError):
         net.step(1)
+    assert b"device error" in net.info().last_error
     net.close()
 
 
@@ -372,7 +390,7 @@ def test_extreme_scales(model, scale, engine):
     sn, sk = scale
     onet = oracle.build_network(model, sn, sk, 9)
     net = snn.Network(model, sn, sk, seed=9, steps_per_graph=40, engine=engine)
-    _row_multisets_equal(onet, *_device_network(net))
+    _row_multisets_equal(onet, *_device_network(net), bounds=_block_bounds(net))
     net.step(250)
     g = net.read_spikes()
     sim = oracle.Sim(model, onet, 9)
@@ -400,7 +418,7 @@ def full(model):
     return wl, onet
 
 
-def _rows_equal_sampled(onet, rp, tg, w, d, rows):
+def _rows_equal_sampled(onet, rp, tg, w, d, rows, bounds=None):
     """Exact per-row multiset comparison for the given rows, plus global sums over all
     synapses (the full sort of 2.8e8 records is left to the smaller scales)."""
     lens = np.diff(onet.row_ptr)
@@ -414,7 +432,7 @@ def _rows_equal_sampled(onet, rp, tg, w, d, rows):
         g = np.sort(tg[b:b + L].astype(np.int64) << 38 | d[b:b + L].astype(np.int64) << 32
                     | (w[b:b + L].astype(np.int64) + 2**31))
         assert np.array_equal(o, g), i
-        assert np.all(np.diff(d[b:b + L].astype(int)) >= 0)
+        _assert_row_order(bounds, tg, d, [b], [L])
         assert np.all(w[b + L:rp[i + 1]] == 0)
     n_real = rp[-1]
     assert int(w[:n_real].astype(np.int64).sum()) == int(onet.w_fx.astype(np.int64).sum())
@@ -424,7 +442,7 @@ def _rows_equal_sampled(onet, rp, tg, w, d, rows):
         onet.delay.astype(np.int64).sum())
 
 
-@pytest.mark.parametrize("engine", [snn.ENGINE_DEFAULT, GRAPH])
+@pytest.mark.parametrize("engine", [snn.ENGINE_DEFAULT, GRAPH, RES])
 def test_full_scale_parity(model, full, engine):
     """Full microcircuit (77,169 neurons, 284,811,022 synapses) in the bench's launch
     configuration (default engine) and with the graph engine: the network (every row
@@ -443,7 +461,7 @@ def test_full_scale_parity(model, full, engine):
     _assert_same_state(net, sim)
     rng = np.random.default_rng(0)
     rows = np.unique(np.concatenate([o_i, rng.integers(0, onet.n, 2000)]))
-    _rows_equal_sampled(onet, *_device_network(net), rows)
+    _rows_equal_sampled(onet, *_device_network(net), rows, bounds=_block_bounds(net))
     net.close()
 
 
@@ -991,7 +1009,7 @@ def test_blocked_full_scale_parity(model, full):
 
 
 @pytest.mark.parametrize("fmt", [snn.RECORD_PLAIN9, snn.RECORD_PACKED_BF16])
-@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("engine", [GRAPH, PERSIST, PIPE])  # the resident engine takes one circuit
 def test_batched_circuits_equal_standalone_runs(model, engine, fmt):
     """Circuits of uneven scale and seed stepped together: every circuit's slice of the
     batched raster and state equals the oracle run of that circuit alone."""
