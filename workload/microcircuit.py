@@ -9,7 +9,7 @@ Every number below is typed from the paper's tables:
   the caption's doubled pathway.
 * Table "params3" (connection probabilities, §2.2).
 
-Readings where the paper is ambiguous (each is also listed in the design doc):
+Readings where the paper is ambiguous:
 
 * Connection table orientation: rows are the *target* population and columns the
   *source* population (the PD model the paper reproduces via NEST, §4.1). The caption's
