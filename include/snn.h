@@ -354,7 +354,8 @@ int snn_get_info(const snn_net *net, snn_info *out);
  * (waits for enqueued steps first): grid_ctas = CTAs of the step kernel (pipelined) or
  * of the delivery kernel (graph engine; SNN_RECORD_BLOCKED6 keeps one CTA per target
  * block), delivery_warps = delivery warps per CTA
- * (pipelined, 1..8; resident, blocks/32 rounded up .. 8), steps_per_graph as in
+ * (pipelined, 1..8; resident: even, two teams of at least blocks/32 warps, at most 16
+ * warps with the neuron warps), steps_per_graph as in
  * snn_spec; 0 keeps a value.  The schedule never changes results, only speed (see
  * paper_2405_02019_gb300.autotune).
  * Errors: SNN_EINVAL (out of range), SNN_ENOTSUP (persistent engine; grid_ctas on the
@@ -465,7 +466,8 @@ void snn_destroy(snn_net *net);
  * again and recompute a step on state that has moved on).
  * Errors: SNN_EINVAL for more than SNN_STATIC_MAX_NEURONS neurons, a missing or
  * misaligned buffer, a negative t; SNN_ENOTSUP for a network with packed synapse
- * records (this step reads plain records) or a batch of circuits; SNN_ESTATE after a
+ * records (this step reads plain records as rows), a batch of circuits or the resident
+ * engine (whose records are stored block-major); SNN_ESTATE after a
  * device error of the network; SNN_ECUDA on a failed CUDA call, or when a CUDA error
  * of earlier work is pending (it is left for the caller to read).
  */

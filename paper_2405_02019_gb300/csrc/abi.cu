@@ -308,8 +308,8 @@ int launch_steps_persistent(snn_net *net, int64_t n, cudaStream_t st)
 int launch_steps_resident(snn_net *net, int64_t n, cudaStream_t st)
 {
     const uint64_t B = net->args.n_blocks;
-    const uint64_t mbox_bytes = 8 * 4 * B * snn::kResidentMboxWords;
-    const uint64_t inbox_bytes = 8 * 4 * B * B * snn::kResidentSlotWords;
+    const uint64_t mbox_bytes = 4 * 4 * B * snn::kResidentMboxWords;
+    const uint64_t inbox_bytes = 4 * 4 * B * B * snn::kResidentSlotWords;
     while (n > 0) {
         const int64_t m = std::min<int64_t>(n, snn::kResidentMaxSteps);
         SNN_CUDA_TRY(cudaMemsetAsync(net->arena + net->L.mbox, 0, mbox_bytes, st));
@@ -802,15 +802,26 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
             }
             a.n_blocks = B;
             a.blk_off = reinterpret_cast<const int32_t *>(A + L.blocks);
-            a.res_segt = reinterpret_cast<const uint32_t *>(A + L.seg);
-            a.mbox = reinterpret_cast<uint64_t *>(A + L.mbox);
-            a.inbox = reinterpret_cast<uint64_t *>(A + L.inbox);
+            const snn::ResTables T = snn::resident_tables(net->n, B);
+            a.res_rbase = reinterpret_cast<const int64_t *>(A + L.seg + T.rbase);
+            a.res_coarse = reinterpret_cast<const uint32_t *>(A + L.seg + T.coarse);
+            a.res_lens = A + L.seg + T.lens;
+            a.res_offt = reinterpret_cast<const uint32_t *>(A + L.seg + T.offt);
+            a.res_lens_stride = static_cast<int32_t>(T.lens_stride);
+            a.res_coarse_stride = static_cast<int32_t>(T.coarse_stride);
+            a.mbox = reinterpret_cast<uint32_t *>(A + L.mbox);
+            a.inbox = reinterpret_cast<uint32_t *>(A + L.inbox);
             a.res_stride = static_cast<int32_t>(width);
-            a.res_rows = snn::resident_rows(static_cast<int>(width), spec->smem_ring_rows);
+            a.res_rows = snn::resident_rows(static_cast<int>(width), spec->smem_ring_rows, net->n);
             a.neuron_warps = static_cast<int32_t>((width + 127) / 128);
-            a.delivery_warps = std::max(snn::kResidentDeliverWarps, (B + 31) / 32);
-            cuda_ok(cudaMemcpyAsync(A + L.seg, hn.segt.data(), 4 * hn.segt.size(), cudaMemcpyHostToDevice, st),
-                    "segment table");
+            // two delivery teams, each with a lane per mailbox
+            a.delivery_warps = 2 * std::max(snn::kResidentTeamWarps, (B + 31) / 32);
+            if (a.neuron_warps + a.delivery_warps > snn::kResidentMaxWarps) {
+                snn_destroy(net);
+                return fail(SNN_ENOTSUP, "the resident engine's CTA would exceed its warp limit for this network");
+            }
+            cuda_ok(cudaMemcpyAsync(A + L.seg, hn.restab.data(), hn.restab.size(), cudaMemcpyHostToDevice, st),
+                    "block tables");
             cuda_ok(cudaMemcpyAsync(A + L.blocks, hn.blk.data(), 4 * hn.blk.size(), cudaMemcpyHostToDevice, st),
                     "blocks");
             cuda_ok(cudaStreamSynchronize(st), "resident upload");
@@ -1266,8 +1277,11 @@ int snn_set_schedule(snn_net *net, int32_t grid_ctas, int32_t delivery_warps, in
         // one CTA per target block; the delivery warps must cover one mailbox per lane
         if (grid_ctas > 0) return fail(SNN_ENOTSUP, "the resident engine runs one CTA per target block");
         if (delivery_warps > 0) {
-            if (delivery_warps > snn::kResidentDeliverWarps || delivery_warps * 32 < a.n_blocks)
-                return fail(SNN_EINVAL, "resident engine: delivery warps out of [blocks / 32, 8]");
+            // two teams of delivery_warps / 2 warps, each with a lane per mailbox
+            if (delivery_warps % 2 != 0 || (delivery_warps / 2) * 32 < a.n_blocks ||
+                a.neuron_warps + delivery_warps > snn::kResidentMaxWarps)
+                return fail(SNN_EINVAL, "resident engine: delivery warps must be even, give each of the two teams "
+                                        "a lane per target block and fit the CTA");
             a.delivery_warps = delivery_warps;
         }
         if (steps_per_graph > 0) net->steps_per_graph = steps_per_graph;
@@ -1328,6 +1342,8 @@ int snn_deliver_spikes(snn_net *net, const int32_t *spikers, int64_t n_spikers, 
     if (!net || (n_spikers > 0 && !spikers)) return fail(SNN_EINVAL, "null argument");
     if (n_spikers < 0 || t < 0 || blocks < 0) return fail(SNN_EINVAL, "negative argument");
     if (n_spikers == 0) return SNN_OK;
+    if (net->engine == SNN_ENGINE_RESIDENT)
+        return fail(SNN_ENOTSUP, "the resident engine stores its records block-major, not as rows");
     if (snn::is_blocked(net->format)) {
         snn::launch_deliver_blocked(net->args, spikers, n_spikers, t, 0, cuda_stream);
         SNN_CUDA_TRY(cudaGetLastError());

@@ -324,11 +324,10 @@ Layout make_layout(const snn_spec &spec)
     const bool resident = spec.engine == SNN_ENGINE_RESIDENT;
     const int64_t res_blocks = resident ? resident_max_blocks(n) : 0;
     L.blocks = o; o = up(o + 4 * std::max<int64_t>(is_blocked(fmt) ? max_target_blocks(n) + 1 : 1, res_blocks + 1));
-    // resident engine: each block's segment table (uint32 [blocks][n]), the outboxes and
-    // the inbox slots
-    L.seg = o; o = up(o + (resident ? 4 * uint64_t(n) * res_blocks : 0));
-    L.mbox = o; o = up(o + (resident ? 8 * uint64_t{4} * res_blocks * kResidentMboxWords : 0));
-    L.inbox = o; o = up(o + (resident ? 8 * uint64_t{4} * res_blocks * res_blocks * kResidentSlotWords : 0));
+    // resident engine: the block tables, the outboxes and the inbox slots
+    L.seg = o; o = up(o + (resident ? resident_tables(n, res_blocks).total : 0));
+    L.mbox = o; o = up(o + (resident ? 4 * uint64_t{4} * res_blocks * kResidentMboxWords : 0));
+    L.inbox = o; o = up(o + (resident ? 4 * uint64_t{4} * res_blocks * res_blocks * kResidentSlotWords : 0));
     L.rast_nrn = o; o = up(o + 4 * L.rast_cap);
     L.rast_t = o; o = up(o + 4 * L.rast_cap);
     L.U2 = o; o = up(o + 4 * L.npad);
@@ -635,49 +634,73 @@ bool pack_blocked(HostNetwork &net, int nthreads, int num_sms, std::string &why)
     return true;
 }
 
-// Resident engine: targets cut into blocks of `width` consecutive neurons (one CTA each)
-// and every row regrouped by target block, delay order kept inside a block (a stable
-// counting sort by block), so that a CTA reads one contiguous segment of each row.  The
-// row padding stays at the row's end.  segt[b][i] = start | length << 16 of block b's
-// segment in row i (start relative to the row): each CTA reads only its own table row.
-bool group_rows_by_block(HostNetwork &net, int64_t width, int nthreads, std::string &why)
+// Resident engine: targets cut into blocks of `width` consecutive neurons (one CTA each),
+// and the records rearranged block-major: block p's region holds every synapse into the
+// block, sender by sender, each sender's segment in the delay order of its row (a stable
+// pass over the delay-sorted rows).  The plain record arrays keep their types; row_ptr
+// then only gives row lengths (prefix sums of the out-degrees).  The tables of
+// resident_tables() locate every (block, sender) segment.
+bool block_major_records(HostNetwork &net, int64_t width, int nthreads, std::string &why)
 {
     const int64_t n = net.n;
     const int B = static_cast<int>((n + width - 1) / width);
     net.blk.resize(B + 1);
     for (int b = 0; b <= B; ++b) net.blk[b] = static_cast<int32_t>(std::min<int64_t>(n, int64_t{b} * width));
-    for (int64_t i = 0; i < n; ++i)
-        if (net.out_degree[i] > 65535) {
-            why = "the resident engine holds rows of at most 65535 synapses";
+    // segment lengths, [block][sender]
+    std::vector<uint32_t> len(static_cast<size_t>(B) * n, 0);
+    parallel_for(nthreads, n, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t i = lo; i < hi; ++i)
+            for (int64_t s = net.row_ptr[i], e = s + net.out_degree[i]; s < e; ++s)
+                ++len[static_cast<size_t>(net.tgt[s] / width) * n + i];
+    });
+    const ResTables T = resident_tables(n, B);
+    net.restab.assign(T.total, 0);
+    int64_t *rbase = reinterpret_cast<int64_t *>(net.restab.data() + T.rbase);
+    uint32_t *coarse = reinterpret_cast<uint32_t *>(net.restab.data() + T.coarse);
+    uint8_t *lens = net.restab.data() + T.lens;
+    uint32_t *offt = reinterpret_cast<uint32_t *>(net.restab.data() + T.offt);
+    rbase[0] = 0;
+    for (int b = 0; b < B; ++b) {
+        uint64_t run = 0;
+        const uint32_t *lb = &len[static_cast<size_t>(b) * n];
+        uint32_t *ob = offt + static_cast<size_t>(b) * (n + 1);
+        uint32_t *cb = coarse + static_cast<size_t>(b) * T.coarse_stride;
+        uint8_t *lnb = lens + static_cast<size_t>(b) * T.lens_stride;
+        for (int64_t i = 0; i < n; ++i) {
+            if (i % 32 == 0) cb[i / 32] = static_cast<uint32_t>(run);
+            ob[i] = static_cast<uint32_t>(run);
+            lnb[i] = static_cast<uint8_t>(std::min<uint32_t>(lb[i], kResidentEscape));
+            if (lb[i] >= kResidentEscape) cb[i / 32] |= kResidentGroupFlag;
+            run += lb[i];
+        }
+        if (run >= kResidentGroupFlag) {
+            why = "a target block receives more than 2^31 synapses";
             return false;
         }
-    net.segt.assign(static_cast<size_t>(n) * B, 0);
+        ob[n] = static_cast<uint32_t>(run);
+        cb[(n + 31) / 32] = static_cast<uint32_t>(run);
+        rbase[b + 1] = rbase[b] + static_cast<int64_t>(run);
+    }
+    const int64_t S = rbase[B];
+    std::vector<int32_t> t2(S), w2(S);
+    std::vector<uint8_t> d2(S);
     parallel_for(nthreads, n, [&](int, int64_t lo, int64_t hi) {
-        std::vector<int64_t> pos(B + 1);
-        std::vector<int32_t> t2, w2;
-        std::vector<uint8_t> d2;
+        std::vector<int64_t> pos(B);
         for (int64_t i = lo; i < hi; ++i) {
-            const int64_t rs = net.row_ptr[i], len = net.out_degree[i];
-            std::fill(pos.begin(), pos.end(), 0);
-            for (int64_t s = rs; s < rs + len; ++s) ++pos[net.tgt[s] / width + 1];
-            for (int b = 0; b < B; ++b) pos[b + 1] += pos[b];
-            for (int b = 0; b < B; ++b)
-                net.segt[static_cast<size_t>(b) * n + i] =
-                    static_cast<uint32_t>(pos[b]) | static_cast<uint32_t>(pos[b + 1] - pos[b]) << 16;
-            t2.resize(len);
-            w2.resize(len);
-            d2.resize(len);
-            for (int64_t s = rs; s < rs + len; ++s) {
+            for (int b = 0; b < B; ++b) pos[b] = rbase[b] + offt[static_cast<size_t>(b) * (n + 1) + i];
+            for (int64_t s = net.row_ptr[i], e = s + net.out_degree[i]; s < e; ++s) {
                 const int64_t dst = pos[net.tgt[s] / width]++;
                 t2[dst] = net.tgt[s];
                 w2[dst] = net.w[s];
                 d2[dst] = net.d[s];
             }
-            std::copy(t2.begin(), t2.end(), net.tgt.begin() + rs);
-            std::copy(w2.begin(), w2.end(), net.w.begin() + rs);
-            std::copy(d2.begin(), d2.end(), net.d.begin() + rs);
         }
     });
+    net.tgt = std::move(t2);
+    net.w = std::move(w2);
+    net.d = std::move(d2);
+    for (int64_t i = 0; i < n; ++i) net.row_ptr[i + 1] = net.row_ptr[i] + net.out_degree[i];
+    net.n_syn_padded = S;
     return true;
 }
 
@@ -695,7 +718,7 @@ bool build_host_network(const snn_spec &spec, const Constants &c, HostNetwork &n
                 why = "more neurons than the resident engine holds on this GPU (1024 per SM)";
                 return false;
             }
-            if (!group_rows_by_block(net, width, resolve_threads(spec.n_threads), why)) return false;
+            if (!block_major_records(net, width, resolve_threads(spec.n_threads), why)) return false;
         }
         return true;
     }

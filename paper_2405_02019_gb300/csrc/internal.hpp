@@ -110,15 +110,44 @@ inline int max_target_blocks(int64_t n)
 constexpr int kResidentMaxWidth = 1024;      // neurons per block (8 neuron warps x 128)
 constexpr int kResidentMaxBlocks = 256;      // blocks (CTAs, at most one per SM)
 constexpr int kResidentAlign = 32;           // block boundaries are multiples of 32
-constexpr int kResidentDeliverWarps = 8;     // delivery warps per CTA (default)
-constexpr int kResidentMboxWords = kResidentMaxWidth + 2;  // u64 words of one outbox: header, entries, pad
-constexpr int kResidentSlotWords = 4;        // u64 words of one inbox slot: header and three entries
+constexpr int kResidentMaxWarps = 16;        // neuron warps + delivery warps per CTA
+constexpr int kResidentTeamWarps = 4;        // delivery warps per team (at least; two teams)
+constexpr int kResidentMboxWords = kResidentMaxWidth + 4;  // u32 words of one outbox (entries of a step)
+constexpr int kResidentSlotWords = 4;        // u32 words of one inbox slot: header and three entries
 constexpr int64_t kResidentMaxSteps = int64_t{1} << 19;     // steps per launch (mailbox tags count them)
-constexpr int kResidentGather = 1024;        // spikes of a step staged in shared memory per pass
+constexpr int kResidentGather = 256;         // spikes of a step staged in shared memory per pass
 constexpr int64_t kResidentMaxNeurons = int64_t{kResidentMaxBlocks} * kResidentMaxWidth;
+constexpr uint32_t kResidentEscape = 255;    // segment length code: 255 or more, read the exact offsets
+constexpr uint32_t kResidentGroupFlag = 1u << 31;  // a group of 32 senders holds an escaped length
 inline int resident_max_blocks(int64_t n)
 {
     return static_cast<int>(std::min<int64_t>(kResidentMaxBlocks, (n + kResidentAlign - 1) / kResidentAlign));
+}
+
+// Resident engine: the records are stored block-major -- every synapse into target block
+// p, by sender and then delay, forms block p's region starting at record rbase[p] -- and
+// each block has its segment tables: offt[p][s] (uint32, offset of sender s's segment in
+// the region, offt[p][n] the region's length), lens[p][s] = min(length, 255) (uint8) and
+// coarse[p][g] = offt[p][32 g] with kResidentGroupFlag set if one of the group's lengths
+// is escaped.  A CTA keeps its lens and coarse rows in shared memory.  This gives the
+// tables' byte offsets within their arena region.
+struct ResTables {
+    uint64_t rbase, coarse, lens, offt, total;
+    int64_t lens_stride, coarse_stride;
+};
+inline ResTables resident_tables(int64_t n, int64_t blocks)
+{
+    auto up = [](uint64_t x) { return (x + 255) & ~uint64_t{255}; };
+    ResTables t{};
+    t.lens_stride = (n + 31) / 32 * 32;
+    t.coarse_stride = (n + 31) / 32 + 1;
+    uint64_t o = 0;
+    t.rbase = o; o = up(o + 8 * uint64_t(blocks + 1));
+    t.coarse = o; o = up(o + 4 * uint64_t(blocks) * t.coarse_stride);
+    t.lens = o; o = up(o + uint64_t(blocks) * t.lens_stride);
+    t.offt = o; o = up(o + 4 * uint64_t(blocks) * (n + 1));
+    t.total = o;
+    return t;
 }
 
 // Kernel arguments (by value; small).
@@ -167,9 +196,14 @@ struct StepArgs {
     int32_t pad4;
     int64_t quad_base;            // first quad the update (or step) launch covers, n its end neuron
     int64_t queue_cap;            // pipelined engine: entries of each queue (a circuit group's neurons)
-    uint64_t *mbox;               // resident engine: outboxes [4][n_blocks][kResidentMboxWords]
-    uint64_t *inbox;              // resident engine: inbox slots [4][n_blocks (reader)][n_blocks (sender)][4]
-    const uint32_t *res_segt;     // resident engine: [n_blocks][n] segment start | length << 16 within a row
+    uint32_t *mbox;               // resident engine: outboxes [4][n_blocks][kResidentMboxWords]
+    uint32_t *inbox;              // resident engine: inbox slots [4][n_blocks (reader)][n_blocks (sender)][4]
+    const int64_t *res_rbase;     // resident engine: first record of every block's region [n_blocks + 1]
+    const uint32_t *res_coarse;   // resident engine: [n_blocks][coarse_stride] (see resident_tables)
+    const uint8_t *res_lens;      // resident engine: [n_blocks][lens_stride]
+    const uint32_t *res_offt;     // resident engine: [n_blocks][n + 1]
+    int32_t res_lens_stride;
+    int32_t res_coarse_stride;
     int32_t res_rows;             // resident engine: ring rows kept in shared memory (power of two, 8..64)
     int32_t res_stride;           // resident engine: shared ring row stride (widest block, multiple of 32)
 };
@@ -207,7 +241,7 @@ struct HostNetwork {
     std::vector<int32_t> blk;      // blocked records: block boundaries
     std::vector<uint16_t> rec16;   // blocked records: local target | delay << 10
     std::vector<uint16_t> seg;     // blocked records: [n][blocks + 1] block starts per row
-    std::vector<uint32_t> segt;    // resident engine: [blocks][n] segment start | length << 16 within each row
+    std::vector<uint8_t> restab;   // resident engine: the tables of resident_tables(n, blocks), as bytes
 };
 
 // Arena layout for a spec.
@@ -257,10 +291,10 @@ int step_threads(const StepArgs &a);
 // Block width of the resident engine for n neurons on num_sms SMs (a multiple of
 // kResidentAlign; 0 if n does not fit kResidentMaxWidth per SM).
 int64_t resident_width(int64_t n, int num_sms);
-size_t resident_smem_bytes(int rows, int stride);
+size_t resident_smem_bytes(int rows, int stride, int64_t n);
 // Ring rows in shared memory: the largest power of two in [8, 64] (at most `cap` when
 // cap > 0) whose shared memory fits one CTA; 0 if none fits.
-int resident_rows(int stride, int cap);
+int resident_rows(int stride, int cap, int64_t n);
 int prepare_resident_kernel(const StepArgs &a);
 int resident_blocks_per_sm(const StepArgs &a);
 // n_steps steps from the device's t_base in one cooperative launch of a.n_blocks CTAs

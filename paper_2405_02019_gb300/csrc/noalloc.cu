@@ -214,6 +214,8 @@ extern "C" int snn_step_static(const snn_net *net, const snn_static_io *io, uint
     if (info.record_format != SNN_RECORD_PLAIN9)
         return static_fail(SNN_ENOTSUP, "snn_step_static: only plain synapse records are supported");
     if (info.n_circuits != 1) return static_fail(SNN_ENOTSUP, "snn_step_static: batched networks are not supported");
+    if (info.engine == SNN_ENGINE_RESIDENT)
+        return static_fail(SNN_ENOTSUP, "snn_step_static: the resident engine's records are block-major, not rows");
     if (info.n_neurons > SNN_STATIC_MAX_NEURONS)
         return static_fail(SNN_EINVAL,
                            "snn_step_static: network has more neurons than the static scratch holds "

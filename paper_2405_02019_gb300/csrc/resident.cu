@@ -8,14 +8,15 @@
 //     memory (all 64 rows when they fit; otherwise the rows of delays below `rows` sit in
 //     shared memory and longer delays go to the ring in global memory, which only this
 //     CTA reads or writes for these columns);
-//   - each sender's row is stored grouped by target block (delay order kept inside a
-//     block), and the CTA's own row of a segment table says where each row's segment into
-//     its block starts and how long it is, so the CTA reads only the synapses that land
-//     in its block (the indexed store of §3.5 split by target).
+//   - the records are stored block-major: every synapse into the block, sender by
+//     sender and each sender's segment in delay order, forms one region (the indexed
+//     store of §3.5 split by target), and the CTA keeps the block's segment lengths
+//     (8 bits) and one offset per 32 senders in shared memory, so it finds a spike's
+//     segment without touching global memory.
 // The only traffic between CTAs is the spike list of every step.  After deciding its
-// spikes, a CTA writes, into one 32-byte inbox slot per reading CTA, the step's spike
-// count and up to three spikes (its index in the block and the row's offset); further
-// spikes go once into its outbox.  Each CTA thus polls only lines that it alone reads.
+// spikes, a CTA writes, into one 16-byte inbox slot per reading CTA, the step's spike
+// count and up to three spikes (their index in the block); further spikes go once into
+// its outbox.  Each CTA thus polls only lines that it alone reads.
 // It then adds its segments of those rows into its shared ring with shared-memory integer
 // atomics (order-independent, so the raster stays bit-exact).  Every mailbox word carries
 // the step's rank in the launch, so a reader tells a fresh word from an old one without
@@ -45,8 +46,10 @@ namespace snn {
 
 namespace {
 
-constexpr int kResidentMaxThreads = 32 * (kResidentMaxWidth / 128 + 8);  // neuron + delivery warps
-constexpr int kResU = 4;  // synapses in flight per lane of a delivery warp
+constexpr int kResidentMaxThreads = 32 * kResidentMaxWarps;  // neuron warps + two delivery teams
+constexpr int kResU = 8;  // synapses in flight per lane of a delivery warp
+constexpr int kJmapShift = 5;  // the flattened synapse list in chunks of 32 ...
+constexpr int kJmap = 256;     // ... the first kJmap of which map to the spike holding their first synapse
 
 __device__ __forceinline__ uint64_t global_ns()
 {
@@ -55,27 +58,24 @@ __device__ __forceinline__ uint64_t global_ns()
     return v;
 }
 
-__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v)
+__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v)
 {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ void st_relaxed_v2u64(uint64_t *p, uint64_t x, uint64_t y)
+__device__ __forceinline__ void st_relaxed_v4u32(uint32_t *p, uint32_t x, uint32_t y, uint32_t z, uint32_t w)
 {
-    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(x), "l"(y) : "memory");
+    asm volatile("st.relaxed.gpu.global.v4.u32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(x), "r"(y), "r"(z), "r"(w)
+                 : "memory");
 }
 
-__device__ __forceinline__ ulonglong2 ld_relaxed_v2u64(const uint64_t *p)
+__device__ __forceinline__ uint4 ld_relaxed_v4u32(const uint32_t *p)
 {
-    ulonglong2 v;
-    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p)
-{
-    uint64_t v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    uint4 v;
+    asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p)
+                 : "memory");
     return v;
 }
 
@@ -113,11 +113,6 @@ __device__ __forceinline__ void red_add_s32(int32_t *addr, int32_t v)
     asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(addr), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 // Barrier among the `n` threads of one warp group (ids 1 and 2; 0 is __syncthreads).
 __device__ __forceinline__ void group_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
@@ -136,51 +131,45 @@ __device__ __forceinline__ bool group_sync_or(int id, int n, bool v)
 
 // Shared memory of one CTA, in bytes from the start of the dynamic allocation.
 struct ResLayout {
-    size_t ring, thr, base, wsum, own, glist, misc, total;
+    size_t ring, lens, coarse, thr, base, wsum, own, glist, sstart, soff, jmap, misc, total;
 };
 
 __host__ __device__ constexpr size_t res_up16(size_t x) { return (x + 15) & ~size_t{15}; }
 
-__host__ __device__ inline ResLayout res_layout(int rows, int stride)
+__host__ __device__ inline ResLayout res_layout(int rows, int stride, int lens_stride, int coarse_stride)
 {
     ResLayout L{};
     L.ring = 0;                                                                   // int32 [rows][stride]
-    L.thr = res_up16(L.ring + sizeof(int32_t) * size_t(rows) * stride);           // u64 [8][24]
+    L.lens = res_up16(L.ring + sizeof(int32_t) * size_t(rows) * stride);          // u8 [lens_stride]
+    L.coarse = res_up16(L.lens + size_t(lens_stride));                            // u32 [coarse_stride]
+    L.thr = res_up16(L.coarse + sizeof(uint32_t) * size_t(coarse_stride));        // u64 [8][24]
     L.base = res_up16(L.thr + sizeof(uint64_t) * SNN_MAX_POPS * kPK);             // int32 [blocks + 1]
-    L.wsum = res_up16(L.base + sizeof(int32_t) * (kResidentMaxBlocks + 1));       // int32 [16] warp sums
-    L.own = res_up16(L.wsum + sizeof(int32_t) * 16);                              // u64 [2][stride]
-    L.glist = res_up16(L.own + sizeof(uint64_t) * 2 * stride);                    // u64 [gather]
-    L.misc = res_up16(L.glist + sizeof(uint64_t) * kResidentGather);              // counters and flags
+    L.wsum = res_up16(L.base + sizeof(int32_t) * (kResidentMaxBlocks + 1));       // int32 [2 teams][16] warp sums
+    L.own = res_up16(L.wsum + sizeof(int32_t) * 2 * 16);                          // u16 [2][stride]
+    L.glist = res_up16(L.own + sizeof(uint16_t) * 2 * stride);                    // int32 [2 teams][gather]
+    L.sstart = res_up16(L.glist + sizeof(int32_t) * 2 * kResidentGather);         // u32 [2][gather] segment starts
+    L.soff = res_up16(L.sstart + sizeof(uint32_t) * 2 * kResidentGather);         // u32 [2][gather] flattened offsets
+    L.jmap = res_up16(L.soff + sizeof(uint32_t) * 2 * kResidentGather);           // u16 [2][kJmap] chunk -> spike
+    L.misc = res_up16(L.jmap + sizeof(uint16_t) * 2 * kJmap);                     // counters and flags
     L.total = res_up16(L.misc + 64);
     return L;
 }
 
 struct ResMisc {
     uint32_t own_cnt[2];  // neuron warps: own spikes of the step with parity s, in own[s & 1]
-    uint32_t d_done;      // steps of this launch whose delivery into the shared ring is complete
-    uint32_t abort;       // a bounded wait timed out: both warp groups leave their loops
+    uint32_t d_done[2];   // per delivery team: rank in the launch of its last step delivered into the ring
+    uint32_t abort;       // a bounded wait timed out: every warp group leaves its loop
+    uint32_t cur_tag[4];  // raster cursor at the start of the step with rank r, in slot r & 3 ...
+    uint32_t cur_val[4];  // ... tagged with r (written by the team that delivered the step before)
 };
 
-// Mailbox words (64-bit, so that a word is read whole) carry the step's rank in the
-// launch in their low half: a header its low 20 bits above the 12-bit spike count, an
-// entry its low 22 bits above the sender's 10-bit index in its block, with the first quad
-// of the sender's row (row offset / 4) in the high half.
+// Mailbox words carry the step's rank in the launch: a header its low 20 bits above the
+// 12-bit spike count, an entry its low 22 bits above the sender's 10-bit index in its
+// block.  Every word is read whole, so each one tells by itself whether it is fresh.
 constexpr uint32_t kHeaderTagMask = (1u << 20) - 1;
 constexpr uint32_t kEntryTagMask = (1u << 22) - 1;
 
-__device__ __forceinline__ bool entry_ok(uint64_t v, uint32_t etag) { return (static_cast<uint32_t>(v) >> 10) == etag; }
-
-// Largest k in [0, 32) with off_k <= e, for off nondecreasing over the lanes (off_0 = 0).
-__device__ __forceinline__ int lane_of(int off, int e)
-{
-    int k = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-        const int ov = __shfl_sync(0xFFFFFFFFu, off, k + step);
-        if (ov <= e) k += step;
-    }
-    return k;
-}
+__device__ __forceinline__ bool entry_ok(uint32_t v, uint32_t etag) { return (v >> 10) == etag; }
 
 __device__ __forceinline__ uint32_t poisson_count_s(uint64_t v, const uint64_t (&r)[8], const uint64_t *thr_row)
 {
@@ -194,13 +183,13 @@ __device__ __forceinline__ uint32_t poisson_count_s(uint64_t v, const uint64_t (
 
 // Waits until mailbox entry `word` carries tag `etag`; false if the wait ran past the
 // bound or another CTA recorded a timeout.
-__device__ __forceinline__ bool wait_entry(const uint64_t *word, uint32_t etag, uint64_t &v, const StepArgs &a)
+__device__ __forceinline__ bool wait_entry(const uint32_t *word, uint32_t etag, uint32_t &v, const StepArgs &a)
 {
-    v = ld_relaxed_u64(word);
+    v = ld_relaxed_u32(word);
     if (entry_ok(v, etag)) return true;
     const uint64_t t_start = global_ns();
     for (uint32_t spins = 1;; ++spins) {
-        v = ld_relaxed_u64(word);
+        v = ld_relaxed_u32(word);
         if (entry_ok(v, etag)) return true;
         if ((spins & 31u) == 0) {
             if (global_ns() - t_start > a.barrier_timeout_ns) return false;
@@ -214,13 +203,18 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
     extern __shared__ int4 res_smem4[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(res_smem4);
     const int rows = a.res_rows, stride = a.res_stride;
-    const ResLayout SL = res_layout(rows, stride);
+    const ResLayout SL = res_layout(rows, stride, a.res_lens_stride, a.res_coarse_stride);
     int32_t *s_ring = reinterpret_cast<int32_t *>(sm + SL.ring);
+    uint8_t *s_lens = sm + SL.lens;
+    uint32_t *s_coarse = reinterpret_cast<uint32_t *>(sm + SL.coarse);
     uint64_t *s_thr = reinterpret_cast<uint64_t *>(sm + SL.thr);
     int32_t *s_base = reinterpret_cast<int32_t *>(sm + SL.base);
     int32_t *s_wsum = reinterpret_cast<int32_t *>(sm + SL.wsum);
-    uint64_t *s_own = reinterpret_cast<uint64_t *>(sm + SL.own);
-    uint64_t *s_glist = reinterpret_cast<uint64_t *>(sm + SL.glist);
+    uint16_t *s_own = reinterpret_cast<uint16_t *>(sm + SL.own);
+    int32_t *s_glist = reinterpret_cast<int32_t *>(sm + SL.glist);
+    uint32_t *s_sstart = reinterpret_cast<uint32_t *>(sm + SL.sstart);
+    uint32_t *s_soff = reinterpret_cast<uint32_t *>(sm + SL.soff);
+    uint16_t *s_jmap = reinterpret_cast<uint16_t *>(sm + SL.jmap);
     ResMisc *s_misc = reinterpret_cast<ResMisc *>(sm + SL.misc);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -237,14 +231,26 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
     const int32_t wpad = (width + 3) & ~3;
     const int64_t npad = a.npad;
 
-    // ---- set-up: tables, block bounds, the block's ring columns ----
+    // ---- set-up: tables, block bounds, the block's segment tables and ring columns ----
     for (int j = threadIdx.x; j < SNN_MAX_POPS * kPK; j += blockDim.x) s_thr[j] = (&a.tables->thresholds[0][0])[j];
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(a.res_lens + static_cast<int64_t>(p) * a.res_lens_stride);
+        for (int j = threadIdx.x; j < a.res_lens_stride / 16; j += blockDim.x)
+            reinterpret_cast<int4 *>(s_lens)[j] = __ldcg(src + j);
+        const uint32_t *cs = a.res_coarse + static_cast<int64_t>(p) * a.res_coarse_stride;
+        for (int j = threadIdx.x; j < a.res_coarse_stride; j += blockDim.x) s_coarse[j] = __ldcg(cs + j);
+    }
+    const int64_t rbase = __ldg(a.res_rbase + p);  // first record of this block's region
     for (int j = threadIdx.x; j <= B; j += blockDim.x) s_base[j] = __ldg(a.blk_off + j);
     if (threadIdx.x == 0) {
         s_misc->own_cnt[0] = 0;
         s_misc->own_cnt[1] = 0;
-        s_misc->d_done = 0;
+        s_misc->d_done[0] = 0;
+        s_misc->d_done[1] = 0;
         s_misc->abort = 0;
+        for (int k = 0; k < 4; ++k) s_misc->cur_tag[k] = 0;
+        s_misc->cur_val[1] = ctl->cursor;  // the first step has rank 1
+        s_misc->cur_tag[1] = 1;
     }
     // shared row r holds the ring row of the step in [t0, t0 + rows) congruent to r
     for (int idx = threadIdx.x; idx < rows * (stride >> 2); idx += blockDim.x) {
@@ -273,7 +279,6 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
         // ====== neuron warps: B(t), then A(t+1), the mailboxes of step t+1 and its draws ======
         uint32_t pops = 0;
         int b0 = 0;
-        int64_t rp[5] = {0, 0, 0, 0, 0};
         uint64_t tr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int32_t thal[4] = {0, 0, 0, 0};    // thalamic input T w_ext of the next B, drawn ahead of time
         int4 gw4 = make_int4(0, 0, 0, 0);  // global ring row of the next B (rows < 64 only)
@@ -287,8 +292,6 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
             pops = __ldg(reinterpret_cast<const unsigned int *>(a.pop_id + g0));
             b0 = pops & 0xFF;
 #pragma unroll
-            for (int j = 0; j < 5; ++j) rp[j] = __ldg(a.row_ptr + g0 + j);
-#pragma unroll
             for (int k = 0; k < 8; ++k) tr[k] = s_thr[b0 * kPK + k];
         }
         for (int64_t t = t0 - 1; t < tend; ++t) {
@@ -299,11 +302,15 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                     // the list of step t+1 starts empty (its last reader, the mailbox of step
                     // t-1, was written by this thread's own warp)
                     s_misc->own_cnt[(t + 1) & 1] = 0;
-                    const uint32_t need = static_cast<uint32_t>(t - t0);
-                    if (ld_acquire_shared(&s_misc->d_done) < need) {
+                    // D(t-1) and D(t-2) come from different teams; each team delivers its
+                    // steps in order, so these two bound every earlier step as well
+                    const uint32_t r1 = static_cast<uint32_t>(t - t0);  // rank of step t-1 (0: none)
+                    const uint32_t need_a = r1, need_b = r1 > 1 ? r1 - 1 : 0;
+                    uint32_t *done_a = &s_misc->d_done[(r1 + 1) & 1], *done_b = &s_misc->d_done[r1 & 1];
+                    if (ld_acquire_shared(done_a) < need_a || ld_acquire_shared(done_b) < need_b) {
                         const uint64_t t_start = global_ns();
                         for (uint32_t spins = 1;; ++spins) {
-                            if (ld_acquire_shared(&s_misc->d_done) >= need) break;
+                            if (ld_acquire_shared(done_a) >= need_a && ld_acquire_shared(done_b) >= need_b) break;
                             if (ld_volatile_shared(&s_misc->abort)) {
                                 stop = true;
                                 break;
@@ -357,7 +364,7 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                     }
                 }
             }
-            // the block's spikes of step t+1 (index in the block | first row quad << 32)
+            // the block's spikes of step t+1 (index in the block)
             const int par = static_cast<int>((t + 1) & 1);
             const int cnt = spk[0] + spk[1] + spk[2] + spk[3];
             if (__ballot_sync(0xFFFFFFFFu, cnt != 0)) {
@@ -373,18 +380,8 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                 wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
                 int k = static_cast<int>(wbase) + incl - cnt;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (!spk[j]) continue;
-                    const int64_t rs = rp[j], re = rp[j + 1];
-                    s_own[par * stride + k++] = static_cast<uint64_t>(i0 + j) | static_cast<uint64_t>(rs >> 2) << 32;
-                    // every CTA reads its segment of the row soon: bring the row into L2 now
-                    if (re > rs) {
-                        prefetch_l2(a.syn_tgt + rs, static_cast<uint32_t>(4 * (re - rs)));
-                        prefetch_l2(a.syn_w + rs, static_cast<uint32_t>(4 * (re - rs)));
-                        const int64_t d0 = rs & ~int64_t{15}, d1 = (re + 15) & ~int64_t{15};
-                        prefetch_l2(a.syn_d + d0, static_cast<uint32_t>(d1 - d0));
-                    }
-                }
+                for (int j = 0; j < 4; ++j)
+                    if (spk[j]) s_own[par * stride + k++] = static_cast<uint16_t>(i0 + j);
             }
             group_sync(1, NW * 32);
             if (warp == 0) {
@@ -392,23 +389,20 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                 // three spikes), the other spikes once in this CTA's outbox
                 const uint32_t rel = static_cast<uint32_t>(t + 1 - t0 + 1);
                 const uint32_t n_own = s_misc->own_cnt[par];
-                const uint64_t etag = static_cast<uint64_t>((rel & kEntryTagMask) << 10);
-                const uint64_t *own = s_own + par * stride;
+                const uint32_t etag = (rel & kEntryTagMask) << 10;
+                const uint16_t *own = s_own + par * stride;
                 const size_t buf = static_cast<size_t>((t + 1) & 3);
-                uint64_t *ob = a.mbox + (buf * B + p) * kResidentMboxWords;
-                for (uint32_t j = 3 + lane; j < n_own; j += 32) st_relaxed_u64(ob + j, etag | own[j]);
-                const uint64_t h = ((rel & kHeaderTagMask) << 12) | n_own;
-                const uint64_t e0 = n_own > 0 ? (etag | own[0]) : 0, e1 = n_own > 1 ? (etag | own[1]) : 0;
-                const uint64_t e2 = n_own > 2 ? (etag | own[2]) : 0;
+                uint32_t *ob = a.mbox + (buf * B + p) * kResidentMboxWords;
+                for (uint32_t j = 3 + lane; j < n_own; j += 32) st_relaxed_u32(ob + j, etag | own[j]);
+                const uint32_t h = ((rel & kHeaderTagMask) << 12) | n_own;
+                const uint32_t e0 = n_own > 0 ? (etag | own[0]) : 0u, e1 = n_own > 1 ? (etag | own[1]) : 0u;
+                const uint32_t e2 = n_own > 2 ? (etag | own[2]) : 0u;
                 // B(t) of every neuron warp (ordered by the group barrier) before the slots:
                 // this CTA's own delivery of step t+1 adds into ring row t with d = 63
                 __threadfence_block();
-                uint64_t *slots = a.inbox + (buf * B * B + p) * kResidentSlotWords;  // reader c's slot: + c * B * 4
-                for (int c = lane; c < B; c += 32) {
-                    uint64_t *sl = slots + static_cast<size_t>(c) * B * kResidentSlotWords;
-                    st_relaxed_v2u64(sl, h, e0);
-                    if (n_own > 1) st_relaxed_v2u64(sl + 2, e1, e2);
-                }
+                uint32_t *slots = a.inbox + (buf * B * B + p) * kResidentSlotWords;  // reader c's slot: + c * B * 4
+                for (int c = lane; c < B; c += 32)
+                    st_relaxed_v4u32(slots + static_cast<size_t>(c) * B * kResidentSlotWords, h, e0, e1, e2);
             }
             if (active) {
                 // thalamic input of step t+1 (counter-based: independent of the dynamics)
@@ -441,38 +435,46 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
             }
         }
     } else {
-        // ====== delivery warps: D(t) for every step, as soon as every slot of step t is written ======
+        // ====== delivery warps: two teams, each delivering every other step as soon as
+        // every slot of that step is written, so that consecutive steps overlap ======
         const int dw = warp - NW;
-        const int ql = dw * 32 + lane;  // the sender whose slot this lane polls
-        uint32_t cursor = ctl->cursor;
+        const int TW = DW >> 1;         // warps per team
+        const int team = dw / TW;       // team k delivers the steps of rank k+1, k+3, ...
+        const int tw = dw - team * TW;  // warp within the team
+        const int ql = tw * 32 + lane;  // the sender whose slot this lane polls
+        const int bar = 2 + team, nbar = TW * 32;
+        int32_t *t_wsum = s_wsum + team * 16;
+        int32_t *t_glist = s_glist + team * kResidentGather;
+        uint32_t *t_sstart = s_sstart + team * kResidentGather;
+        uint32_t *t_soff = s_soff + team * kResidentGather;
+        uint16_t *t_jmap = s_jmap + team * kJmap;
         const bool stall_test = a.barrier_extra != 0 && p == 0;  // waits for a tag nobody writes
-        for (int64_t t = t0; t < tend; ++t) {
+        for (int64_t t = t0 + team; t < tend; t += 2) {
             const uint32_t rel = static_cast<uint32_t>(t - t0 + 1);
             const uint32_t htag = stall_test ? kHeaderTagMask : (rel & kHeaderTagMask);
             const uint32_t etag = rel & kEntryTagMask;
-            if (!full_ring && (t & ((rows >> 1) - 1)) == 0) __threadfence();  // earlier long-delay adds visible
+            if (!full_ring) __threadfence();  // this lane's earlier long-delay adds are visible
             const size_t buf = static_cast<size_t>(t & 3);
             uint32_t cnt = 0;
-            ulonglong2 h = make_ulonglong2(0, 0), e = make_ulonglong2(0, 0);
+            uint4 h = make_uint4(0, 0, 0, 0);
             bool ok = true;
             if (ql < B) {
-                const uint64_t *sl = a.inbox + ((buf * B + p) * B + ql) * kResidentSlotWords;
-                h = ld_relaxed_v2u64(sl);
-                e = ld_relaxed_v2u64(sl + 2);
-                if ((static_cast<uint32_t>(h.x) >> 12) != htag) {
+                const uint32_t *sl = a.inbox + ((buf * B + p) * B + ql) * kResidentSlotWords;
+                h = ld_relaxed_v4u32(sl);
+                if ((h.x >> 12) != htag) {
                     const uint64_t t_start = global_ns();
                     for (uint32_t spins = 1;; ++spins) {
-                        h = ld_relaxed_v2u64(sl);
-                        e = ld_relaxed_v2u64(sl + 2);
-                        if ((static_cast<uint32_t>(h.x) >> 12) == htag) break;
+                        h = ld_relaxed_v4u32(sl);
+                        if ((h.x >> 12) == htag) break;
                         if ((spins & 31u) == 0 && (global_ns() - t_start > a.barrier_timeout_ns ||
-                                                   (ld_relaxed_u32(&ctl->err) & kErrTimeout))) {
+                                                   (ld_relaxed_u32(&ctl->err) & kErrTimeout) ||
+                                                   ld_volatile_shared(&s_misc->abort))) {
                             ok = false;
                             break;
                         }
                     }
                 }
-                if (ok) cnt = static_cast<uint32_t>(h.x) & 0xFFFu;
+                if (ok) cnt = h.x & 0xFFFu;
                 if (ql == p) __threadfence_block();  // pairs with the fence before this CTA's own slots
             }
             if (!ok) atomicOr(&ctl->err, kErrTimeout);
@@ -483,31 +485,52 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                 const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
                 if (lane >= o) incl += v;
             }
-            if (lane == 31) s_wsum[dw] = incl;
-            if (group_sync_or(2, DW * 32, !ok)) {
-                if (dw == 0 && lane == 0) st_volatile_shared(&s_misc->abort, 1u);
+            if (lane == 31) t_wsum[tw] = incl;
+            if (group_sync_or(bar, nbar, !ok)) {
+                if (tw == 0 && lane == 0) st_volatile_shared(&s_misc->abort, 1u);
                 break;
             }
             int before = 0, total = 0;
-            for (int w = 0; w < DW; ++w) {
-                const int v = s_wsum[w];
-                before += w < dw ? v : 0;
+            for (int w = 0; w < TW; ++w) {
+                const int v = t_wsum[w];
+                before += w < tw ? v : 0;
                 total += v;
             }
             const int off = before + incl - static_cast<int>(cnt);
-            bool late = false;  // a spike entry never arrived
+            // the raster cursor at this step: left by the team of the step before
+            uint32_t cursor = 0;
+            bool late = false;  // a wait (spike entry or cursor) gave up
+            if (ql == p || (tw == 0 && lane == 0)) {
+                const uint32_t slot = rel & 3;
+                if (ld_acquire_shared(&s_misc->cur_tag[slot]) != rel) {
+                    const uint64_t t_start = global_ns();
+                    for (uint32_t spins = 1;; ++spins) {
+                        if (ld_acquire_shared(&s_misc->cur_tag[slot]) == rel) break;
+                        if ((spins & 255u) == 0 && (global_ns() - t_start > a.barrier_timeout_ns ||
+                                                    ld_volatile_shared(&s_misc->abort))) {
+                            late = true;
+                            break;
+                        }
+                    }
+                }
+                cursor = s_misc->cur_val[slot];
+                if (tw == 0 && lane == 0 && !late) {
+                    s_misc->cur_val[(rel + 1) & 3] = cursor + static_cast<uint32_t>(total);
+                    st_release_shared(&s_misc->cur_tag[(rel + 1) & 3], rel + 1);
+                }
+            }
             for (int lo = 0; lo < total; lo += kResidentGather) {
                 const int m = total - lo < kResidentGather ? total - lo : kResidentGather;
-                // spikes lo .. lo + m of the step into the gather list (global index | row quad
-                // << 32); a slot's entries may predate its header, so each is checked
+                // spikes lo .. lo + m of the step into the gather list; a slot's entries may
+                // predate its header, so each is checked
                 if (cnt > 0) {
                     const int j0 = lo > off ? lo - off : 0;
                     const int j1 = min(static_cast<int>(cnt), lo + m - off);
-                    const uint64_t *sl = a.inbox + ((buf * B + p) * B + ql) * kResidentSlotWords;
-                    const uint64_t *ob = a.mbox + (buf * B + ql) * kResidentMboxWords;
+                    const uint32_t *sl = a.inbox + ((buf * B + p) * B + ql) * kResidentSlotWords;
+                    const uint32_t *ob = a.mbox + (buf * B + ql) * kResidentMboxWords;
                     const int32_t src_base = s_base[ql];
                     for (int j = j0; j < j1; ++j) {
-                        uint64_t v = j == 0 ? h.y : j == 1 ? e.x : e.y;
+                        uint32_t v = j == 0 ? h.y : j == 1 ? h.z : h.w;
                         if (j >= 3 || !entry_ok(v, etag)) {
                             if (!wait_entry(j < 3 ? sl + 1 + j : ob + j, etag, v, a)) {
                                 atomicOr(&ctl->err, kErrTimeout);
@@ -516,7 +539,7 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                             }
                         }
                         const int32_t s_id = src_base + static_cast<int32_t>(v & 0x3FFu);
-                        s_glist[off + j - lo] = static_cast<uint32_t>(s_id) | (v & 0xFFFFFFFF00000000ull);
+                        t_glist[off + j - lo] = s_id;
                         if (ql == p) {
                             // this CTA's own spikes of step t go into the raster, in slot order
                             const uint64_t pos = static_cast<uint64_t>(cursor) + static_cast<uint64_t>(off + j);
@@ -527,78 +550,134 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                         }
                     }
                 }
-                group_sync(2, DW * 32);
-                // warp dw takes spikes dw, dw + DW, ...; lane k of a round the (k+1)-th of them
-                for (int jb = dw; jb < m; jb += DW * 32) {
-                    const int j = jb + DW * lane;
-                    int64_t start = 0;
-                    int len = 0;
-                    if (j < m) {
-                        const uint64_t g = s_glist[j];
-                        const uint32_t s = static_cast<uint32_t>(g);
-                        if (s < static_cast<uint64_t>(a.n)) {
-                            const uint32_t sg = __ldcg(a.res_segt + static_cast<int64_t>(p) * a.n + s);
-                            start = static_cast<int64_t>(g >> 32) * 4 + (sg & 0xFFFFu);
-                            len = static_cast<int>(sg >> 16);
-                        }
-                    }
-                    int sincl = len;
+                group_sync(bar, nbar);
+                // every spike's segment in this block's region, from the shared tables (the
+                // group's offset plus the lengths of the group's earlier senders); thread gt
+                // takes spikes gt * kper .. + kper, so that a prefix over threads orders them
+                const int G = nbar, gt = ql;
+                const int kper = (m + G - 1) / G;
+                uint32_t mine = 0;
+                for (int q = 0; q < kper; ++q) {
+                    const int j = gt * kper + q;
+                    if (j >= m) break;
+                    uint32_t st = 0, ln = 0;
+                    const int s = t_glist[j];
+                    if (static_cast<uint32_t>(s) < static_cast<uint64_t>(a.n)) {
+                        const uint32_t c = s_coarse[s >> 5];
+                        if (c & kResidentGroupFlag) {  // an escaped length in the group: exact offsets
+                            const uint32_t *o = a.res_offt + static_cast<int64_t>(p) * (a.n + 1) + s;
+                            st = __ldcg(o);
+                            ln = __ldcg(o + 1) - st;
+                        } else {
+                            const uint4 *gl = reinterpret_cast<const uint4 *>(s_lens + (s & ~31));
+                            const uint4 lo4 = gl[0], hi4 = gl[1];
+                            const uint32_t wv8[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
+                            const int before_s = s & 31;
+                            uint32_t acc = 0;
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int v = __shfl_up_sync(0xFFFFFFFFu, sincl, o);
-                        if (lane >= o) sincl += v;
-                    }
-                    const int T = __shfl_sync(0xFFFFFFFFu, sincl, 31);
-                    const int soff = sincl - len;
-                    for (int e0 = 0; e0 < T; e0 += 32 * kResU) {
-                        int32_t tg[kResU], wv[kResU];
-                        uint32_t dv[kResU];
-#pragma unroll
-                        for (int u = 0; u < kResU; ++u) {
-                            const int ei = e0 + 32 * u + lane;
-                            const int k = lane_of(soff, ei < T ? ei : T - 1);
-                            const int64_t st = __shfl_sync(0xFFFFFFFFu, start, k);
-                            const int so = __shfl_sync(0xFFFFFFFFu, soff, k);
-                            wv[u] = 0;
-                            tg[u] = base;
-                            dv[u] = 1;
-                            if (ei < T) {
-                                const int64_t idx = st + (ei - so);
-                                tg[u] = __ldcg(a.syn_tgt + idx);
-                                wv[u] = __ldcg(a.syn_w + idx);
-                                dv[u] = __ldcg(a.syn_d + idx);
+                            for (int k = 0; k < 8; ++k) {
+                                const int nb = min(max(before_s - 4 * k, 0), 4);
+                                const uint32_t mask = nb == 4 ? 0xFFFFFFFFu : ((1u << (8 * nb)) - 1u);
+                                acc = __dp4a(wv8[k] & mask, 0x01010101u, acc);
                             }
+                            st = (c & ~kResidentGroupFlag) + acc;
+                            ln = s_lens[s];
                         }
+                    }
+                    t_sstart[j] = st;
+                    t_soff[j] = ln;
+                    mine += ln;
+                }
+                // prefix of the segment lengths over the spikes: the flattened synapse list
+                uint32_t sincl = mine;
 #pragma unroll
-                        for (int u = 0; u < kResU; ++u) {
-                            const int lt = tg[u] - base;
-                            if (wv[u] == 0 || static_cast<uint32_t>(lt) >= static_cast<uint32_t>(width)) continue;
-                            const int d = static_cast<int>(dv[u]);
-                            if (full_ring || d < rows)
-                                atomicAdd(s_ring + ((t + d) & rmask) * stride + lt, wv[u]);
-                            else
-                                red_add_s32(a.ring + ((t + d) & kDMask) * npad + base + lt, wv[u]);
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, sincl, o);
+                    if (lane >= o) sincl += v;
+                }
+                if (lane == 31) t_wsum[tw] = static_cast<int32_t>(sincl);
+                group_sync(bar, nbar);
+                uint32_t run = 0, Tt = 0;
+                for (int w = 0; w < TW; ++w) {
+                    const uint32_t v = static_cast<uint32_t>(t_wsum[w]);
+                    run += w < tw ? v : 0u;
+                    Tt += v;
+                }
+                run += sincl - mine;
+                for (int q = 0; q < kper; ++q) {
+                    const int j = gt * kper + q;
+                    if (j >= m) break;
+                    const uint32_t ln = t_soff[j];
+                    t_soff[j] = run;
+                    // chunks of 32 synapses whose first synapse lies in this segment
+                    for (uint32_t k = (run + 31u) >> kJmapShift; k < static_cast<uint32_t>(kJmap) &&
+                                                                 (k << kJmapShift) < run + ln; ++k)
+                        t_jmap[k] = static_cast<uint16_t>(j);
+                    run += ln;
+                }
+                group_sync(bar, nbar);
+                // every delivery thread takes synapses gt, gt + G, ... of the flattened list
+                for (uint32_t e0 = 0; e0 < Tt; e0 += static_cast<uint32_t>(G) * kResU) {
+                    int32_t tg[kResU], wv[kResU];
+                    uint32_t dv[kResU];
+#pragma unroll
+                    for (int u = 0; u < kResU; ++u) {
+                        const uint32_t e = e0 + static_cast<uint32_t>(gt + G * u);
+                        wv[u] = 0;
+                        tg[u] = base;
+                        dv[u] = 1;
+                        if (e < Tt) {
+                            // the last spike whose segment starts at or before e: from the spike
+                            // holding e's chunk start, a short walk forward (segments of empty
+                            // spikes share their offset)
+                            int lo_j;
+                            if ((e >> kJmapShift) < static_cast<uint32_t>(kJmap)) {
+                                lo_j = t_jmap[e >> kJmapShift];
+                            } else {
+                                int lo = 0, hi = m - 1;
+                                while (lo < hi) {
+                                    const int mid = (lo + hi + 1) >> 1;
+                                    if (t_soff[mid] <= e) lo = mid;
+                                    else hi = mid - 1;
+                                }
+                                lo_j = lo;
+                            }
+                            while (lo_j + 1 < m && t_soff[lo_j + 1] <= e) ++lo_j;
+                            const int64_t idx = rbase + t_sstart[lo_j] + (e - t_soff[lo_j]);
+                            tg[u] = __ldcg(a.syn_tgt + idx);
+                            wv[u] = __ldcg(a.syn_w + idx);
+                            dv[u] = __ldcg(a.syn_d + idx);
                         }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kResU; ++u) {
+                        const int lt = tg[u] - base;
+                        if (wv[u] == 0 || static_cast<uint32_t>(lt) >= static_cast<uint32_t>(width)) continue;
+                        const int d = static_cast<int>(dv[u]);
+                        if (full_ring || d < rows)
+                            atomicAdd(s_ring + ((t + d) & rmask) * stride + lt, wv[u]);
+                        else
+                            red_add_s32(a.ring + ((t + d) & kDMask) * npad + base + lt, wv[u]);
                     }
                 }
-                group_sync(2, DW * 32);  // every add of this pass is done; the list may be rewritten
+                group_sync(bar, nbar);  // every add of this pass is done; the list may be rewritten
             }
-            cursor += static_cast<uint32_t>(total);
-            if (group_sync_or(2, DW * 32, late)) {
-                if (dw == 0 && lane == 0) st_volatile_shared(&s_misc->abort, 1u);
+            if (group_sync_or(bar, nbar, late)) {
+                if (tw == 0 && lane == 0) st_volatile_shared(&s_misc->abort, 1u);
                 break;
             }
-            if (dw == 0 && lane == 0) st_release_shared(&s_misc->d_done, static_cast<uint32_t>(t - t0 + 1));
-        }
-        if (p == 0 && dw == 0 && lane == 0 && !ld_volatile_shared(&s_misc->abort)) {
-            ctl->cursor = cursor;
-            if (cursor > a.rast_cap) atomicOr(&ctl->err, kErrRaster);
-            ctl->t_base = tend;
+            if (tw == 0 && lane == 0) st_release_shared(&s_misc->d_done[team], rel);
         }
     }
     if (!full_ring) __threadfence();  // the long-delay adds before the ring write-back reads them
     __syncthreads();
     if (ld_volatile_shared(&s_misc->abort)) return;  // a wait timed out: the error is recorded, the state is void
+    if (p == 0 && threadIdx.x == 0) {
+        const uint32_t cursor = s_misc->cur_val[static_cast<uint32_t>(n_steps + 1) & 3];
+        ctl->cursor = cursor;
+        if (cursor > a.rast_cap) atomicOr(&ctl->err, kErrRaster);
+        ctl->t_base = tend;
+    }
 
     // ---- write the state after tend steps back to the arena ----
     if (active) {
@@ -635,19 +714,23 @@ int64_t resident_width(int64_t n, int num_sms)
     return w > kResidentMaxWidth ? 0 : w;
 }
 
-size_t resident_smem_bytes(int rows, int stride) { return res_layout(rows, stride).total; }
+size_t resident_smem_bytes(int rows, int stride, int64_t n)
+{
+    const ResTables T = resident_tables(n, 1);
+    return res_layout(rows, stride, static_cast<int>(T.lens_stride), static_cast<int>(T.coarse_stride)).total;
+}
 
-int resident_rows(int stride, int cap)
+int resident_rows(int stride, int cap, int64_t n)
 {
     for (int rows = kDMax; rows >= 8; rows >>= 1)
-        if ((cap <= 0 || rows <= cap) && resident_smem_bytes(rows, stride) <= 232448) return rows;
+        if ((cap <= 0 || rows <= cap) && resident_smem_bytes(rows, stride, n) <= 232448) return rows;
     return 0;
 }
 
 int prepare_resident_kernel(const StepArgs &a)
 {
     return static_cast<int>(cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(resident_smem_bytes(a.res_rows, a.res_stride))));
+                                                 static_cast<int>(resident_smem_bytes(a.res_rows, a.res_stride, a.n))));
 }
 
 int resident_blocks_per_sm(const StepArgs &a)
@@ -655,7 +738,7 @@ int resident_blocks_per_sm(const StepArgs &a)
     int nb = 0;
     const int threads = 32 * (a.neuron_warps + a.delivery_warps);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_resident, threads,
-                                                      resident_smem_bytes(a.res_rows, a.res_stride)) != cudaSuccess)
+                                                      resident_smem_bytes(a.res_rows, a.res_stride, a.n)) != cudaSuccess)
         return 0;
     return nb;
 }
@@ -667,7 +750,7 @@ int launch_resident(const StepArgs &a, int64_t n_steps, void *stream)
     void *params[] = {&args, &n};
     const cudaError_t e = cudaLaunchCooperativeKernel(
         reinterpret_cast<const void *>(k_resident), dim3(a.n_blocks), dim3(32 * (a.neuron_warps + a.delivery_warps)),
-        params, resident_smem_bytes(a.res_rows, a.res_stride), static_cast<cudaStream_t>(stream));
+        params, resident_smem_bytes(a.res_rows, a.res_stride, a.n), static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? 0 : static_cast<int>(e);
 }
 

@@ -43,16 +43,67 @@ def _assert_same_state(net, sim):
     assert np.array_equal(R, sim.R)
 
 
+def _resident_tables(net):
+    """The resident engine's block-major tables (rbase, offt) read back from the arena."""
+    n, B = net.n_neurons, int(net.info().target_blocks)
+    up = lambda x: (x + 255) // 256 * 256  # noqa: E731
+    coarse_stride = (n + 31) // 32 + 1
+    lens_stride = (n + 31) // 32 * 32
+    o_coarse = up(8 * (B + 1))
+    o_lens = up(o_coarse + 4 * B * coarse_stride)
+    o_offt = up(o_lens + B * lens_stride)
+    base = int(net.layout().block_starts)
+    region = net._arena[net._arena_ptr - net._arena.data_ptr() + base:][: o_offt + 4 * B * (n + 1)]
+    raw = region.cpu().numpy()
+    rbase = raw[: 8 * (B + 1)].view(np.int64)
+    coarse = raw[o_coarse: o_coarse + 4 * B * coarse_stride].view(np.uint32).reshape(B, coarse_stride)
+    lens = raw[o_lens: o_lens + B * lens_stride].reshape(B, lens_stride)
+    offt = raw[o_offt: o_offt + 4 * B * (n + 1)].view(np.uint32).reshape(B, n + 1).astype(np.int64)
+    return rbase, offt, lens, coarse
+
+
 def _device_network(net):
-    """(pre, post, delay, w) of every real synapse read back from the device arena."""
+    """(row_ptr, post, w, delay) of the device network in row form: rows padded to
+    multiples of 4 with entries that deliver nothing.  The resident engine stores its
+    records block-major; its rows are reassembled here, each grouped by target block."""
     lay = net.layout()
     n = net.n_neurons
     sp = int(lay.n_synapses_padded)
-    rp = net.device_view("row_ptr", torch.int64, n + 1).cpu().numpy()
     tg = net.device_view("syn_tgt", torch.int32, sp).cpu().numpy()
     w = net.device_view("syn_w", torch.int32, sp).cpu().numpy()
     d = net.device_view("syn_delay", torch.uint8, sp).cpu().numpy()
-    return rp, tg, w, d
+    if net.info().engine != RES:
+        rp = net.device_view("row_ptr", torch.int64, n + 1).cpu().numpy()
+        return rp, tg, w, d
+    rbase, offt, _, _ = _resident_tables(net)
+    lens = np.diff(offt, axis=1)                                  # [block][sender]
+    sender = np.concatenate([np.repeat(np.arange(n), lens[b]) for b in range(len(lens))])
+    order = np.argsort(sender, kind="stable")                     # by sender, blocks in order
+    deg = lens.sum(axis=0)
+    plen = (deg + 3) // 4 * 4
+    rp = np.concatenate([[0], np.cumsum(plen)]).astype(np.int64)
+    pos = np.arange(len(order)) - np.repeat(np.concatenate([[0], np.cumsum(deg)[:-1]]), deg) \
+        + np.repeat(rp[:-1], deg)
+    T = np.repeat(np.arange(n, dtype=np.int32), plen)             # padding: onto the sender, w = 0
+    W = np.zeros(rp[-1], np.int32)
+    D = np.ones(rp[-1], np.uint8)
+    T[pos], W[pos], D[pos] = tg[order], w[order], d[order]
+    return rp, T, W, D
+
+
+def _resident_rows(net, rows):
+    """The resident engine's rows `rows` reassembled from the block-major regions (sampled
+    rows of a large network); returns {row: (post, w, delay)}."""
+    rbase, offt, _, _ = _resident_tables(net)
+    sp = int(net.layout().n_synapses_padded)
+    tg = net.device_view("syn_tgt", torch.int32, sp).cpu().numpy()
+    w = net.device_view("syn_w", torch.int32, sp).cpu().numpy()
+    d = net.device_view("syn_delay", torch.uint8, sp).cpu().numpy()
+    out = {}
+    for i in rows:
+        idx = np.concatenate([np.arange(rbase[b] + offt[b, i], rbase[b] + offt[b, i + 1]) for b in range(len(offt))])
+        out[int(i)] = (tg[idx], w[idx], d[idx])
+    return out
 
 
 def _block_bounds(net):
@@ -460,8 +511,26 @@ def test_full_scale_parity(model, full, engine):
     assert np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
     _assert_same_state(net, sim)
     rng = np.random.default_rng(0)
-    rows = np.unique(np.concatenate([o_i, rng.integers(0, onet.n, 2000)]))
-    _rows_equal_sampled(onet, *_device_network(net), rows, bounds=_block_bounds(net))
+    if engine == RES:
+        # block-major records: sampled rows reassembled from the 151 block regions
+        rows = np.unique(np.concatenate([rng.choice(o_i, 300), rng.integers(0, onet.n, 700)]))
+        got = _resident_rows(net, rows)
+        bounds = _block_bounds(net)
+        for i in rows:
+            a, L = onet.row_ptr[i], onet.row_ptr[i + 1] - onet.row_ptr[i]
+            o = np.sort(onet.post[a:a + L].astype(np.int64) << 38 | onet.delay[a:a + L].astype(np.int64) << 32
+                        | (onet.w_fx[a:a + L].astype(np.int64) + 2**31))
+            tg, w, d = got[int(i)]
+            g = np.sort(tg.astype(np.int64) << 38 | d.astype(np.int64) << 32 | (w.astype(np.int64) + 2**31))
+            assert np.array_equal(o, g), i
+            _assert_row_order(bounds, tg, d, [0], [L])
+        sp = int(net.layout().n_synapses_padded)
+        assert sp == len(onet.post)
+        assert int(net.device_view("syn_w", torch.int32, sp).cpu().numpy().astype(np.int64).sum()) == \
+            int(onet.w_fx.astype(np.int64).sum())
+    else:
+        rows = np.unique(np.concatenate([o_i, rng.integers(0, onet.n, 2000)]))
+        _rows_equal_sampled(onet, *_device_network(net), rows, bounds=_block_bounds(net))
     net.close()
 
 

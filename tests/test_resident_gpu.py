@@ -1,14 +1,15 @@
 """GPU parity of the resident engine (one cooperative CTA per target block, neuron state
-in registers, the block's ring columns in shared memory, spikes exchanged through
-step-tagged mailboxes) against the CPU oracle, through the C ABI.
+in registers, the block's ring columns and segment tables in shared memory, block-major
+records, spikes exchanged through step-tagged inbox slots) against the CPU oracle,
+through the C ABI.
 
 The engine's arithmetic is the plain mode's (FP32 without FMA, int32 ring), so rasters
 and states are compared element by element with no tolerance.  The cases reach the
 engine's own mechanics: launch boundaries at every phase of the ring, the shared-memory
 window with long delays in global memory, bursts larger than the per-pass gather list
-and mailboxes holding more spikes than one probe reads, the per-row block table, a
-checkpoint loaded into a handle whose mailboxes hold later steps, and the bounded
-mailbox wait.
+and slots holding more spikes than one probe reads, the block-major tables and their
+escaped lengths, a checkpoint loaded into a handle whose mailboxes hold later steps,
+and the bounded mailbox wait.
 """
 
 import numpy as np
@@ -75,43 +76,93 @@ def _assert_same(net, sim, ring=True):
         assert np.array_equal(_ring(net), _oracle_ring(sim))
 
 
+def _tables(net):
+    """The block-major tables (rbase, offt, lens, coarse) read back from the arena."""
+    n, B = net.n_neurons, int(net.info().target_blocks)
+    up = lambda x: (x + 255) // 256 * 256  # noqa: E731
+    coarse_stride, lens_stride = (n + 31) // 32 + 1, (n + 31) // 32 * 32
+    o_coarse = up(8 * (B + 1))
+    o_lens = up(o_coarse + 4 * B * coarse_stride)
+    o_offt = up(o_lens + B * lens_stride)
+    start = net._arena_ptr - net._arena.data_ptr() + int(net.layout().block_starts)
+    raw = net._arena[start: start + o_offt + 4 * B * (n + 1)].cpu().numpy()
+    rbase = raw[: 8 * (B + 1)].view(np.int64)
+    coarse = raw[o_coarse: o_coarse + 4 * B * coarse_stride].view(np.uint32).reshape(B, coarse_stride)
+    lens = raw[o_lens: o_lens + B * lens_stride].reshape(B, lens_stride)[:, :n]
+    offt = raw[o_offt: o_offt + 4 * B * (n + 1)].view(np.uint32).reshape(B, n + 1).astype(np.int64)
+    return rbase, offt, lens, coarse
+
+
 def test_resident_structure_tiny(model, tiny):
-    """Blocks of equal width (a multiple of 32) cover the neurons, one CTA each; every row
-    holds the oracle's synapses grouped by target block, delay-sorted inside a block, and
-    the block table gives each segment's start."""
+    """Blocks of equal width (a multiple of 32) cover the neurons, one CTA each.  The
+    records are block-major: block b's region holds, sender by sender, exactly the
+    oracle's synapses of that sender into block b, in delay order; the tables give every
+    segment's offset (exact), its length capped at 255 (with escapes flagged per group of
+    32 senders) and each group's first offset."""
     wl, onet = tiny
     net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, engine=RES)
     info = net.info()
     assert info.engine == RES and info.record_format == snn.RECORD_PLAIN9
     B = int(info.target_blocks)
     assert B >= 1 and info.schedule_ctas == B and info.schedule_delivery_warps * 32 >= B
+    n = onet.n
     bounds = net.device_view("blocks", torch.int32, B + 1).cpu().numpy().astype(np.int64)
     width = bounds[1] - bounds[0]
-    assert bounds[0] == 0 and bounds[-1] == onet.n and width % 32 == 0 and width <= 1024
+    assert bounds[0] == 0 and bounds[-1] == n and width % 32 == 0 and width <= 1024
     assert np.all(np.diff(bounds)[:-1] == width) and 0 < bounds[-1] - bounds[-2] <= width
-    lay = net.layout()
-    n = onet.n
-    sp = int(lay.n_synapses_padded)
-    rp = net.device_view("row_ptr", torch.int64, n + 1).cpu().numpy()
-    tg = net.device_view("syn_tgt", torch.int32, sp).cpu().numpy().astype(np.int64)
-    w = net.device_view("syn_w", torch.int32, sp).cpu().numpy()
-    d = net.device_view("syn_delay", torch.uint8, sp).cpu().numpy()
-    segt = net.device_view("block_starts", torch.int32, B * n).cpu().numpy().view(np.uint32).reshape(B, n)
-    starts, seglen = (segt & 0xFFFF).astype(np.int64), (segt >> 16).astype(np.int64)
-    lens = np.diff(onet.row_ptr)
-    assert np.array_equal(seglen.sum(axis=0), lens)
+    rbase, offt, lens, coarse = _tables(net)
+    S = len(onet.post)
+    assert rbase[0] == 0 and rbase[-1] == S and int(net.layout().n_synapses_padded) == S
+    assert np.array_equal(np.diff(rbase), offt[:, n])
+    seglen = np.diff(offt, axis=1)
+    assert np.array_equal(lens, np.minimum(seglen, 255))
+    assert np.array_equal(coarse[:, :-1] & 0x7FFFFFFF, offt[:, 0:n:32])
+    flagged = (coarse[:, :-1] >> 31).astype(bool)
+    groups = np.add.reduceat(seglen >= 255, np.arange(0, n, 32), axis=1) > 0
+    assert np.array_equal(flagged, groups)
+    tg = net.device_view("syn_tgt", torch.int32, S).cpu().numpy().astype(np.int64)
+    w = net.device_view("syn_w", torch.int32, S).cpu().numpy()
+    d = net.device_view("syn_delay", torch.uint8, S).cpu().numpy()
+    blk_of = np.searchsorted(bounds, onet.post, side="right") - 1
     for i in range(0, n, 7):
-        a, L = rp[i], lens[i]
-        blk = np.searchsorted(bounds, tg[a:a + L], side="right") - 1
-        key = blk * 64 + d[a:a + L]
-        assert np.all(np.diff(key) >= 0)
-        assert np.array_equal(starts[:, i], np.searchsorted(blk, np.arange(B), side="left"))
-        assert np.array_equal(seglen[:, i], np.bincount(blk, minlength=B))
-        oa = onet.row_ptr[i]
-        o = np.sort(onet.post[oa:oa + L].astype(np.int64) << 38 | onet.delay[oa:oa + L].astype(np.int64) << 32
-                    | (onet.w_fx[oa:oa + L].astype(np.int64) + 2**31))
-        g = np.sort(tg[a:a + L] << 38 | d[a:a + L].astype(np.int64) << 32 | (w[a:a + L].astype(np.int64) + 2**31))
-        assert np.array_equal(o, g)
+        oa, ob = onet.row_ptr[i], onet.row_ptr[i + 1]
+        for b in range(0, B, 5):
+            a0, a1 = rbase[b] + offt[b, i], rbase[b] + offt[b, i + 1]
+            sel = slice(oa, ob)
+            mine = blk_of[sel] == b
+            o = np.sort(onet.post[sel][mine].astype(np.int64) << 38 | onet.delay[sel][mine].astype(np.int64) << 32
+                        | (onet.w_fx[sel][mine].astype(np.int64) + 2**31))
+            g = np.sort(tg[a0:a1] << 38 | d[a0:a1].astype(np.int64) << 32 | (w[a0:a1].astype(np.int64) + 2**31))
+            assert np.array_equal(o, g), (i, b)
+            assert np.all(np.diff(d[a0:a1].astype(int)) >= 0)
+            assert np.all((tg[a0:a1] >= bounds[b]) & (tg[a0:a1] < bounds[b + 1]))
+    with pytest.raises(snn.SnnError):  # records are not rows: phase 2 alone is refused
+        net.deliver_spikes(torch.zeros(1, dtype=torch.int32, device="cuda"), 0)
+    net.close()
+
+
+def test_resident_escaped_segment_lengths(model):
+    """Segments of 255 synapses or more (a sender with many synapses into one block) are
+    escaped in the 8-bit length table; their group is flagged and their offsets come
+    from the exact table.  Raster and state equal the oracle's."""
+    n = 600
+    rng = np.random.default_rng(17)
+    pre = np.concatenate([np.full(700, 3), np.full(300, 40), rng.integers(0, n, 20000)])
+    post = np.concatenate([rng.integers(0, 32, 700), rng.integers(64, 96, 300), rng.integers(0, n, 20000)])
+    S = len(pre)
+    c = dict(pre=pre, post=post, w_fx=rng.integers(-800_000, 1_600_000, S), delay=rng.integers(1, 64, S),
+             u0=rng.uniform(5, 16, n).astype(np.float32), pop_offsets=[0] + [n] * 8)
+    net = snn.Network(model, custom=c, seed=9, engine=RES)
+    rbase, offt, lens, coarse = _tables(net)
+    assert (np.diff(offt, axis=1) >= 255).any() and ((coarse[:, :-1] >> 31) == 1).any()
+    onet = oracle.network_from_edges(n, c["pre"], c["post"], c["w_fx"], c["delay"], c["u0"], c["pop_offsets"])
+    sim = oracle.Sim(model, onet, 9)
+    net.step(300)
+    g = net.read_spikes()
+    o = sim.run(300)
+    assert len(o[0]) > 100
+    assert np.array_equal(g[0], o[0]) and np.array_equal(g[1], o[1])
+    _assert_same(net, sim)
     net.close()
 
 
@@ -155,8 +206,9 @@ def _burst_net(n, seed, syn_per_neuron=40):
 @pytest.mark.parametrize("rows", [0, 8])
 def test_resident_bursts_beyond_gather_list(model, rows):
     """Two thirds of 7,000 neurons spike at step 0: a step's spike list exceeds the
-    2,048-entry gather list (several passes) and every mailbox holds more spikes than
-    its first probe reads; 150 steps against the oracle."""
+    256-entry gather list (several passes) and every slot holds more spikes than its
+    three entries (the rest come from the sender's outbox); 150 steps against the
+    oracle."""
     m = model
     n = 7000
     c = _burst_net(n, 3)
@@ -203,8 +255,9 @@ def test_resident_delivery_warps_do_not_change_results(model, tiny):
     o = oracle.Sim(model, onet, wl.seed).run(400)
     net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, engine=RES)
     B = int(net.info().target_blocks)
+    team = max(1, (B + 31) // 32)
     parts = []
-    for k, dw in enumerate(range(max(1, (B + 31) // 32), 9)):
+    for k, dw in enumerate(range(2 * team, 2 * team + 6, 2)):
         net.set_schedule(delivery_warps=dw)
         assert net.info().schedule_delivery_warps == dw
         net.step(50)
@@ -215,6 +268,8 @@ def test_resident_delivery_warps_do_not_change_results(model, tiny):
     assert np.array_equal(np.concatenate([p[1] for p in parts]), o[1])
     with pytest.raises(snn.SnnError):
         net.set_schedule(grid_ctas=10)
+    with pytest.raises(snn.SnnError):
+        net.set_schedule(delivery_warps=2 * team + 1)  # teams of equal size only
     net.close()
 
 
