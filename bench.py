@@ -337,11 +337,15 @@ def run_gpu(args):
     energy = EnergyCounter(local)
     with ClockSampler(local) as clk:
         mj0 = energy.read()
+        if args.profile_region == "timed":
+            torch.cuda.profiler.start()
         start.record(stream)
         for _ in range(args.steps):
             net.step(tps)
         end.record(stream)
         torch.cuda.synchronize(dev)
+        if args.profile_region == "timed":
+            torch.cuda.profiler.stop()
         mj1 = energy.read()
     _barrier(ws)
     ms = start.elapsed_time(end)
@@ -444,10 +448,14 @@ def run_gpu(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize(dev)
+            if args.profile_region == "saturating":
+                torch.cuda.profiler.start()
             e0.record(stream)
             net.deliver_spikes(dev_spk, 0)
             e1.record(stream)
             torch.cuda.synchronize(dev)
+            if args.profile_region == "saturating":
+                torch.cuda.profiler.stop()
             if r >= 2:
                 ms_list.append(e0.elapsed_time(e1))
                 ev_list.append(int(outdeg[spk].sum()))
@@ -459,6 +467,42 @@ def run_gpu(args):
                     "reductions_per_s": ev_avg / (ms_avg * 1e-3)})
 
     net.close()
+
+    # the paper's RTF is the mean over 10 random network instances (§4): the same step loop
+    # on network seeds seed .. seed + n - 1, each after one warm-up bench step
+    instances = []
+    for k in range(args.seeds):
+        sk = seed + k
+        inet = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, sk, steps_per_graph=tps,
+                           raster_capacity=1 << 25, device=dev, engine=engine)
+        inet.step(tps)
+        inet.read_spikes()
+        ie0 = inet.info().events_read
+        torch.cuda.synchronize(dev)
+        i0 = torch.cuda.Event(enable_timing=True)
+        i1 = torch.cuda.Event(enable_timing=True)
+        i0.record(stream)
+        for _ in range(args.seed_steps):
+            inet.step(tps)
+        i1.record(stream)
+        torch.cuda.synchronize(dev)
+        isecs = i0.elapsed_time(i1) * 1e-3
+        inet.read_spikes()
+        iev = inet.info().events_read - ie0
+        instances.append({"seed": sk, "events_per_s": iev / isecs,
+                          "rtf": isecs / (args.seed_steps * tps * model.dt_ms * 1e-3)})
+        inet.close()
+    seeds_summary = None
+    if instances:
+        ev = np.array([x["events_per_s"] for x in instances])
+        rt = np.array([x["rtf"] for x in instances])
+        seeds_summary = {"n": len(instances), "steps_each": args.seed_steps * tps,
+                         "events_per_s_mean": float(ev.mean()), "events_per_s_sd": float(ev.std(ddof=1)) if len(ev) > 1 else 0.0,
+                         "rtf_mean": float(rt.mean()), "rtf_sd": float(rt.std(ddof=1)) if len(rt) > 1 else 0.0,
+                         "realtime_x_mean": float((1.0 / rt).mean()), "instances": instances,
+                         "note": "network seeds seed .. seed + n - 1 (the paper's RTF is the mean over 10 instances, "
+                                 "section 4); each timed over steps_each steps after one warm-up bench step"}
+    torch.cuda.empty_cache()
 
     # compressed synapse records on the same workload: step time and saturating delivery
     forms = {}
@@ -498,10 +542,14 @@ def run_gpu(args):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 torch.cuda.synchronize(dev)
+                if args.profile_region == "saturating":
+                    torch.cuda.profiler.start()
                 e0.record(stream)
                 fnet.deliver_spikes(spk, 0)
                 e1.record(stream)
                 torch.cuda.synchronize(dev)
+                if args.profile_region == "saturating":
+                    torch.cuda.profiler.stop()
                 if r >= 2:
                     ms_l.append(e0.elapsed_time(e1))
                     ev_l.append(int(outdeg[spk_np].sum()))
@@ -631,6 +679,7 @@ def run_gpu(args):
                    "deliver_blocks": info.deliver_blocks, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (2.56 GB synapse store); ring and neuron state are L2-resident by design"},
         "rtf": rtf, "realtime_x": 1.0 / rtf, "spikes_per_tick": spikes / (args.steps * tps),
+        "instances": seeds_summary,
         "events_incl_thalamic": {
             "value": value + ws * thal_bio * bio_s / secs_max, "unit": "synaptic events/s",
             "thalamic_per_bio_second": thal_bio,
@@ -707,9 +756,12 @@ def main():
     ap.add_argument("--batched-groups", type=int, default=-1,
                     help="circuits per group for the batched workload instead of autotuning (-1: autotune)")
     ap.add_argument("--x4-steps", type=int, default=10240)
-    ap.add_argument("--profile-region", choices=["none", "batched", "x4"], default="none",
-                    help="bracket that workload's timed region with cudaProfilerStart/Stop")
+    ap.add_argument("--profile-region", choices=["none", "timed", "saturating", "batched", "x4"], default="none",
+                    help="bracket that region (the main timed region, the saturating delivery launches, or a "
+                         "workload's timed region) with cudaProfilerStart/Stop")
     ap.add_argument("--form-steps", type=int, default=20)
+    ap.add_argument("--seeds", type=int, default=10, help="network instances timed for the mean RTF (0: none)")
+    ap.add_argument("--seed-steps", type=int, default=10, help="bench steps timed per instance")
     ap.add_argument("--engine", default="default", choices=["default", "graph", "persistent", "pipelined", "resident"])
     args = ap.parse_args()
     if args.warmup < 3:
