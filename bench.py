@@ -439,6 +439,13 @@ def run_gpu(args):
     # runs after every other measurement
     sat = []
     outdeg = net.out_degrees()
+    snet = net
+    if info.engine == snn.ENGINE_RESIDENT:
+        # the resident engine stores its records block-major (no sender rows): phase 2
+        # alone runs on the row-major network of the same spec and seed
+        net.close()
+        snet = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, seed, steps_per_graph=tps,
+                           raster_capacity=1 << 25, device=dev, engine=others)
     rng = np.random.default_rng(1234 + rank)
     for nsp in args.saturating:
         ms_list, ev_list = [], []
@@ -451,7 +458,7 @@ def run_gpu(args):
             if args.profile_region == "saturating":
                 torch.cuda.profiler.start()
             e0.record(stream)
-            net.deliver_spikes(dev_spk, 0)
+            snet.deliver_spikes(dev_spk, 0)
             e1.record(stream)
             torch.cuda.synchronize(dev)
             if args.profile_region == "saturating":
@@ -466,7 +473,7 @@ def run_gpu(args):
                     "gbs": nbytes / (ms_avg * 1e-3) / 1e9, "frac": nbytes / (ms_avg * 1e-3) / 1e9 / peak,
                     "reductions_per_s": ev_avg / (ms_avg * 1e-3)})
 
-    net.close()
+    snet.close()
 
     # the paper's RTF is the mean over 10 random network instances (§4): the same step loop
     # on network seeds seed .. seed + n - 1, each after one warm-up bench step
