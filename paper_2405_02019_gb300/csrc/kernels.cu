@@ -709,10 +709,10 @@ __global__ void __launch_bounds__(kStepMaxThreads, 1) k_persistent(const StepArg
 // of quads.  The
 // stream is taken in windows of kBlockedWindow quads; for a window the record-array
 // index of every quad is written into a shared table, after which the quads are
-// independent work: warp w takes rounds w, w + 32, ... of 32 consecutive quads,
-// kBlockedRounds rounds at a time, issuing all their loads (per quad 8 bytes of records
-// and 16 of int32 weights, or one 16-byte unit of records and bfloat16 weights) before
-// adding any.
+// independent work: warp w takes rounds w, w + 32, ... of 32 consecutive quads, in
+// sets of kBlockedRounds / 2 rounds whose loads (per quad 8 bytes of records and 16 of
+// int32 weights, or one 16-byte unit of records and bfloat16 weights) are issued while
+// the previous set's weights are added.
 // With many senders the weights of delays up to kBlockedBinDelays are summed per (delay,
 // local target) in shared memory and each nonzero sum is added to its ring entry once at
 // the end; only this CTA writes these ring columns during the launch, so that final add
@@ -781,51 +781,81 @@ __device__ __forceinline__ int32_t bf16_fx(uint32_t h)
 
 // Quads [w0, w1) of the staged stream; qidx[e - w0] is quad e's index in the record
 // arrays: BLOCKED6 reads 8 bytes of records and 16 of int32 weights per quad, BLOCKED4
-// one 16-byte unit of records and bfloat16 weights.
-template <bool kAggregate, int FMT>
-__device__ __forceinline__ void blocked_window(const StepArgs &a, int32_t *bins, const uint32_t *qidx, int32_t w0,
-                                               int32_t w1, int64_t t, int32_t base)
+// one 16-byte unit of records and bfloat16 weights.  The window is taken in sets of
+// kBlockedRounds / 2 rounds, software-pipelined: the loads of the next set are in flight
+// while the current set's weights are added, so the record stream never drains inside
+// a window.
+constexpr int kBlockedSet = kBlockedRounds / 2;  // rounds per pipelined set
+
+template <int FMT>
+__device__ __forceinline__ void blocked_load_set(const StepArgs &a, const uint32_t *qidx, int32_t w0, int32_t w1,
+                                                 int32_t e0, uint2 (&rec)[kBlockedSet], int4 (&w)[kBlockedSet])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint2 *recq = reinterpret_cast<const uint2 *>(a.blk_rec);
     const int4 *wq = reinterpret_cast<const int4 *>(a.syn_w);
     const uint4 *q16 = reinterpret_cast<const uint4 *>(a.blk_rec);
-    // round k of a step is quads e0 + 32 * (warp + kBlockedWarps * k) + lane: the warps
-    // of the CTA interleave, so that a window's rounds spread evenly over them
-    for (int32_t e0 = w0; e0 < w1; e0 += kBlockedThreads * kBlockedRounds) {
-        uint2 rec[kBlockedRounds];
-        int4 w[kBlockedRounds];
 #pragma unroll
-        for (int k = 0; k < kBlockedRounds; ++k) {
-            const int32_t e = e0 + 32 * (warp + kBlockedWarps * k) + lane;
-            if (e < w1) {
-                const uint32_t q = qidx[e - w0];
-                if (FMT == SNN_RECORD_BLOCKED4) {
-                    const uint4 v = __ldcs(q16 + q);
-                    rec[k] = make_uint2(v.x, v.y);
-                    w[k] = make_int4(static_cast<int32_t>(v.z), static_cast<int32_t>(v.w), 0, 0);  // decoded below
-                } else {
-                    rec[k] = __ldcs(recq + q);
-                    w[k] = __ldcs(wq + q);
-                }
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < kBlockedRounds; ++k) {
-            if (e0 + 32 * (warp + kBlockedWarps * k) + lane >= w1) continue;
-            int32_t w0v = w[k].x, w1v = w[k].y, w2v = w[k].z, w3v = w[k].w;
+    for (int k = 0; k < kBlockedSet; ++k) {
+        // round k of a set is quads e0 + 32 * (warp + kBlockedWarps * k) + lane: the warps
+        // of the CTA interleave, so that a window's rounds spread evenly over them
+        const int32_t e = e0 + 32 * (warp + kBlockedWarps * k) + lane;
+        rec[k] = make_uint2(0, 0);
+        w[k] = make_int4(0, 0, 0, 0);
+        if (e < w1) {
+            const uint32_t q = qidx[e - w0];
             if (FMT == SNN_RECORD_BLOCKED4) {
-                const uint32_t h01 = static_cast<uint32_t>(w[k].x), h23 = static_cast<uint32_t>(w[k].y);
-                w0v = bf16_fx(h01);
-                w1v = bf16_fx(h01 >> 16);
-                w2v = bf16_fx(h23);
-                w3v = bf16_fx(h23 >> 16);
+                const uint4 v = __ldcs(q16 + q);
+                rec[k] = make_uint2(v.x, v.y);
+                w[k] = make_int4(static_cast<int32_t>(v.z), static_cast<int32_t>(v.w), 0, 0);  // decoded below
+            } else {
+                rec[k] = __ldcs(recq + q);
+                w[k] = __ldcs(wq + q);
             }
-            blocked_apply<kAggregate>(a, bins, t, base, rec[k].x & 0xffffu, w0v);
-            blocked_apply<kAggregate>(a, bins, t, base, rec[k].x >> 16, w1v);
-            blocked_apply<kAggregate>(a, bins, t, base, rec[k].y & 0xffffu, w2v);
-            blocked_apply<kAggregate>(a, bins, t, base, rec[k].y >> 16, w3v);
         }
+    }
+}
+
+template <bool kAggregate, int FMT>
+__device__ __forceinline__ void blocked_apply_set(const StepArgs &a, int32_t *bins, int64_t t, int32_t base,
+                                                  const uint2 (&rec)[kBlockedSet], const int4 (&w)[kBlockedSet])
+{
+#pragma unroll
+    for (int k = 0; k < kBlockedSet; ++k) {
+        int32_t w0v = w[k].x, w1v = w[k].y, w2v = w[k].z, w3v = w[k].w;
+        if (FMT == SNN_RECORD_BLOCKED4) {
+            const uint32_t h01 = static_cast<uint32_t>(w[k].x), h23 = static_cast<uint32_t>(w[k].y);
+            w0v = bf16_fx(h01);
+            w1v = bf16_fx(h01 >> 16);
+            w2v = bf16_fx(h23);
+            w3v = bf16_fx(h23 >> 16);
+        }
+        // quads past the window end were left zero: zero weights add nothing
+        blocked_apply<kAggregate>(a, bins, t, base, rec[k].x & 0xffffu, w0v);
+        blocked_apply<kAggregate>(a, bins, t, base, rec[k].x >> 16, w1v);
+        blocked_apply<kAggregate>(a, bins, t, base, rec[k].y & 0xffffu, w2v);
+        blocked_apply<kAggregate>(a, bins, t, base, rec[k].y >> 16, w3v);
+    }
+}
+
+template <bool kAggregate, int FMT>
+__device__ __forceinline__ void blocked_window(const StepArgs &a, int32_t *bins, const uint32_t *qidx, int32_t w0,
+                                               int32_t w1, int64_t t, int32_t base)
+{
+    constexpr int32_t kStep = kBlockedThreads * kBlockedSet;
+    uint2 recA[kBlockedSet], recB[kBlockedSet];
+    int4 wA[kBlockedSet], wB[kBlockedSet];
+    int32_t e0 = w0;
+    blocked_load_set<FMT>(a, qidx, w0, w1, e0, recA, wA);
+    for (;;) {
+        if (e0 + kStep < w1) blocked_load_set<FMT>(a, qidx, w0, w1, e0 + kStep, recB, wB);
+        blocked_apply_set<kAggregate, FMT>(a, bins, t, base, recA, wA);
+        e0 += kStep;
+        if (e0 >= w1) break;
+        if (e0 + kStep < w1) blocked_load_set<FMT>(a, qidx, w0, w1, e0 + kStep, recA, wA);
+        blocked_apply_set<kAggregate, FMT>(a, bins, t, base, recB, wB);
+        e0 += kStep;
+        if (e0 >= w1) break;
     }
 }
 

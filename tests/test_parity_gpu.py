@@ -768,6 +768,7 @@ def _check_blocked_structure(net, onet, rows=None):
     rp = net.device_view("row_ptr", torch.int64, n + 1).cpu().numpy()
     seg = net.device_view("syn_delay", torch.int16, n * (B + 1)).cpu().numpy().view(np.uint16)
     seg = seg.reshape(n, B + 1).astype(np.int64)
+    q = 4  # records per padding unit (a quad)
     if info.record_format == snn.RECORD_BLOCKED4:
         quads = net.device_view("syn_tgt", torch.int16, 2 * SP).cpu().numpy().view(np.uint16).reshape(-1, 8)
         rec = np.ascontiguousarray(quads[:, :4]).reshape(-1)
@@ -779,9 +780,9 @@ def _check_blocked_structure(net, onet, rows=None):
     assert np.all(blk[1:-1] % 32 == 0) and np.all(np.diff(blk) <= 768)
     lens = np.diff(onet.row_ptr)
     plen = np.diff(rp)
-    assert rp[0] == 0 and rp[-1] == SP and np.all(plen >= lens) and np.all(rp % 4 == 0)
+    assert rp[0] == 0 and rp[-1] == SP and np.all(plen >= lens) and np.all(rp % q == 0)
     assert np.all(seg[:, 0] == 0) and np.array_equal(seg[:, -1], plen) and np.all(np.diff(seg, axis=1) >= 0)
-    assert np.all(seg % 4 == 0)
+    assert np.all(seg % q == 0)
     real = w != 0
     assert int(real.sum()) == S and np.all(rec[~real] == 1024)
     # block of every entry, segment starts, then chunked decode
@@ -807,10 +808,10 @@ def _check_blocked_structure(net, onet, rows=None):
     assert sums[2] == int(onet.w_fx.astype(np.int64).sum())
     if rows is None:
         rows = np.arange(n)
-        # fewer than 4 padding entries per segment
+        # fewer than q padding entries per segment
         segid = np.repeat(np.arange(n * B), np.diff(seg, axis=1).ravel())
         pads = np.bincount(segid[~real], minlength=n * B)
-        assert pads.max() < 4
+        assert pads.max() < q
     for i in rows:
         a, L = onet.row_ptr[i], lens[i]
         sl = slice(rp[i], rp[i + 1])
@@ -863,13 +864,17 @@ def _expected_ring(onet, spikers, t, npad):
     return exp.astype(np.int64).reshape(64, npad)
 
 
-@pytest.mark.parametrize("nspk", [1, 63, 64, 700, 1024, 1025, 3000])
-def test_blocked_deliver_spikes_matches_oracle_network(model, tiny, nspk):
+@pytest.mark.parametrize("fmt", [BLK, snn.RECORD_BLOCKED4])
+@pytest.mark.parametrize("nspk", [1, 63, 64, 700, 1024, 1025, 2048, 2049, 3000, 9000])
+def test_blocked_deliver_spikes_matches_oracle_network(model, tiny, nspk, fmt):
     """Phase 2 alone with blocked records, below (reductions straight into the ring) and
-    above (shared-memory sums) the 64-sender switch and across the 1,024-sender staging
-    passes, repeats included: the ring equals the sums over the oracle's rows."""
+    above (shared-memory sums) the 64-sender switch and across the 2,048-sender staging
+    passes, repeats included: the ring equals the sums over the oracle's rows (bfloat16 read-back
+    weights for BLOCKED4)."""
     wl, onet = tiny
-    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=BLK)
+    if fmt == snn.RECORD_BLOCKED4:
+        onet = oracle.with_weights(onet, oracle.quantize_bf16(onet.w_fx))
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=fmt)
     rng = np.random.default_rng(100 + nspk)
     spikers = rng.integers(0, onet.n, nspk).astype(np.int32)
     t = 61
