@@ -587,6 +587,55 @@ def run_gpu(args):
 
     torch.cuda.empty_cache()
 
+    # phase 2 alone on block-major records (the resident engine's layout): one CTA per
+    # target block reads only its region, where consecutive senders' segments are
+    # adjacent; the same random senders, and the same list sorted by sender
+    regions = []
+    if args.regions and args.saturating:
+        rnet = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, seed, steps_per_graph=tps,
+                           raster_capacity=1 << 25, device=dev, engine=snn.ENGINE_RESIDENT)
+        rinfo = rnet.info()
+        rring = rnet.device_view("ring", torch.int32, 64 * int(rnet.layout().n_neurons_padded))
+        nblk = int(rinfo.target_blocks)
+        for nsp in args.saturating:
+            for order in ("random", "sorted"):
+                ms_l, ev_l, nnz_l = [], [], []
+                for r in range(args.saturating_reps + 2):
+                    spk_np = rng.integers(0, n, nsp).astype(np.int32)
+                    if order == "sorted":
+                        spk_np.sort()
+                    spk = torch.from_numpy(spk_np).to(dev)
+                    rring.zero_()  # so that the entries this launch updates can be counted
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize(dev)
+                    if args.profile_region == "regions":
+                        torch.cuda.profiler.start()
+                    e0.record(stream)
+                    rnet.deliver_spikes(spk, 0)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    if args.profile_region == "regions":
+                        torch.cuda.profiler.stop()
+                    if r >= 2:
+                        ms_l.append(e0.elapsed_time(e1))
+                        ev_l.append(int(outdeg[spk_np].sum()))
+                        nnz_l.append(int(torch.count_nonzero(rring).item()))
+                ms_avg, ev_avg, nnz = float(np.mean(ms_l)), float(np.mean(ev_l)), float(np.mean(nnz_l))
+                # own bytes: 9 B per record (target, weight, delay); per sender its list
+                # entry and its two segment offsets in every block's table; 8 B (read +
+                # write) per ring entry updated
+                nbytes = 9 * ev_avg + (4 + 8 * nblk) * nsp + 8 * nnz
+                plain_ms = [p_["ms"] for p_ in sat if p_["spikers"] == nsp]
+                regions.append({"spikers": nsp, "order": order, "events": ev_avg, "ms": ms_avg,
+                                "events_per_s": ev_avg / (ms_avg * 1e-3), "bytes": nbytes,
+                                "gbs": nbytes / (ms_avg * 1e-3) / 1e9, "frac": nbytes / (ms_avg * 1e-3) / 1e9 / peak,
+                                "ring_entries_updated": nnz,
+                                "speedup_vs_plain": float(plain_ms[0] / ms_avg) if plain_ms else None})
+        rnet.close()
+        del rring
+        torch.cuda.empty_cache()
+
     def run_workload(label, circuits=None, wlx=None, fmt=snn.RECORD_PLAIN9, n_steps=None, tune=False, weng=None,
                      region=None):
         """Build, optionally autotune, warm up and time a workload; returns a summary.  With
@@ -718,7 +767,14 @@ def run_gpu(args):
                                 "blocked4": {"kernel": "k_deliver_blocked",
                                              "traffic_20480": _recorded_traffic("k_deliver_blocked_bf16"),
                                              "note": "the same with bfloat16 weights (4 B per event)",
-                                             "points": forms.get("blocked4", {}).get("delivery_saturating")}},
+                                             "points": forms.get("blocked4", {}).get("delivery_saturating")},
+                                "block_major": {"kernel": "k_deliver_regions",
+                                                "note": "the resident engine's block-major records (9 B per event): "
+                                                        "one CTA per target block reads its region's segments; frac "
+                                                        "on its own bytes (records, per-sender offsets in every "
+                                                        "block's table, 8 B per ring entry updated); random and "
+                                                        "sorted sender lists",
+                                                "points": regions}},
         "clocks": clk.summary(), "build_s": build_s,
         "paper_context": {"fpga_best_rtf": 0.79, "hardware": "Intel Agilex 7 FPGA (horiz/multi/s)"},
     }
@@ -763,10 +819,12 @@ def main():
     ap.add_argument("--batched-groups", type=int, default=-1,
                     help="circuits per group for the batched workload instead of autotuning (-1: autotune)")
     ap.add_argument("--x4-steps", type=int, default=10240)
-    ap.add_argument("--profile-region", choices=["none", "timed", "saturating", "batched", "x4"], default="none",
+    ap.add_argument("--profile-region", choices=["none", "timed", "saturating", "regions", "batched", "x4"],
+                    default="none",
                     help="bracket that region (the main timed region, the saturating delivery launches, or a "
                          "workload's timed region) with cudaProfilerStart/Stop")
     ap.add_argument("--form-steps", type=int, default=20)
+    ap.add_argument("--regions", type=int, default=1, help="saturating delivery on block-major records (0: skip)")
     ap.add_argument("--seeds", type=int, default=10, help="network instances timed for the mean RTF (0: none)")
     ap.add_argument("--seed-steps", type=int, default=10, help="bench steps timed per instance")
     ap.add_argument("--engine", default="default", choices=["default", "graph", "persistent", "pipelined", "resident"])

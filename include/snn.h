@@ -417,7 +417,8 @@ int snn_load_state(snn_net *net, const void *host_buf, uint64_t bytes);
  * synapse of the senders spikers[0 .. n_spikers) (device int32 neuron ids, each
  * below n_neurons; repeats allowed) into the ring as spikes of step t, i.e.
  * W[(t + d) mod 64][target] += w, in one launch of `blocks` CTAs (0 = full
- * occupancy; SNN_RECORD_BLOCKED6 always launches one CTA per target block) on
+ * occupancy; the blocked formats and the resident engine's block-major records always
+ * launch one CTA per target block, which reads only its block's segments) on
  * `cuda_stream`; returns without waiting.  The ring keeps the added
  * input, so the simulated dynamics change accordingly.
  * Errors: SNN_EINVAL (null or negative arguments), SNN_ECUDA. */

@@ -1342,8 +1342,12 @@ int snn_deliver_spikes(snn_net *net, const int32_t *spikers, int64_t n_spikers, 
     if (!net || (n_spikers > 0 && !spikers)) return fail(SNN_EINVAL, "null argument");
     if (n_spikers < 0 || t < 0 || blocks < 0) return fail(SNN_EINVAL, "negative argument");
     if (n_spikers == 0) return SNN_OK;
-    if (net->engine == SNN_ENGINE_RESIDENT)
-        return fail(SNN_ENOTSUP, "the resident engine stores its records block-major, not as rows");
+    if (net->engine == SNN_ENGINE_RESIDENT) {
+        // block-major records: each target block's CTA reads its region's segments
+        const int e = snn::launch_deliver_regions(net->args, spikers, n_spikers, t, cuda_stream);
+        if (e != 0) return fail(SNN_ECUDA, std::string("deliver: ") + cudaGetErrorString(static_cast<cudaError_t>(e)));
+        return SNN_OK;
+    }
     if (snn::is_blocked(net->format)) {
         snn::launch_deliver_blocked(net->args, spikers, n_spikers, t, 0, cuda_stream);
         SNN_CUDA_TRY(cudaGetLastError());

@@ -299,5 +299,8 @@ int prepare_resident_kernel(const StepArgs &a);
 int resident_blocks_per_sm(const StepArgs &a);
 // n_steps steps from the device's t_base in one cooperative launch of a.n_blocks CTAs
 int launch_resident(const StepArgs &a, int64_t n_steps, void *stream);
+// phase 2 alone for list[0 .. n) as spikes of step t on block-major records: one CTA per
+// target block, reads confined to the block's region
+int launch_deliver_regions(const StepArgs &a, const int32_t *list, int64_t n, int64_t t, void *stream);
 
 }  // namespace snn

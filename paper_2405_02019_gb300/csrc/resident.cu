@@ -703,6 +703,204 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
     }
 }
 
+
+// ---------------------------------------------------------------------------------
+// Phase 2 alone on block-major records (snn_deliver_spikes of a resident-engine
+// network): one CTA per target block p reads, for every sender of the list, that
+// sender's segment of block p's region (offsets from the block's exact segment table),
+// so all of its reads stay inside its own region, where consecutive senders' segments
+// are adjacent.  Per pass of kRegBatch senders the segments are concatenated; the
+// stream is taken in windows of kRegWindow records whose region index is tabled, and
+// each window in pipelined sets of kRegSet rounds (lane l of warp w: records
+// 32 (w + 32 k) + l), the next set's loads in flight while the current one is added.
+// With at least kBlockedAggregateMin senders the weights of delays up to
+// kBlockedBinDelays are summed per (delay, local target) in shared memory and added
+// to the ring once at the end (only this CTA writes these ring columns); longer delays,
+// and all of them for short lists, are reductions into the ring.
+// ---------------------------------------------------------------------------------
+constexpr int kRegThreads = 1024;
+constexpr int kRegWarps = kRegThreads / 32;
+constexpr int kRegBatch = 2048;   // senders per pass
+constexpr int kRegWindow = 8192;  // records whose region index is tabled at once
+constexpr int kRegSet = 2;        // rounds per pipelined set
+
+__host__ __device__ inline size_t regions_smem_bytes(int stride)
+{
+    return sizeof(int32_t) * (size_t(kBlockedBinDelays + 1) * stride + 3 * kRegBatch + kRegWarps + kRegWindow);
+}
+
+struct RegSet {
+    int32_t tg[kRegSet], w[kRegSet];
+    uint32_t d[kRegSet];
+};
+
+__device__ __forceinline__ void regions_load(const StepArgs &a, int64_t rbase, const uint32_t *ridx, int32_t w0,
+                                             int32_t w1, int32_t e0, int warp, int lane, RegSet &r)
+{
+#pragma unroll
+    for (int k = 0; k < kRegSet; ++k) {
+        const int32_t e = e0 + 32 * (warp + kRegWarps * k) + lane;
+        r.tg[k] = 0;
+        r.w[k] = 0;
+        r.d[k] = 1;
+        if (e < w1) {
+            const int64_t idx = rbase + ridx[e - w0];
+            r.tg[k] = __ldcs(a.syn_tgt + idx);
+            r.w[k] = __ldcs(a.syn_w + idx);
+            r.d[k] = __ldcs(a.syn_d + idx);
+        }
+    }
+}
+
+template <bool kAggregate>
+__device__ __forceinline__ void regions_apply(const StepArgs &a, int32_t *bins, int stride, int64_t t, int32_t base,
+                                              int32_t width, const RegSet &r)
+{
+#pragma unroll
+    for (int k = 0; k < kRegSet; ++k) {
+        const int lt = r.tg[k] - base;
+        if (r.w[k] == 0 || static_cast<uint32_t>(lt) >= static_cast<uint32_t>(width)) continue;
+        const int d = static_cast<int>(r.d[k]);
+        if (kAggregate && d <= kBlockedBinDelays) atomicAdd(bins + d * stride + lt, r.w[k]);
+        else red_add_s32(a.ring + ((t + d) & kDMask) * a.npad + base + lt, r.w[k]);
+    }
+}
+
+template <bool kAggregate>
+__device__ __forceinline__ void regions_window(const StepArgs &a, int32_t *bins, int stride, const uint32_t *ridx,
+                                               int32_t w0, int32_t w1, int64_t t, int32_t base, int32_t width,
+                                               int64_t rbase)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int32_t kStep = kRegThreads * kRegSet;
+    RegSet A, Bs;
+    int32_t e0 = w0;
+    regions_load(a, rbase, ridx, w0, w1, e0, warp, lane, A);
+    for (;;) {
+        if (e0 + kStep < w1) regions_load(a, rbase, ridx, w0, w1, e0 + kStep, warp, lane, Bs);
+        regions_apply<kAggregate>(a, bins, stride, t, base, width, A);
+        e0 += kStep;
+        if (e0 >= w1) break;
+        if (e0 + kStep < w1) regions_load(a, rbase, ridx, w0, w1, e0 + kStep, warp, lane, A);
+        regions_apply<kAggregate>(a, bins, stride, t, base, width, Bs);
+        e0 += kStep;
+        if (e0 >= w1) break;
+    }
+}
+
+// Exclusive prefix over the CTA of one value per thread into out[threadIdx.x]; returns
+// the total.
+__device__ __forceinline__ int32_t regions_scan(int32_t v, int32_t *out, int32_t *warp_sums)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = lane < kRegWarps ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kRegWarps) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    out[threadIdx.x] = (warp > 0 ? warp_sums[warp - 1] : 0) + x - v;
+    return warp_sums[kRegWarps - 1];
+}
+
+__global__ void __launch_bounds__(kRegThreads, 1)
+    k_deliver_regions(const StepArgs a, const int32_t *list, int64_t nspk, int64_t t)
+{
+    extern __shared__ int4 reg_smem4[];
+    const int stride = a.res_stride;
+    int32_t *bins = reinterpret_cast<int32_t *>(reg_smem4);                            // [33][stride]
+    uint32_t *seg_st = reinterpret_cast<uint32_t *>(bins + (kBlockedBinDelays + 1) * stride);  // [kRegBatch]
+    int32_t *pfx = reinterpret_cast<int32_t *>(seg_st + kRegBatch);                    // [kRegBatch]
+    int32_t *seg_n = pfx + kRegBatch;                                                  // [kRegBatch]
+    int32_t *warp_sums = seg_n + kRegBatch;                                            // [kRegWarps]
+    uint32_t *ridx = reinterpret_cast<uint32_t *>(warp_sums + kRegWarps);              // [kRegWindow]
+
+    const int p = blockIdx.x, tid = threadIdx.x;
+    const int32_t base = __ldg(a.blk_off + p);
+    const int32_t width = __ldg(a.blk_off + p + 1) - base;
+    const int64_t rbase = __ldg(a.res_rbase + p);
+    const uint32_t *offt = a.res_offt + static_cast<int64_t>(p) * (a.n + 1);
+    const bool aggregate = nspk >= kBlockedAggregateMin;
+    constexpr int kPer = kRegBatch / kRegThreads;
+    if (aggregate)
+        for (int j = tid; j < (kBlockedBinDelays + 1) * stride; j += kRegThreads) bins[j] = 0;
+    for (int64_t b0 = 0; b0 < nspk; b0 += kRegBatch) {
+        const int nb = static_cast<int>(nspk - b0 < kRegBatch ? nspk - b0 : kRegBatch);
+        int32_t mine = 0;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int j = tid * kPer + i;
+            int32_t len = 0;
+            if (j < nb) {
+                const int32_t s = __ldcg(list + b0 + j);
+                if (static_cast<uint32_t>(s) < static_cast<uint64_t>(a.n)) {
+                    const uint32_t st = __ldg(offt + s);
+                    seg_st[j] = st;
+                    len = static_cast<int32_t>(__ldg(offt + s + 1) - st);
+                }
+            }
+            seg_n[j] = len;
+            mine += len;
+        }
+        int32_t *scan_out = reinterpret_cast<int32_t *>(ridx);  // the window table is idle here
+        const int32_t total = regions_scan(mine, scan_out, warp_sums);
+        {
+            int32_t run = scan_out[tid];
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) {
+                pfx[tid * kPer + i] = run;
+                run += seg_n[tid * kPer + i];
+            }
+        }
+        __syncthreads();
+        for (int32_t w0 = 0; w0 < total; w0 += kRegWindow) {
+            const int32_t w1 = total - w0 < kRegWindow ? total : w0 + kRegWindow;
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) {
+                const int j = tid * kPer + i;
+                if (j >= nb) break;
+                const int32_t lo = max(pfx[j], w0), hi = min(pfx[j] + seg_n[j], w1);
+                const uint32_t r0 = seg_st[j] - static_cast<uint32_t>(pfx[j]);
+                for (int32_t e = lo; e < hi; ++e) ridx[e - w0] = r0 + static_cast<uint32_t>(e);
+            }
+            __syncthreads();
+            if (aggregate) regions_window<true>(a, bins, stride, ridx, w0, w1, t, base, width, rbase);
+            else regions_window<false>(a, bins, stride, ridx, w0, w1, t, base, width, rbase);
+            __syncthreads();  // the table is rebuilt for the next window
+        }
+    }
+    if (!aggregate) return;
+    // the sums of delays 1..kBlockedBinDelays into their ring rows (plain read-modify-
+    // writes: only this CTA writes these columns during the launch); stride and the ring
+    // row are multiples of 4, and the last block's extra columns lie inside the padded row
+    const int w4 = (width + 3) >> 2, s4 = stride >> 2;
+    for (int q = tid; q < kBlockedBinDelays * w4; q += kRegThreads) {
+        const int d = 1 + q / w4;
+        const int c4 = q - (d - 1) * w4;
+        const int4 v = reinterpret_cast<const int4 *>(bins)[d * s4 + c4];
+        if ((v.x | v.y | v.z | v.w) == 0) continue;
+        int4 *dst = reinterpret_cast<int4 *>(a.ring + ((t + d) & kDMask) * a.npad + base) + c4;
+        int4 o = __ldcg(dst);
+        o.x = static_cast<int32_t>(static_cast<uint32_t>(o.x) + static_cast<uint32_t>(v.x));
+        o.y = static_cast<int32_t>(static_cast<uint32_t>(o.y) + static_cast<uint32_t>(v.y));
+        o.z = static_cast<int32_t>(static_cast<uint32_t>(o.z) + static_cast<uint32_t>(v.z));
+        o.w = static_cast<int32_t>(static_cast<uint32_t>(o.w) + static_cast<uint32_t>(v.w));
+        __stcg(dst, o);
+    }
+}
+
 }  // namespace
 
 int64_t resident_width(int64_t n, int num_sms)
@@ -729,8 +927,19 @@ int resident_rows(int stride, int cap, int64_t n)
 
 int prepare_resident_kernel(const StepArgs &a)
 {
-    return static_cast<int>(cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(resident_smem_bytes(a.res_rows, a.res_stride, a.n))));
+    cudaError_t e = cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(resident_smem_bytes(a.res_rows, a.res_stride, a.n)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_deliver_regions, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(regions_smem_bytes(a.res_stride)));
+    return static_cast<int>(e);
+}
+
+int launch_deliver_regions(const StepArgs &a, const int32_t *list, int64_t n, int64_t t, void *stream)
+{
+    k_deliver_regions<<<a.n_blocks, kRegThreads, regions_smem_bytes(a.res_stride), static_cast<cudaStream_t>(stream)>>>(
+        a, list, n, t);
+    return static_cast<int>(cudaGetLastError());
 }
 
 int resident_blocks_per_sm(const StepArgs &a)

@@ -136,8 +136,29 @@ def test_resident_structure_tiny(model, tiny):
             assert np.array_equal(o, g), (i, b)
             assert np.all(np.diff(d[a0:a1].astype(int)) >= 0)
             assert np.all((tg[a0:a1] >= bounds[b]) & (tg[a0:a1] < bounds[b + 1]))
-    with pytest.raises(snn.SnnError):  # records are not rows: phase 2 alone is refused
-        net.deliver_spikes(torch.zeros(1, dtype=torch.int32, device="cuda"), 0)
+    net.close()
+
+
+@pytest.mark.parametrize("nspk", [1, 63, 64, 700, 2048, 2049, 9000])
+def test_resident_deliver_spikes_matches_oracle_network(model, tiny, nspk):
+    """Phase 2 alone on block-major records (one CTA per target block reading its
+    region's segments), below and above the 64-sender switch to shared-memory sums and
+    across 2,048-sender passes, repeats included: the ring equals the sums over the
+    oracle's rows."""
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, engine=RES)
+    rng = np.random.default_rng(300 + nspk)
+    spikers = rng.integers(0, onet.n, nspk).astype(np.int32)
+    t = 61
+    net.deliver_spikes(torch.from_numpy(spikers).cuda(), t)
+    torch.cuda.synchronize()
+    npad = int(net.layout().n_neurons_padded)
+    ring = net.device_view("ring", torch.int32, 64 * npad).cpu().numpy().reshape(64, npad).astype(np.int64)
+    lens = np.diff(onet.row_ptr)
+    idx = np.concatenate([np.arange(onet.row_ptr[s], onet.row_ptr[s] + lens[s]) for s in spikers])
+    flat = ((t + onet.delay[idx].astype(np.int64)) % 64) * npad + onet.post[idx]
+    exp = np.bincount(flat, weights=onet.w_fx[idx].astype(np.float64), minlength=64 * npad)
+    assert np.array_equal(ring, exp.astype(np.int64).reshape(64, npad))
     net.close()
 
 
