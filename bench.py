@@ -59,7 +59,7 @@ def _kernel_sources_hash() -> str:
 
     csrc = os.path.join(ROOT, "paper_2405_02019_gb300", "csrc")
     lines = []
-    for f in ("kernels.cu", "internal.hpp"):
+    for f in ("kernels.cu", "resident.cu", "internal.hpp"):
         for line in open(os.path.join(csrc, f), encoding="utf-8"):
             code = line.strip()
             if code and not code.startswith("//"):
