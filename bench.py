@@ -513,9 +513,10 @@ def run_gpu(args):
 
     # compressed synapse records on the same workload: step time and saturating delivery
     forms = {}
-    blocked_formats = (snn.RECORD_BLOCKED6, snn.RECORD_BLOCKED4)
+    blocked_formats = (snn.RECORD_BLOCKED6, snn.RECORD_BLOCKED4, snn.RECORD_BLOCKED8)
     for fname, fmt in (("int8_pair", snn.RECORD_PACKED_I8), ("bf16", snn.RECORD_PACKED_BF16),
-                       ("blocked6", snn.RECORD_BLOCKED6), ("blocked4", snn.RECORD_BLOCKED4)):
+                       ("blocked6", snn.RECORD_BLOCKED6), ("blocked4", snn.RECORD_BLOCKED4),
+                       ("blocked8", snn.RECORD_BLOCKED8)):
         if fname not in args.forms:
             continue
         feng = snn.ENGINE_DEFAULT if fmt in blocked_formats else others
@@ -768,6 +769,11 @@ def run_gpu(args):
                                              "traffic_20480": _recorded_traffic("k_deliver_blocked_bf16"),
                                              "note": "the same with bfloat16 weights (4 B per event)",
                                              "points": forms.get("blocked4", {}).get("delivery_saturating")},
+                                "blocked8": {"kernel": "k_deliver_blocked",
+                                             "traffic_20480": _recorded_traffic("k_deliver_blocked_8"),
+                                             "note": "exact weights interleaved with the records (8 B per event): "
+                                                     "one contiguous read per segment",
+                                             "points": forms.get("blocked8", {}).get("delivery_saturating")},
                                 "block_major": {"kernel": "k_deliver_regions",
                                                 "note": "the resident engine's block-major records (9 B per event): "
                                                         "one CTA per target block reads its region's segments; frac "
@@ -813,7 +819,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--saturating", type=int, nargs="*", default=[2048, 8192, 20480])
     ap.add_argument("--saturating-reps", type=int, default=5)
-    ap.add_argument("--forms", nargs="*", default=["int8_pair", "bf16", "blocked6", "blocked4"])
+    ap.add_argument("--forms", nargs="*", default=["int8_pair", "bf16", "blocked6", "blocked4", "blocked8"])
     ap.add_argument("--extra", nargs="*", default=["batched", "x4"])
     ap.add_argument("--batched-steps", type=int, default=20480)
     ap.add_argument("--batched-groups", type=int, default=-1,

@@ -178,14 +178,21 @@ typedef struct snn_circuit {
  *                           current of SNN_RECORD_PACKED_BF16: every quad of a segment is
  *                           one 16-byte unit (four uint16 records, then four bfloat16
  *                           weights), 4 bytes per synapse.  Same rules as BLOCKED6.
+ *   SNN_RECORD_BLOCKED8:    the same target-blocked rows, exact, with weight and record
+ *                           interleaved: a synapse is the int32 weight then the uint32
+ *                           record (target - block start : 10 | delay : 6), 8 bytes, so a
+ *                           segment is one contiguous run of 32-byte quads (one read per
+ *                           segment instead of two).  Same rules as BLOCKED6.
  * Packed formats hold up to 2^20 neurons.  The dynamics are the plain ones applied to
- * the read-back weights (unchanged for SNN_RECORD_BLOCKED6); accumulation stays int32.
+ * the read-back weights (unchanged for SNN_RECORD_BLOCKED6 and _BLOCKED8); accumulation
+ * stays int32.
  */
 #define SNN_RECORD_PLAIN9 0
 #define SNN_RECORD_PACKED_I8 1
 #define SNN_RECORD_PACKED_BF16 2
 #define SNN_RECORD_BLOCKED6 3
 #define SNN_RECORD_BLOCKED4 4
+#define SNN_RECORD_BLOCKED8 5
 typedef struct snn_spec {
     uint32_t abi_version; /* must be SNN_ABI_VERSION */
     int32_t scale_n_permille;

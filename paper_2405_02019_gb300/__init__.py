@@ -18,7 +18,7 @@ import numpy as np
 from . import _abi
 from ._abi import (ABI_VERSION, D_MAX, ENGINE_DEFAULT, ENGINE_GRAPH, ENGINE_PERSISTENT, ENGINE_PIPELINED,  # noqa: F401
                    ENGINE_RESIDENT,
-                   RECORD_BLOCKED4, RECORD_BLOCKED6, RECORD_PACKED_BF16, RECORD_PACKED_I8, RECORD_PLAIN9,
+                   RECORD_BLOCKED4, RECORD_BLOCKED6, RECORD_BLOCKED8, RECORD_PACKED_BF16, RECORD_PACKED_I8, RECORD_PLAIN9,
                    FX_SHIFT, MAX_POPS, POISSON_KMAX, SNN_EOVERFLOW, SNN_ETIMEOUT, load, snn_info, snn_layout,
                    snn_sizes, snn_spec)
 

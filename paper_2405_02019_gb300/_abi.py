@@ -12,7 +12,7 @@ FX_SHIFT = 12
 POISSON_KMAX = 24
 ABI_VERSION = 2
 ENGINE_DEFAULT, ENGINE_GRAPH, ENGINE_PERSISTENT, ENGINE_PIPELINED, ENGINE_RESIDENT = 0, 1, 2, 3, 4
-RECORD_PLAIN9, RECORD_PACKED_I8, RECORD_PACKED_BF16, RECORD_BLOCKED6, RECORD_BLOCKED4 = 0, 1, 2, 3, 4
+RECORD_PLAIN9, RECORD_PACKED_I8, RECORD_PACKED_BF16, RECORD_BLOCKED6, RECORD_BLOCKED4, RECORD_BLOCKED8 = 0, 1, 2, 3, 4, 5
 
 STATUS = {0: "SNN_OK", 1: "SNN_EINVAL", 2: "SNN_ENOMEM", 3: "SNN_ECUDA", 4: "SNN_EOVERFLOW",
           5: "SNN_ETIMEOUT", 6: "SNN_ESTATE", 7: "SNN_ENOTSUP"}

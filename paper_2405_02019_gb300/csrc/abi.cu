@@ -667,10 +667,9 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
                     "tgt");
             cuda_ok(cudaMemcpyAsync(A + L.syn_w, hn.w.data(), 4 * net->n_syn_padded, cudaMemcpyHostToDevice, st), "w");
             cuda_ok(cudaMemcpyAsync(A + L.syn_d, hn.d.data(), net->n_syn_padded, cudaMemcpyHostToDevice, st), "d");
-        } else if (hn.format == SNN_RECORD_BLOCKED4) {
+        } else if (hn.format == SNN_RECORD_BLOCKED4 || hn.format == SNN_RECORD_BLOCKED8) {
             if (net->n_syn_padded > 0)
-                cuda_ok(cudaMemcpyAsync(A + L.syn_tgt, hn.word.data(), 4 * net->n_syn_padded, cudaMemcpyHostToDevice,
-                                        st),
+                cuda_ok(cudaMemcpyAsync(A + L.syn_tgt, hn.word.data(), 4 * hn.word.size(), cudaMemcpyHostToDevice, st),
                         "record quads");
             cuda_ok(cudaMemcpyAsync(A + L.syn_d, hn.seg.data(), 2 * hn.seg.size(), cudaMemcpyHostToDevice, st),
                     "block table");

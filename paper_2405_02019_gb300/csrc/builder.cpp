@@ -223,7 +223,7 @@ bool validate_spec(const snn_spec &spec, std::string &why)
         if (spec.record_format != SNN_RECORD_PLAIN9) return fail("the resident engine reads plain records");
         if (count_neurons(spec) > kResidentMaxNeurons) return fail("more neurons than the resident engine holds");
     }
-    if (spec.record_format < SNN_RECORD_PLAIN9 || spec.record_format > SNN_RECORD_BLOCKED4)
+    if (spec.record_format < SNN_RECORD_PLAIN9 || spec.record_format > SNN_RECORD_BLOCKED8)
         return fail("unknown record_format");
     if ((spec.record_format == SNN_RECORD_PACKED_I8 || spec.record_format == SNN_RECORD_PACKED_BF16) &&
         count_neurons(spec) > kPackedMaxNeurons)
@@ -306,11 +306,15 @@ Layout make_layout(const snn_spec &spec)
     if (is_blocked(fmt)) {
         // rows of quad-padded block segments (a nonempty segment gains at most
         // kBlockQuad - 1 pad entries): BLOCKED6 keeps uint16 records and int32 weights,
-        // BLOCKED4 16-byte quads of records and bfloat16 weights; then the per-row block table
+        // BLOCKED4 16-byte quads of records and bfloat16 weights, BLOCKED8 interleaved
+        // (weight, record) pairs; then the per-row block table
         L.syn_padded_max = s + (kBlockQuad - 1) * std::min<int64_t>(s, n * int64_t{max_target_blocks(n)});
         if (fmt == SNN_RECORD_BLOCKED6) {
             L.syn_tgt = o; o = up(o + 2 * L.syn_padded_max + 16);
             L.syn_w = o; o = up(o + 4 * L.syn_padded_max + 16);
+        } else if (fmt == SNN_RECORD_BLOCKED8) {
+            L.syn_tgt = o; o = up(o + 8 * L.syn_padded_max + 16);
+            L.syn_w = o; o = up(o + 16);
         } else {
             L.syn_tgt = o; o = up(o + 4 * L.syn_padded_max + 16);
             L.syn_w = o; o = up(o + 16);
@@ -624,6 +628,18 @@ bool pack_blocked(HostNetwork &net, int nthreads, int num_sms, std::string &why)
                 net.word[e + 1] = uint32_t{net.rec16[e + 2]} | uint32_t{net.rec16[e + 3]} << 16;
                 net.word[e + 2] = uint32_t{h[0]} | uint32_t{h[1]} << 16;
                 net.word[e + 3] = uint32_t{h[2]} | uint32_t{h[3]} << 16;
+            }
+        });
+        std::vector<uint16_t>().swap(net.rec16);
+        std::vector<int32_t>().swap(net.w);
+    } else if (net.format == SNN_RECORD_BLOCKED8) {
+        // synapse e: word 2e its int32 weight, word 2e+1 its record (local target | delay
+        // << 10), so a quad is 32 contiguous bytes
+        net.word.assign(2 * S, 0);
+        parallel_for(nthreads, S, [&](int, int64_t e0, int64_t e1) {
+            for (int64_t e = e0; e < e1; ++e) {
+                net.word[2 * e] = static_cast<uint32_t>(w[e]);
+                net.word[2 * e + 1] = uint32_t{net.rec16[e]};
             }
         });
         std::vector<uint16_t>().swap(net.rec16);

@@ -82,9 +82,13 @@ inline int record_bytes(int format)
     return format == SNN_RECORD_PACKED_I8                                         ? 5
            : format == SNN_RECORD_PACKED_BF16 || format == SNN_RECORD_BLOCKED6 ? 6
            : format == SNN_RECORD_BLOCKED4                                      ? 4
+           : format == SNN_RECORD_BLOCKED8                                      ? 8
                                                                                 : 9;
 }
-inline bool is_blocked(int format) { return format == SNN_RECORD_BLOCKED6 || format == SNN_RECORD_BLOCKED4; }
+inline bool is_blocked(int format)
+{
+    return format == SNN_RECORD_BLOCKED6 || format == SNN_RECORD_BLOCKED4 || format == SNN_RECORD_BLOCKED8;
+}
 
 // Blocked records: target blocks and the delivery kernel that owns one block per CTA.
 constexpr int kBlockLocalBits = 10;          // record = local target | delay << 10

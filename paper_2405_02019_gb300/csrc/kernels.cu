@@ -787,30 +787,37 @@ __device__ __forceinline__ int32_t bf16_fx(uint32_t h)
 // a window.
 constexpr int kBlockedSet = kBlockedRounds / 2;  // rounds per pipelined set
 
+// A set's loads are kept raw (decoded only when added, so that issuing the next set
+// never waits for this one): per round two 16-byte values, used per format as
+//   BLOCKED6: va.xy = the quad's four uint16 records, vb = its four int32 weights;
+//   BLOCKED4: va = the 16-byte unit (records, then bfloat16 currents);
+//   BLOCKED8: va, vb = the 32-byte quad of (int32 weight, uint32 record) pairs.
 template <int FMT>
 __device__ __forceinline__ void blocked_load_set(const StepArgs &a, const uint32_t *qidx, int32_t w0, int32_t w1,
-                                                 int32_t e0, uint2 (&rec)[kBlockedSet], int4 (&w)[kBlockedSet])
+                                                 int32_t e0, uint4 (&va)[kBlockedSet], uint4 (&vb)[kBlockedSet])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint2 *recq = reinterpret_cast<const uint2 *>(a.blk_rec);
-    const int4 *wq = reinterpret_cast<const int4 *>(a.syn_w);
+    const uint4 *wq = reinterpret_cast<const uint4 *>(a.syn_w);
     const uint4 *q16 = reinterpret_cast<const uint4 *>(a.blk_rec);
 #pragma unroll
     for (int k = 0; k < kBlockedSet; ++k) {
         // round k of a set is quads e0 + 32 * (warp + kBlockedWarps * k) + lane: the warps
         // of the CTA interleave, so that a window's rounds spread evenly over them
         const int32_t e = e0 + 32 * (warp + kBlockedWarps * k) + lane;
-        rec[k] = make_uint2(0, 0);
-        w[k] = make_int4(0, 0, 0, 0);
+        va[k] = make_uint4(0, 0, 0, 0);
+        vb[k] = make_uint4(0, 0, 0, 0);
         if (e < w1) {
             const uint32_t q = qidx[e - w0];
             if (FMT == SNN_RECORD_BLOCKED4) {
-                const uint4 v = __ldcs(q16 + q);
-                rec[k] = make_uint2(v.x, v.y);
-                w[k] = make_int4(static_cast<int32_t>(v.z), static_cast<int32_t>(v.w), 0, 0);  // decoded below
+                va[k] = __ldcs(q16 + q);
+            } else if (FMT == SNN_RECORD_BLOCKED8) {
+                va[k] = __ldcs(q16 + 2 * uint64_t(q));
+                vb[k] = __ldcs(q16 + 2 * uint64_t(q) + 1);
             } else {
-                rec[k] = __ldcs(recq + q);
-                w[k] = __ldcs(wq + q);
+                const uint2 r = __ldcs(recq + q);
+                va[k] = make_uint4(r.x, r.y, 0, 0);
+                vb[k] = __ldcs(wq + q);
             }
         }
     }
@@ -818,23 +825,39 @@ __device__ __forceinline__ void blocked_load_set(const StepArgs &a, const uint32
 
 template <bool kAggregate, int FMT>
 __device__ __forceinline__ void blocked_apply_set(const StepArgs &a, int32_t *bins, int64_t t, int32_t base,
-                                                  const uint2 (&rec)[kBlockedSet], const int4 (&w)[kBlockedSet])
+                                                  const uint4 (&va)[kBlockedSet], const uint4 (&vb)[kBlockedSet])
 {
 #pragma unroll
     for (int k = 0; k < kBlockedSet; ++k) {
-        int32_t w0v = w[k].x, w1v = w[k].y, w2v = w[k].z, w3v = w[k].w;
+        uint32_t r01, r23;
+        int32_t w0v, w1v, w2v, w3v;
         if (FMT == SNN_RECORD_BLOCKED4) {
-            const uint32_t h01 = static_cast<uint32_t>(w[k].x), h23 = static_cast<uint32_t>(w[k].y);
-            w0v = bf16_fx(h01);
-            w1v = bf16_fx(h01 >> 16);
-            w2v = bf16_fx(h23);
-            w3v = bf16_fx(h23 >> 16);
+            r01 = va[k].x;
+            r23 = va[k].y;
+            w0v = bf16_fx(va[k].z);
+            w1v = bf16_fx(va[k].z >> 16);
+            w2v = bf16_fx(va[k].w);
+            w3v = bf16_fx(va[k].w >> 16);
+        } else if (FMT == SNN_RECORD_BLOCKED8) {
+            r01 = (va[k].y & 0xffffu) | (va[k].w << 16);
+            r23 = (vb[k].y & 0xffffu) | (vb[k].w << 16);
+            w0v = static_cast<int32_t>(va[k].x);
+            w1v = static_cast<int32_t>(va[k].z);
+            w2v = static_cast<int32_t>(vb[k].x);
+            w3v = static_cast<int32_t>(vb[k].z);
+        } else {
+            r01 = va[k].x;
+            r23 = va[k].y;
+            w0v = static_cast<int32_t>(vb[k].x);
+            w1v = static_cast<int32_t>(vb[k].y);
+            w2v = static_cast<int32_t>(vb[k].z);
+            w3v = static_cast<int32_t>(vb[k].w);
         }
         // quads past the window end were left zero: zero weights add nothing
-        blocked_apply<kAggregate>(a, bins, t, base, rec[k].x & 0xffffu, w0v);
-        blocked_apply<kAggregate>(a, bins, t, base, rec[k].x >> 16, w1v);
-        blocked_apply<kAggregate>(a, bins, t, base, rec[k].y & 0xffffu, w2v);
-        blocked_apply<kAggregate>(a, bins, t, base, rec[k].y >> 16, w3v);
+        blocked_apply<kAggregate>(a, bins, t, base, r01 & 0xffffu, w0v);
+        blocked_apply<kAggregate>(a, bins, t, base, r01 >> 16, w1v);
+        blocked_apply<kAggregate>(a, bins, t, base, r23 & 0xffffu, w2v);
+        blocked_apply<kAggregate>(a, bins, t, base, r23 >> 16, w3v);
     }
 }
 
@@ -843,17 +866,16 @@ __device__ __forceinline__ void blocked_window(const StepArgs &a, int32_t *bins,
                                                int32_t w1, int64_t t, int32_t base)
 {
     constexpr int32_t kStep = kBlockedThreads * kBlockedSet;
-    uint2 recA[kBlockedSet], recB[kBlockedSet];
-    int4 wA[kBlockedSet], wB[kBlockedSet];
+    uint4 aA[kBlockedSet], bA[kBlockedSet], aB[kBlockedSet], bB[kBlockedSet];
     int32_t e0 = w0;
-    blocked_load_set<FMT>(a, qidx, w0, w1, e0, recA, wA);
+    blocked_load_set<FMT>(a, qidx, w0, w1, e0, aA, bA);
     for (;;) {
-        if (e0 + kStep < w1) blocked_load_set<FMT>(a, qidx, w0, w1, e0 + kStep, recB, wB);
-        blocked_apply_set<kAggregate, FMT>(a, bins, t, base, recA, wA);
+        if (e0 + kStep < w1) blocked_load_set<FMT>(a, qidx, w0, w1, e0 + kStep, aB, bB);
+        blocked_apply_set<kAggregate, FMT>(a, bins, t, base, aA, bA);
         e0 += kStep;
         if (e0 >= w1) break;
-        if (e0 + kStep < w1) blocked_load_set<FMT>(a, qidx, w0, w1, e0 + kStep, recA, wA);
-        blocked_apply_set<kAggregate, FMT>(a, bins, t, base, recB, wB);
+        if (e0 + kStep < w1) blocked_load_set<FMT>(a, qidx, w0, w1, e0 + kStep, aA, bA);
+        blocked_apply_set<kAggregate, FMT>(a, bins, t, base, aB, bB);
         e0 += kStep;
         if (e0 >= w1) break;
     }
@@ -1037,6 +1059,9 @@ int prepare_blocked_kernel()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_deliver_blocked<SNN_RECORD_BLOCKED4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_deliver_blocked<SNN_RECORD_BLOCKED8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 bytes);
     return static_cast<int>(e);
 }
 
@@ -1045,6 +1070,8 @@ void launch_deliver_blocked(const StepArgs &a, const int32_t *list, int64_t n, i
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (a.format == SNN_RECORD_BLOCKED4)
         k_deliver_blocked<SNN_RECORD_BLOCKED4><<<a.n_blocks, kBlockedThreads, kBlockedSmemBytes, st>>>(a, list, n, t, k);
+    else if (a.format == SNN_RECORD_BLOCKED8)
+        k_deliver_blocked<SNN_RECORD_BLOCKED8><<<a.n_blocks, kBlockedThreads, kBlockedSmemBytes, st>>>(a, list, n, t, k);
     else
         k_deliver_blocked<SNN_RECORD_BLOCKED6><<<a.n_blocks, kBlockedThreads, kBlockedSmemBytes, st>>>(a, list, n, t, k);
 }

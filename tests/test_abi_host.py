@@ -125,7 +125,10 @@ def test_blocked_records_sizes_and_rules(lib):
     b4 = snn.snn_query_sizes(snn._Spec(m, 1000, 1000, 1, record_format=snn.RECORD_BLOCKED4).spec)
     assert b4.n_synapses_padded_max == blk.n_synapses_padded_max
     assert b4.arena_bytes < blk.arena_bytes - 2 * S  # 4 instead of 6 bytes per (padded) synapse
-    for fmt in (snn.RECORD_BLOCKED6, snn.RECORD_BLOCKED4):
+    b8 = snn.snn_query_sizes(snn._Spec(m, 1000, 1000, 1, record_format=snn.RECORD_BLOCKED8).spec)
+    assert b8.n_synapses_padded_max == blk.n_synapses_padded_max
+    assert b8.arena_bytes > blk.arena_bytes + 2 * S  # 8 instead of 6 bytes per (padded) synapse
+    for fmt in (snn.RECORD_BLOCKED6, snn.RECORD_BLOCKED4, snn.RECORD_BLOCKED8):
         for engine in (snn.ENGINE_PIPELINED, snn.ENGINE_PERSISTENT):
             spec = snn._Spec(m, 100, 100, 1, record_format=fmt, engine=engine).spec
             with pytest.raises(snn.SnnError):

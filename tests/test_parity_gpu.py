@@ -769,7 +769,12 @@ def _check_blocked_structure(net, onet, rows=None):
     seg = net.device_view("syn_delay", torch.int16, n * (B + 1)).cpu().numpy().view(np.uint16)
     seg = seg.reshape(n, B + 1).astype(np.int64)
     q = 4  # records per padding unit (a quad)
-    if info.record_format == snn.RECORD_BLOCKED4:
+    if info.record_format == snn.RECORD_BLOCKED8:
+        pairs = net.device_view("syn_tgt", torch.int32, 2 * SP).cpu().numpy().reshape(-1, 2)
+        w = np.ascontiguousarray(pairs[:, 0])
+        assert np.all((pairs[:, 1] >> 16) == 0)  # the record is a zero-extended uint16
+        rec = pairs[:, 1].astype(np.uint16)
+    elif info.record_format == snn.RECORD_BLOCKED4:
         quads = net.device_view("syn_tgt", torch.int16, 2 * SP).cpu().numpy().view(np.uint16).reshape(-1, 8)
         rec = np.ascontiguousarray(quads[:, :4]).reshape(-1)
         w = _bf16_fx(np.ascontiguousarray(quads[:, 4:]).reshape(-1))
@@ -864,7 +869,7 @@ def _expected_ring(onet, spikers, t, npad):
     return exp.astype(np.int64).reshape(64, npad)
 
 
-@pytest.mark.parametrize("fmt", [BLK, snn.RECORD_BLOCKED4])
+@pytest.mark.parametrize("fmt", [BLK, snn.RECORD_BLOCKED4, snn.RECORD_BLOCKED8])
 @pytest.mark.parametrize("nspk", [1, 63, 64, 700, 1024, 1025, 2048, 2049, 3000, 9000])
 def test_blocked_deliver_spikes_matches_oracle_network(model, tiny, nspk, fmt):
     """Phase 2 alone with blocked records, below (reductions straight into the ring) and
@@ -971,6 +976,25 @@ def test_blocked4_structure_and_raster_tiny(model, tiny):
     pk.close()
 
 
+def test_blocked8_structure_and_raster_tiny(model, tiny):
+    """Blocked records with interleaved (int32 weight, record) pairs, 8 bytes per synapse:
+    the decoded network equals the oracle's exactly, and 1,000 steps give the oracle's
+    raster and state bit for bit."""
+    wl, onet = tiny
+    net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=snn.RECORD_BLOCKED8,
+                      steps_per_graph=96)
+    info = net.info()
+    assert info.record_format == snn.RECORD_BLOCKED8 and info.bytes_per_synapse == 8 and info.engine == GRAPH
+    _check_blocked_structure(net, onet)
+    net.step(1000)
+    g_t, g_i = net.read_spikes()
+    sim = oracle.Sim(model, onet, wl.seed)
+    o_t, o_i = sim.run(1000)
+    assert len(o_t) > 0 and np.array_equal(g_t, o_t) and np.array_equal(g_i, o_i)
+    _assert_same_state(net, sim)
+    net.close()
+
+
 @pytest.mark.parametrize("nspk", [37, 700, 3000])
 def test_blocked4_deliver_spikes_matches_oracle_network(model, tiny, nspk):
     wl, onet = tiny
@@ -1070,15 +1094,15 @@ def test_blocked_full_scale_parity(model, full):
     net.close()
     spikers = np.random.default_rng(7).integers(0, onet.n, 4096).astype(np.int32)
     qnet = oracle.with_weights(onet, oracle.quantize_bf16(onet.w_fx))
-    for fmt, ref in ((BLK, onet), (snn.RECORD_BLOCKED4, qnet)):
+    for fmt, ref in ((BLK, onet), (snn.RECORD_BLOCKED4, qnet), (snn.RECORD_BLOCKED8, onet)):
         net = snn.Network(model, wl.scale_n_permille, wl.scale_k_permille, wl.seed, record_format=fmt)
         net.deliver_spikes(torch.from_numpy(spikers).cuda(), 40)
         torch.cuda.synchronize()
         npad = int(net.layout().n_neurons_padded)
         ring = net.device_view("ring", torch.int32, 64 * npad).cpu().numpy().reshape(64, npad).astype(np.int64)
         assert np.array_equal(ring, _expected_ring(ref, spikers, 40, npad))
-        if fmt == snn.RECORD_BLOCKED4:
-            _check_blocked_structure(net, qnet, rows=np.random.default_rng(4).integers(0, onet.n, 500))
+        if fmt != BLK:
+            _check_blocked_structure(net, ref, rows=np.random.default_rng(4).integers(0, onet.n, 500))
         net.close()
 
 
