@@ -821,6 +821,10 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
             }
             cuda_ok(cudaMemcpyAsync(A + L.seg, hn.restab.data(), hn.restab.size(), cudaMemcpyHostToDevice, st),
                     "block tables");
+            if (!hn.rec8.empty())
+                cuda_ok(cudaMemcpyAsync(A + L.res_rec, hn.rec8.data(), 8 * hn.rec8.size(), cudaMemcpyHostToDevice, st),
+                        "block-major records");
+            a.res_rec = A + L.res_rec;
             cuda_ok(cudaMemcpyAsync(A + L.blocks, hn.blk.data(), 4 * hn.blk.size(), cudaMemcpyHostToDevice, st),
                     "blocks");
             cuda_ok(cudaStreamSynchronize(st), "resident upload");

@@ -332,6 +332,7 @@ Layout make_layout(const snn_spec &spec)
     L.seg = o; o = up(o + (resident ? resident_tables(n, res_blocks).total : 0));
     L.mbox = o; o = up(o + (resident ? 4 * uint64_t{4} * res_blocks * kResidentMboxWords : 0));
     L.inbox = o; o = up(o + (resident ? 4 * uint64_t{4} * res_blocks * res_blocks * kResidentSlotWords : 0));
+    L.res_rec = o; o = up(o + (resident ? 8 * uint64_t(L.syn_padded_max) + 16 : 0));
     L.rast_nrn = o; o = up(o + 4 * L.rast_cap);
     L.rast_t = o; o = up(o + 4 * L.rast_cap);
     L.U2 = o; o = up(o + 4 * L.npad);
@@ -711,6 +712,18 @@ bool block_major_records(HostNetwork &net, int64_t width, int nthreads, std::str
                 d2[dst] = net.d[s];
             }
         }
+    });
+    // the step kernel's 8-byte records: the weight in the low word, the target's index in
+    // its block and the delay (above bit 16) in the high word: one contiguous read per
+    // segment (the three arrays stay for phase 2 alone and the tests)
+    net.rec8.resize(S);
+    parallel_for(nthreads, B, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t b = lo; b < hi; ++b)
+            for (int64_t k = rbase[b]; k < rbase[b + 1]; ++k) {
+                const uint32_t local = static_cast<uint32_t>(t2[k] - net.blk[b]);
+                net.rec8[k] = static_cast<uint64_t>(static_cast<uint32_t>(w2[k])) |
+                              (static_cast<uint64_t>(local | (static_cast<uint32_t>(d2[k]) << 16)) << 32);
+            }
     });
     net.tgt = std::move(t2);
     net.w = std::move(w2);

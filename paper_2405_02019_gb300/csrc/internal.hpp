@@ -206,6 +206,7 @@ struct StepArgs {
     const uint32_t *res_coarse;   // resident engine: [n_blocks][coarse_stride] (see resident_tables)
     const uint8_t *res_lens;      // resident engine: [n_blocks][lens_stride]
     const uint32_t *res_offt;     // resident engine: [n_blocks][n + 1]
+    const void *res_rec;          // resident engine: block-major int2 records {weight, local target | delay << 16}
     int32_t res_lens_stride;
     int32_t res_coarse_stride;
     int32_t res_rows;             // resident engine: ring rows kept in shared memory (power of two, 8..64)
@@ -246,12 +247,13 @@ struct HostNetwork {
     std::vector<uint16_t> rec16;   // blocked records: local target | delay << 10
     std::vector<uint16_t> seg;     // blocked records: [n][blocks + 1] block starts per row
     std::vector<uint8_t> restab;   // resident engine: the tables of resident_tables(n, blocks), as bytes
+    std::vector<uint64_t> rec8;    // resident engine: weight (low word), local target | delay << 16 (high word)
 };
 
 // Arena layout for a spec.
 struct Layout {
     uint64_t ctl, tables, U, I, R, ring, row_ptr, syn_tgt, syn_w, syn_d, rast_nrn, rast_t, U2, R2, queue, qcount, pop_id,
-        group_circuit, circuits, blocks, seg, mbox, inbox, total;
+        group_circuit, circuits, blocks, seg, mbox, inbox, res_rec, total;
     int64_t npad, syn_padded_max, rast_cap;
 };
 

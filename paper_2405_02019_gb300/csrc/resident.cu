@@ -616,16 +616,15 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                     run += ln;
                 }
                 group_sync(bar, nbar);
-                // every delivery thread takes synapses gt, gt + G, ... of the flattened list
+                // every delivery thread takes synapses gt, gt + G, ... of the flattened list;
+                // a synapse is one 8-byte record (weight, local target | delay << 16)
+                const int2 *rec8 = reinterpret_cast<const int2 *>(a.res_rec);
                 for (uint32_t e0 = 0; e0 < Tt; e0 += static_cast<uint32_t>(G) * kResU) {
-                    int32_t tg[kResU], wv[kResU];
-                    uint32_t dv[kResU];
+                    int2 rv[kResU];
 #pragma unroll
                     for (int u = 0; u < kResU; ++u) {
                         const uint32_t e = e0 + static_cast<uint32_t>(gt + G * u);
-                        wv[u] = 0;
-                        tg[u] = base;
-                        dv[u] = 1;
+                        rv[u] = make_int2(0, 0);
                         if (e < Tt) {
                             // the last spike whose segment starts at or before e: from the spike
                             // holding e's chunk start, a short walk forward (segments of empty
@@ -644,20 +643,18 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                             }
                             while (lo_j + 1 < m && t_soff[lo_j + 1] <= e) ++lo_j;
                             const int64_t idx = rbase + t_sstart[lo_j] + (e - t_soff[lo_j]);
-                            tg[u] = __ldcg(a.syn_tgt + idx);
-                            wv[u] = __ldcg(a.syn_w + idx);
-                            dv[u] = __ldcg(a.syn_d + idx);
+                            rv[u] = __ldcg(rec8 + idx);
                         }
                     }
 #pragma unroll
                     for (int u = 0; u < kResU; ++u) {
-                        const int lt = tg[u] - base;
-                        if (wv[u] == 0 || static_cast<uint32_t>(lt) >= static_cast<uint32_t>(width)) continue;
-                        const int d = static_cast<int>(dv[u]);
+                        const int lt = rv[u].y & 0xFFFF;
+                        if (rv[u].x == 0 || lt >= width) continue;
+                        const int d = static_cast<int>(static_cast<uint32_t>(rv[u].y) >> 16);
                         if (full_ring || d < rows)
-                            atomicAdd(s_ring + ((t + d) & rmask) * stride + lt, wv[u]);
+                            atomicAdd(s_ring + ((t + d) & rmask) * stride + lt, rv[u].x);
                         else
-                            red_add_s32(a.ring + ((t + d) & kDMask) * npad + base + lt, wv[u]);
+                            red_add_s32(a.ring + ((t + d) & kDMask) * npad + base + lt, rv[u].x);
                     }
                 }
                 group_sync(bar, nbar);  // every add of this pass is done; the list may be rewritten
