@@ -506,13 +506,13 @@ namespace {
 // most `budget`.  For a bound L, cutting greedily wherever the next group of kBlockAlign
 // targets would pass L or the width limit gives the fewest blocks; the smallest L whose
 // greedy cut fits the budget is found by bisection.
-std::vector<int32_t> cut_blocks(const std::vector<int64_t> &grp, int64_t n, int64_t L)
+std::vector<int32_t> cut_blocks(const std::vector<int64_t> &grp, int64_t n, int64_t L, int64_t maxw)
 {
     std::vector<int32_t> blk{0};
     int64_t load = 0;
     for (size_t g = 0; g < grp.size(); ++g) {
         const int64_t j = static_cast<int64_t>(g) * kBlockAlign;
-        if (j > blk.back() && (j - blk.back() + kBlockAlign > kBlockMaxWidth || load + grp[g] > L)) {
+        if (j > blk.back() && (j - blk.back() + kBlockAlign > maxw || load + grp[g] > L)) {
             blk.push_back(static_cast<int32_t>(j));
             load = 0;
         }
@@ -534,22 +534,26 @@ std::vector<int32_t> target_blocks(const std::vector<int64_t> &indeg, int64_t n,
         total += g;
         gmax = std::max(gmax, g);
     }
+    auto bisect = [&](int64_t budget, int64_t maxw) {
+        int64_t lo = gmax, hi = std::max(gmax, total);
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (static_cast<int64_t>(cut_blocks(grp, n, mid, maxw).size()) - 1 <= budget) hi = mid;
+            else lo = mid + 1;
+        }
+        return cut_blocks(grp, n, lo, maxw);
+    };
+    const int64_t seg_cap = total / (16 * std::max<int64_t>(n, 1));  // ~16 synapses per (row, block) segment
     const int64_t min_blocks = n / (kBlockMaxWidth - kBlockAlign) + 1;
     int64_t budget;
     if (num_sms > 0) {
         budget = (min_blocks + num_sms - 1) / num_sms * num_sms;
-        budget = std::min(budget, std::max(min_blocks, total / (16 * std::max<int64_t>(n, 1))));
+        budget = std::min(budget, std::max(min_blocks, seg_cap));
     } else {
         budget = std::max(min_blocks, (n + kBlockAvgWidth - 1) / kBlockAvgWidth);
     }
     budget = std::min<int64_t>(budget, max_target_blocks(n));
-    int64_t lo = gmax, hi = std::max(gmax, total);
-    while (lo < hi) {
-        const int64_t mid = lo + (hi - lo) / 2;
-        if (static_cast<int64_t>(cut_blocks(grp, n, mid).size()) - 1 <= budget) hi = mid;
-        else lo = mid + 1;
-    }
-    return cut_blocks(grp, n, lo);
+    return bisect(budget, kBlockMaxWidth);
 }
 
 // Regroups the delay-sorted rows into block-grouped rows (delay order kept inside a
@@ -597,7 +601,11 @@ bool pack_blocked(HostNetwork &net, int nthreads, int num_sms, std::string &why)
     }
     for (int64_t i = 0; i < n; ++i) rp[i + 1] += rp[i];
     const int64_t S = rp[n];
-    net.rec16.assign(S, static_cast<uint16_t>(1u << kBlockLocalBits));
+    // BLOCKED8 keeps the local target and the delay in separate 16-bit fields of its
+    // 32-bit record; the other formats pack both in 16 bits
+    const bool wide = net.format == SNN_RECORD_BLOCKED8;
+    if (wide) net.word.assign(2 * S, 0);
+    else net.rec16.assign(S, static_cast<uint16_t>(1u << kBlockLocalBits));
     std::vector<int32_t> w(S, 0);
     parallel_for(nthreads, n, [&](int, int64_t lo, int64_t hi) {
         std::vector<int64_t> pos(B);
@@ -607,7 +615,9 @@ bool pack_blocked(HostNetwork &net, int nthreads, int num_sms, std::string &why)
             for (int64_t s = net.row_ptr[i], e = s + net.out_degree[i]; s < e; ++s) {
                 const int b = block_of[net.tgt[s]];
                 const int64_t dst = pos[b]++;
-                net.rec16[dst] = static_cast<uint16_t>((net.tgt[s] - net.blk[b]) | (int32_t{net.d[s]} << kBlockLocalBits));
+                const uint32_t local = static_cast<uint32_t>(net.tgt[s] - net.blk[b]);
+                if (wide) net.word[2 * dst + 1] = local | (uint32_t{net.d[s]} << 16);
+                else net.rec16[dst] = static_cast<uint16_t>(local | (uint32_t{net.d[s]} << kBlockLocalBits));
                 w[dst] = net.w[s];
             }
         }
@@ -635,15 +645,13 @@ bool pack_blocked(HostNetwork &net, int nthreads, int num_sms, std::string &why)
         std::vector<int32_t>().swap(net.w);
     } else if (net.format == SNN_RECORD_BLOCKED8) {
         // synapse e: word 2e its int32 weight, word 2e+1 its record (local target | delay
-        // << 10), so a quad is 32 contiguous bytes
-        net.word.assign(2 * S, 0);
+        // << 16; padding: local 0, delay 1, weight 0), so a quad is 32 contiguous bytes
         parallel_for(nthreads, S, [&](int, int64_t e0, int64_t e1) {
             for (int64_t e = e0; e < e1; ++e) {
                 net.word[2 * e] = static_cast<uint32_t>(w[e]);
-                net.word[2 * e + 1] = uint32_t{net.rec16[e]};
+                if (w[e] == 0) net.word[2 * e + 1] = 1u << 16;
             }
         });
-        std::vector<uint16_t>().swap(net.rec16);
         std::vector<int32_t>().swap(net.w);
     } else {
         net.w = std::move(w);

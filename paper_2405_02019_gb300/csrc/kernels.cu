@@ -724,25 +724,42 @@ __global__ void __launch_bounds__(kStepMaxThreads, 1) k_persistent(const StepArg
 
 constexpr int kBlockedWarps = kBlockedThreads / 32;
 // dynamic shared memory of k_deliver_blocked, in bytes from its start
-constexpr size_t kBlockedOffSegQ = sizeof(int32_t) * (kBlockedBinDelays + 1) * kBlockMaxWidth;  // bins
-constexpr size_t kBlockedOffPfx = kBlockedOffSegQ + sizeof(uint32_t) * kBlockedBatch;  // first quad per sender
-constexpr size_t kBlockedOffNq = kBlockedOffPfx + sizeof(int32_t) * kBlockedBatch;     // quad prefix per sender
-constexpr size_t kBlockedOffWarp = kBlockedOffNq + sizeof(int32_t) * kBlockedBatch;    // quads per sender
-constexpr size_t kBlockedOffQidx = kBlockedOffWarp + sizeof(int32_t) * kBlockedWarps;  // scan scratch
-constexpr size_t kBlockedSmemBytes = kBlockedOffQidx + sizeof(uint32_t) * kBlockedWindow;
+// kW: width of the bins (kBlockMaxWidth)
+template <int kW>
+struct BlockedSmem {
+    static constexpr size_t seg_q = sizeof(int32_t) * (kBlockedBinDelays + 1) * kW;    // after the bins
+    static constexpr size_t pfx = seg_q + sizeof(uint32_t) * kBlockedBatch;          // first quad per sender
+    static constexpr size_t nq = pfx + sizeof(int32_t) * kBlockedBatch;              // quad prefix per sender
+    static constexpr size_t warp = nq + sizeof(int32_t) * kBlockedBatch;             // quads per sender
+    static constexpr size_t qidx = warp + sizeof(int32_t) * kBlockedWarps;           // scan scratch
+    static constexpr size_t total = qidx + sizeof(uint32_t) * kBlockedWindow;
+};
+constexpr size_t kBlockedSmemBytes = BlockedSmem<kBlockMaxWidth>::total;
 static_assert(kBlockedSmemBytes <= 232448, "blocked delivery: shared memory above the 227 KB opt-in limit");
 static_assert(kBlockedWindow >= kBlockedThreads, "the scan output must fit the window table");
 static_assert(kBlockedBatch % kBlockedThreads == 0, "staged senders per thread");
 static_assert(kBlockedBinDelays >= 1 && kBlockedBinDelays < kDMax && kBlockMaxWidth % 4 == 0, "bins");
 
-template <bool kAggregate>
+template <bool kAggregate, int kW>
 __device__ __forceinline__ void blocked_apply(const StepArgs &a, int32_t *bins, int64_t t, int32_t base, uint32_t rec,
                                               int32_t w)
 {
     if (w == 0) return;  // padding (adding zero changes nothing)
     const int d = static_cast<int>(rec >> kBlockLocalBits);
     const int lt = static_cast<int>(rec & ((1u << kBlockLocalBits) - 1));
-    if (kAggregate && d <= kBlockedBinDelays) atomicAdd(bins + d * kBlockMaxWidth + lt, w);
+    if (kAggregate && d <= kBlockedBinDelays) atomicAdd(bins + d * kW + lt, w);
+    else red_add_s32(a.ring + ((t + d) & kDMask) * a.npad + base + lt, w);
+}
+
+// The same for a BLOCKED8 record: local target in the low 16 bits, delay above.
+template <bool kAggregate, int kW>
+__device__ __forceinline__ void blocked_apply_wide(const StepArgs &a, int32_t *bins, int64_t t, int32_t base,
+                                                   uint32_t rec, int32_t w)
+{
+    if (w == 0) return;
+    const int d = static_cast<int>(rec >> 16);
+    const int lt = static_cast<int>(rec & 0xFFFFu);
+    if (kAggregate && d <= kBlockedBinDelays) atomicAdd(bins + d * kW + lt, w);
     else red_add_s32(a.ring + ((t + d) & kDMask) * a.npad + base + lt, w);
 }
 
@@ -807,13 +824,28 @@ __device__ __forceinline__ void blocked_load_set(const StepArgs &a, const uint32
         const int32_t e = e0 + 32 * (warp + kBlockedWarps * k) + lane;
         va[k] = make_uint4(0, 0, 0, 0);
         vb[k] = make_uint4(0, 0, 0, 0);
+        if (FMT == SNN_RECORD_BLOCKED8) {
+            // the round's 32 quads as 64 16-byte halves, consecutive halves on consecutive
+            // lanes (so one load instruction reads whole lines of a segment): lane l takes
+            // halves l and 32 + l
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int32_t hq = 32 * j + lane;  // half within the round
+                const int32_t eq = e0 + 32 * (warp + kBlockedWarps * k) + (hq >> 1);
+                if (eq < w1) {
+                    const uint4 v = __ldcs(q16 + 2 * uint64_t(qidx[eq - w0]) + (hq & 1));
+                    if (j == 0) va[k] = v;
+                    else vb[k] = v;
+                }
+            }
+            continue;
+        }
         if (e < w1) {
             const uint32_t q = qidx[e - w0];
             if (FMT == SNN_RECORD_BLOCKED4) {
                 va[k] = __ldcs(q16 + q);
             } else if (FMT == SNN_RECORD_BLOCKED8) {
-                va[k] = __ldcs(q16 + 2 * uint64_t(q));
-                vb[k] = __ldcs(q16 + 2 * uint64_t(q) + 1);
+                // loaded below, by half-quads
             } else {
                 const uint2 r = __ldcs(recq + q);
                 va[k] = make_uint4(r.x, r.y, 0, 0);
@@ -823,7 +855,7 @@ __device__ __forceinline__ void blocked_load_set(const StepArgs &a, const uint32
     }
 }
 
-template <bool kAggregate, int FMT>
+template <bool kAggregate, int FMT, int kW>
 __device__ __forceinline__ void blocked_apply_set(const StepArgs &a, int32_t *bins, int64_t t, int32_t base,
                                                   const uint4 (&va)[kBlockedSet], const uint4 (&vb)[kBlockedSet])
 {
@@ -839,12 +871,12 @@ __device__ __forceinline__ void blocked_apply_set(const StepArgs &a, int32_t *bi
             w2v = bf16_fx(va[k].w);
             w3v = bf16_fx(va[k].w >> 16);
         } else if (FMT == SNN_RECORD_BLOCKED8) {
-            r01 = (va[k].y & 0xffffu) | (va[k].w << 16);
-            r23 = (vb[k].y & 0xffffu) | (vb[k].w << 16);
-            w0v = static_cast<int32_t>(va[k].x);
-            w1v = static_cast<int32_t>(va[k].z);
-            w2v = static_cast<int32_t>(vb[k].x);
-            w3v = static_cast<int32_t>(vb[k].z);
+            // two (weight, record) pairs per 16-byte half
+            blocked_apply_wide<kAggregate, kW>(a, bins, t, base, va[k].y, static_cast<int32_t>(va[k].x));
+            blocked_apply_wide<kAggregate, kW>(a, bins, t, base, va[k].w, static_cast<int32_t>(va[k].z));
+            blocked_apply_wide<kAggregate, kW>(a, bins, t, base, vb[k].y, static_cast<int32_t>(vb[k].x));
+            blocked_apply_wide<kAggregate, kW>(a, bins, t, base, vb[k].w, static_cast<int32_t>(vb[k].z));
+            continue;
         } else {
             r01 = va[k].x;
             r23 = va[k].y;
@@ -854,14 +886,14 @@ __device__ __forceinline__ void blocked_apply_set(const StepArgs &a, int32_t *bi
             w3v = static_cast<int32_t>(vb[k].w);
         }
         // quads past the window end were left zero: zero weights add nothing
-        blocked_apply<kAggregate>(a, bins, t, base, r01 & 0xffffu, w0v);
-        blocked_apply<kAggregate>(a, bins, t, base, r01 >> 16, w1v);
-        blocked_apply<kAggregate>(a, bins, t, base, r23 & 0xffffu, w2v);
-        blocked_apply<kAggregate>(a, bins, t, base, r23 >> 16, w3v);
+        blocked_apply<kAggregate, kW>(a, bins, t, base, r01 & 0xffffu, w0v);
+        blocked_apply<kAggregate, kW>(a, bins, t, base, r01 >> 16, w1v);
+        blocked_apply<kAggregate, kW>(a, bins, t, base, r23 & 0xffffu, w2v);
+        blocked_apply<kAggregate, kW>(a, bins, t, base, r23 >> 16, w3v);
     }
 }
 
-template <bool kAggregate, int FMT>
+template <bool kAggregate, int FMT, int kW>
 __device__ __forceinline__ void blocked_window(const StepArgs &a, int32_t *bins, const uint32_t *qidx, int32_t w0,
                                                int32_t w1, int64_t t, int32_t base)
 {
@@ -871,11 +903,11 @@ __device__ __forceinline__ void blocked_window(const StepArgs &a, int32_t *bins,
     blocked_load_set<FMT>(a, qidx, w0, w1, e0, aA, bA);
     for (;;) {
         if (e0 + kStep < w1) blocked_load_set<FMT>(a, qidx, w0, w1, e0 + kStep, aB, bB);
-        blocked_apply_set<kAggregate, FMT>(a, bins, t, base, aA, bA);
+        blocked_apply_set<kAggregate, FMT, kW>(a, bins, t, base, aA, bA);
         e0 += kStep;
         if (e0 >= w1) break;
         if (e0 + kStep < w1) blocked_load_set<FMT>(a, qidx, w0, w1, e0 + kStep, aA, bA);
-        blocked_apply_set<kAggregate, FMT>(a, bins, t, base, aB, bB);
+        blocked_apply_set<kAggregate, FMT, kW>(a, bins, t, base, aB, bB);
         e0 += kStep;
         if (e0 >= w1) break;
     }
@@ -885,14 +917,16 @@ template <int FMT>
 __global__ void __launch_bounds__(kBlockedThreads, 1)
     k_deliver_blocked(const StepArgs a, const int32_t *list, int64_t n_list, int64_t t_list, int k)
 {
+    constexpr int kW = kBlockMaxWidth;
+    using SL = BlockedSmem<kW>;
     extern __shared__ int4 smem4[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(smem4);
-    int32_t *bins = reinterpret_cast<int32_t *>(sm);                          // [kBlockedBinDelays + 1][768]
-    uint32_t *seg_q = reinterpret_cast<uint32_t *>(sm + kBlockedOffSegQ);     // [kBlockedBatch]
-    int32_t *pfx = reinterpret_cast<int32_t *>(sm + kBlockedOffPfx);          // [kBlockedBatch]
-    int32_t *seg_nq = reinterpret_cast<int32_t *>(sm + kBlockedOffNq);        // [kBlockedBatch]
-    int32_t *warp_sums = reinterpret_cast<int32_t *>(sm + kBlockedOffWarp);   // [kBlockedWarps]
-    uint32_t *qidx = reinterpret_cast<uint32_t *>(sm + kBlockedOffQidx);      // [kBlockedWindow]
+    int32_t *bins = reinterpret_cast<int32_t *>(sm);                       // [kBlockedBinDelays + 1][kW]
+    uint32_t *seg_q = reinterpret_cast<uint32_t *>(sm + SL::seg_q);        // [kBlockedBatch]
+    int32_t *pfx = reinterpret_cast<int32_t *>(sm + SL::pfx);              // [kBlockedBatch]
+    int32_t *seg_nq = reinterpret_cast<int32_t *>(sm + SL::nq);            // [kBlockedBatch]
+    int32_t *warp_sums = reinterpret_cast<int32_t *>(sm + SL::warp);       // [kBlockedWarps]
+    uint32_t *qidx = reinterpret_cast<uint32_t *>(sm + SL::qidx);          // [kBlockedWindow]
 
     int64_t t;
     const int32_t *spk;
@@ -922,8 +956,7 @@ __global__ void __launch_bounds__(kBlockedThreads, 1)
     constexpr int kPer = kBlockedBatch / kBlockedThreads;  // senders staged per thread
 
     if (aggregate)
-        for (int j = tid; j < (kBlockedBinDelays + 1) * kBlockMaxWidth / 4; j += kBlockedThreads)
-            smem4[j] = make_int4(0, 0, 0, 0);
+        for (int j = tid; j < (kBlockedBinDelays + 1) * kW / 4; j += kBlockedThreads) smem4[j] = make_int4(0, 0, 0, 0);
 
     for (int64_t b0 = 0; b0 < nspk; b0 += kBlockedBatch) {
         const int nb = static_cast<int>(nspk - b0 < kBlockedBatch ? nspk - b0 : kBlockedBatch);
@@ -967,8 +1000,8 @@ __global__ void __launch_bounds__(kBlockedThreads, 1)
                 for (int32_t e = lo; e < hi; ++e) qidx[e - w0] = q0 + static_cast<uint32_t>(e);
             }
             __syncthreads();
-            if (aggregate) blocked_window<true, FMT>(a, bins, qidx, w0, w1, t, base);
-            else blocked_window<false, FMT>(a, bins, qidx, w0, w1, t, base);
+            if (aggregate) blocked_window<true, FMT, kW>(a, bins, qidx, w0, w1, t, base);
+            else blocked_window<false, FMT, kW>(a, bins, qidx, w0, w1, t, base);
             __syncthreads();  // the table is rebuilt for the next window
         }
     }
@@ -979,7 +1012,7 @@ __global__ void __launch_bounds__(kBlockedThreads, 1)
     for (int q = tid; q < kBlockedBinDelays * w4; q += kBlockedThreads) {
         const int d = 1 + q / w4;
         const int c4 = q - (d - 1) * w4;
-        const int4 v = smem4[(d * kBlockMaxWidth) / 4 + c4];
+        const int4 v = smem4[(d * kW) / 4 + c4];
         if ((v.x | v.y | v.z | v.w) == 0) continue;
         int4 *dst = reinterpret_cast<int4 *>(a.ring + ((t + d) & kDMask) * a.npad + base) + c4;
         int4 o = __ldcg(dst);

@@ -769,11 +769,12 @@ def _check_blocked_structure(net, onet, rows=None):
     seg = net.device_view("syn_delay", torch.int16, n * (B + 1)).cpu().numpy().view(np.uint16)
     seg = seg.reshape(n, B + 1).astype(np.int64)
     q = 4  # records per padding unit (a quad)
+    LM, DS = 1023, 10  # record = local target | delay << DS
     if info.record_format == snn.RECORD_BLOCKED8:
         pairs = net.device_view("syn_tgt", torch.int32, 2 * SP).cpu().numpy().reshape(-1, 2)
         w = np.ascontiguousarray(pairs[:, 0])
-        assert np.all((pairs[:, 1] >> 16) == 0)  # the record is a zero-extended uint16
-        rec = pairs[:, 1].astype(np.uint16)
+        rec = pairs[:, 1].astype(np.int64)  # local target (16 bits) | delay << 16
+        LM, DS = 0xFFFF, 16
     elif info.record_format == snn.RECORD_BLOCKED4:
         quads = net.device_view("syn_tgt", torch.int16, 2 * SP).cpu().numpy().view(np.uint16).reshape(-1, 8)
         rec = np.ascontiguousarray(quads[:, :4]).reshape(-1)
@@ -789,7 +790,7 @@ def _check_blocked_structure(net, onet, rows=None):
     assert np.all(seg[:, 0] == 0) and np.array_equal(seg[:, -1], plen) and np.all(np.diff(seg, axis=1) >= 0)
     assert np.all(seg % q == 0)
     real = w != 0
-    assert int(real.sum()) == S and np.all(rec[~real] == 1024)
+    assert int(real.sum()) == S and np.all(rec[~real] == 1 << DS)  # padding: local 0, delay 1
     # block of every entry, segment starts, then chunked decode
     bid = np.repeat(np.tile(np.arange(B, dtype=np.int16), n), np.diff(seg, axis=1).ravel())
     start = np.zeros(SP + 1, bool)
@@ -801,7 +802,7 @@ def _check_blocked_structure(net, onet, rows=None):
         r = rec[c0:c1].astype(np.int64)
         b = bid[c0:c1].astype(np.int64)
         rl = real[c0:c1]
-        local, d = r & 1023, r >> 10
+        local, d = r & LM, r >> DS
         assert np.all(local < width[b])
         # padding only after the real entries of a segment; delay order among them
         assert not np.any(~rl[:-1] & rl[1:] & ~start[c0 + 1:c1])
@@ -822,10 +823,10 @@ def _check_blocked_structure(net, onet, rows=None):
         sl = slice(rp[i], rp[i + 1])
         keep = real[sl]
         r = rec[sl].astype(np.int64)[keep]
-        tg = blk[bid[sl].astype(np.int64)[keep]] + (r & 1023)
+        tg = blk[bid[sl].astype(np.int64)[keep]] + (r & LM)
         o = np.sort(onet.post[a:a + L].astype(np.int64) << 38 | onet.delay[a:a + L].astype(np.int64) << 32
                     | (onet.w_fx[a:a + L].astype(np.int64) + 2**31))
-        g = np.sort(tg << 38 | (r >> 10) << 32 | (w[sl][keep].astype(np.int64) + 2**31))
+        g = np.sort(tg << 38 | (r >> DS) << 32 | (w[sl][keep].astype(np.int64) + 2**31))
         assert np.array_equal(o, g), i
     # blocks balanced by in-degree (the heaviest within 30 % of the mean, up to one
     # 32-neuron group), and no more than whole waves of one CTA per SM
