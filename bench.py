@@ -466,7 +466,7 @@ def run_gpu(args):
             if r >= 2:
                 ms_list.append(e0.elapsed_time(e1))
                 ev_list.append(int(outdeg[spk].sum()))
-        ms_avg = float(np.mean(ms_list))
+        ms_avg = float(np.median(ms_list))  # median over the repetitions: robust to a stray slow launch
         ev_avg = float(np.mean(ev_list))
         nbytes = EVENT_BYTES * ev_avg + SPIKE_BYTES * nsp
         sat.append({"spikers": nsp, "events": ev_avg, "ms": ms_avg, "bytes": nbytes,
@@ -563,7 +563,7 @@ def run_gpu(args):
                     ev_l.append(int(outdeg[spk_np].sum()))
                     if blocked:
                         nnz_l.append(int(torch.count_nonzero(ring).item()))
-            ms_avg, ev_avg = float(np.mean(ms_l)), float(np.mean(ev_l))
+            ms_avg, ev_avg = float(np.median(ms_l)), float(np.mean(ev_l))
             plain_ms = [p_["ms"] for p_ in sat if p_["spikers"] == nsp]
             pt = {"spikers": nsp, "events": ev_avg, "ms": ms_avg, "events_per_s": ev_avg / (ms_avg * 1e-3),
                   "speedup_vs_plain": float(plain_ms[0] / ms_avg) if plain_ms else None}
@@ -622,7 +622,7 @@ def run_gpu(args):
                         ms_l.append(e0.elapsed_time(e1))
                         ev_l.append(int(outdeg[spk_np].sum()))
                         nnz_l.append(int(torch.count_nonzero(rring).item()))
-                ms_avg, ev_avg, nnz = float(np.mean(ms_l)), float(np.mean(ev_l)), float(np.mean(nnz_l))
+                ms_avg, ev_avg, nnz = float(np.median(ms_l)), float(np.mean(ev_l)), float(np.mean(nnz_l))
                 # own bytes: 9 B per record (target, weight, delay); per sender its list
                 # entry and its two segment offsets in every block's table; 8 B (read +
                 # write) per ring entry updated
