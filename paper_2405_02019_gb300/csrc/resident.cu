@@ -17,10 +17,13 @@
 // spikes, a CTA writes, into one 16-byte inbox slot per reading CTA, the step's spike
 // count and up to three spikes (their index in the block); further spikes go once into
 // its outbox.  Each CTA thus polls only lines that it alone reads.
-// It then adds its segments of those rows into its shared ring with shared-memory integer
-// atomics (order-independent, so the raster stays bit-exact).  Every mailbox word carries
-// the step's rank in the launch, so a reader tells a fresh word from an old one without
-// any other handshake (the host zeroes the mailboxes before each launch).
+// Once a step's slots are all in, the lanes that received spikes locate their segments in
+// the block's tables, and the team adds them into its shared ring with shared-memory
+// integer atomics (order-independent, so the raster stays bit-exact).  Every mailbox word
+// carries the step's rank in the launch, so a reader tells a fresh word from an old one
+// without any other handshake (the host zeroes the mailboxes before each launch).  A CTA
+// appends its own spikes to the raster with one atomic on the raster cursor per step
+// that has any.
 //
 // The two warp groups of a CTA run their own loops:
 //   neuron warps:   for each t: wait until D(t-1) is complete in this CTA, then B(t)
@@ -159,8 +162,6 @@ struct ResMisc {
     uint32_t own_cnt[2];  // neuron warps: own spikes of the step with parity s, in own[s & 1]
     uint32_t d_done[2];   // per delivery team: rank in the launch of its last step delivered into the ring
     uint32_t abort;       // a bounded wait timed out: every warp group leaves its loop
-    uint32_t cur_tag[4];  // raster cursor at the start of the step with rank r, in slot r & 3 ...
-    uint32_t cur_val[4];  // ... tagged with r (written by the team that delivered the step before)
 };
 
 // Mailbox words carry the step's rank in the launch: a header its low 20 bits above the
@@ -194,6 +195,88 @@ __device__ __forceinline__ bool wait_entry(const uint32_t *word, uint32_t etag, 
         if ((spins & 31u) == 0) {
             if (global_ns() - t_start > a.barrier_timeout_ns) return false;
             if (ld_relaxed_u32(&a.ctl->err) & kErrTimeout) return false;
+        }
+    }
+}
+
+// Segment of sender s in block p's region: first record (relative to the region) and
+// length, from the CTA's shared tables (8-bit lengths and one offset per 32 senders);
+// a group of 32 senders with an escaped length reads its exact offsets from global memory.
+__device__ __forceinline__ void res_segment(const StepArgs &a, const uint32_t *s_coarse, const uint8_t *s_lens, int p,
+                                            int32_t s, uint32_t &st, uint32_t &ln)
+{
+    st = 0;
+    ln = 0;
+    if (static_cast<uint32_t>(s) >= static_cast<uint64_t>(a.n)) return;
+    const uint32_t c = s_coarse[s >> 5];
+    if (c & kResidentGroupFlag) {  // an escaped length in the group: exact offsets
+        const uint32_t *o = a.res_offt + static_cast<int64_t>(p) * (a.n + 1) + s;
+        st = __ldcg(o);
+        ln = __ldcg(o + 1) - st;
+        return;
+    }
+    const uint4 *gl = reinterpret_cast<const uint4 *>(s_lens + (s & ~31));
+    const uint4 lo4 = gl[0], hi4 = gl[1];
+    const uint32_t wv8[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
+    const int before_s = s & 31;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int nb = min(max(before_s - 4 * k, 0), 4);
+        const uint32_t mask = nb == 4 ? 0xFFFFFFFFu : ((1u << (8 * nb)) - 1u);
+        acc = __dp4a(wv8[k] & mask, 0x01010101u, acc);
+    }
+    st = c + acc;
+    ln = s_lens[s];
+}
+
+// The m spikes' segments (t_sstart: first record, t_soff: offset in their concatenation,
+// Tt records in all; t_jmap: the spike holding each chunk of 32 records' first record)
+// added into the block's ring columns: thread gt of the G takes records gt, gt + G, ...,
+// kResU at a time, each one 8-byte record (weight, local target | delay << 16).
+__device__ __forceinline__ void res_adds(const StepArgs &a, int32_t *s_ring, const uint32_t *t_sstart,
+                                         const uint32_t *t_soff, const uint16_t *t_jmap, int m, uint32_t Tt, int gt,
+                                         int G, int64_t rbase, int32_t base, int32_t width, int64_t t, int rows,
+                                         int stride, bool full_ring)
+{
+    const int rmask = rows - 1;
+    const int2 *rec8 = reinterpret_cast<const int2 *>(a.res_rec);
+    for (uint32_t e0 = 0; e0 < Tt; e0 += static_cast<uint32_t>(G) * kResU) {
+        int2 rv[kResU];
+#pragma unroll
+        for (int u = 0; u < kResU; ++u) {
+            const uint32_t e = e0 + static_cast<uint32_t>(gt + G * u);
+            rv[u] = make_int2(0, 0);
+            if (e < Tt) {
+                // the last spike whose segment starts at or before e: from the spike
+                // holding e's chunk start, a short walk forward (segments of empty spikes
+                // share their offset)
+                int lo_j;
+                if ((e >> kJmapShift) < static_cast<uint32_t>(kJmap)) {
+                    lo_j = t_jmap[e >> kJmapShift];
+                } else {
+                    int lo = 0, hi = m - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (t_soff[mid] <= e) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    lo_j = lo;
+                }
+                while (lo_j + 1 < m && t_soff[lo_j + 1] <= e) ++lo_j;
+                const int64_t idx = rbase + t_sstart[lo_j] + (e - t_soff[lo_j]);
+                rv[u] = __ldcg(rec8 + idx);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kResU; ++u) {
+            const int lt = rv[u].y & 0xFFFF;
+            if (rv[u].x == 0 || lt >= width) continue;
+            const int d = static_cast<int>(static_cast<uint32_t>(rv[u].y) >> 16);
+            if (full_ring || d < rows)
+                atomicAdd(s_ring + ((t + d) & rmask) * stride + lt, rv[u].x);
+            else
+                red_add_s32(a.ring + ((t + d) & kDMask) * a.npad + base + lt, rv[u].x);
         }
     }
 }
@@ -248,9 +331,6 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
         s_misc->d_done[0] = 0;
         s_misc->d_done[1] = 0;
         s_misc->abort = 0;
-        for (int k = 0; k < 4; ++k) s_misc->cur_tag[k] = 0;
-        s_misc->cur_val[1] = ctl->cursor;  // the first step has rank 1
-        s_misc->cur_tag[1] = 1;
     }
     // shared row r holds the ring row of the step in [t0, t0 + rows) congruent to r
     for (int idx = threadIdx.x; idx < rows * (stride >> 2); idx += blockDim.x) {
@@ -384,6 +464,7 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                     if (spk[j]) s_own[par * stride + k++] = static_cast<uint16_t>(i0 + j);
             }
             group_sync(1, NW * 32);
+            uint32_t n_raster = 0, rpos = 0;  // warp 0: own spikes of step t+1 and their raster position
             if (warp == 0) {
                 // mailboxes of step t+1: one slot in every CTA's inbox (header and the first
                 // three spikes), the other spikes once in this CTA's outbox
@@ -403,6 +484,10 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                 uint32_t *slots = a.inbox + (buf * B * B + p) * kResidentSlotWords;  // reader c's slot: + c * B * 4
                 for (int c = lane; c < B; c += 32)
                     st_relaxed_v4u32(slots + static_cast<size_t>(c) * B * kResidentSlotWords, h, e0, e1, e2);
+                // raster space for the own spikes; the position is used after the draws, so
+                // the atomic's round trip overlaps them
+                n_raster = n_own;
+                if (n_own > 0 && lane == 0) rpos = atomicAdd(&ctl->cursor, n_own);
             }
             if (active) {
                 // thalamic input of step t+1 (counter-based: independent of the dynamics)
@@ -432,6 +517,20 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                     gw4.z = atomicExch(g + 2, 0);
                     gw4.w = atomicExch(g + 3, 0);
                 }
+            }
+            if (warp == 0 && n_raster > 0) {
+                // the own spikes of step t+1 into the raster (the reader orders entries by
+                // step and neuron); own[(t + 1) & 1] is rewritten only by A(t+3)
+                rpos = __shfl_sync(0xFFFFFFFFu, rpos, 0);
+                const uint16_t *own = s_own + par * stride;
+                for (uint32_t j = lane; j < n_raster; j += 32) {
+                    const uint64_t pos = static_cast<uint64_t>(rpos) + j;
+                    if (pos < a.rast_cap) {
+                        a.rast_nrn[pos] = base + own[j];
+                        a.rast_t[pos] = static_cast<int32_t>(t + 1);
+                    }
+                }
+                if (lane == 0 && static_cast<uint64_t>(rpos) + n_raster > a.rast_cap) atomicOr(&ctl->err, kErrRaster);
             }
         }
     } else {
@@ -497,32 +596,13 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                 total += v;
             }
             const int off = before + incl - static_cast<int>(cnt);
-            // the raster cursor at this step: left by the team of the step before
-            uint32_t cursor = 0;
-            bool late = false;  // a wait (spike entry or cursor) gave up
-            if (ql == p || (tw == 0 && lane == 0)) {
-                const uint32_t slot = rel & 3;
-                if (ld_acquire_shared(&s_misc->cur_tag[slot]) != rel) {
-                    const uint64_t t_start = global_ns();
-                    for (uint32_t spins = 1;; ++spins) {
-                        if (ld_acquire_shared(&s_misc->cur_tag[slot]) == rel) break;
-                        if ((spins & 255u) == 0 && (global_ns() - t_start > a.barrier_timeout_ns ||
-                                                    ld_volatile_shared(&s_misc->abort))) {
-                            late = true;
-                            break;
-                        }
-                    }
-                }
-                cursor = s_misc->cur_val[slot];
-                if (tw == 0 && lane == 0 && !late) {
-                    s_misc->cur_val[(rel + 1) & 3] = cursor + static_cast<uint32_t>(total);
-                    st_release_shared(&s_misc->cur_tag[(rel + 1) & 3], rel + 1);
-                }
-            }
+            bool late = false;  // a wait for a spike entry gave up
+            const int G = nbar, gt = ql;
+            // passes of kResidentGather spikes through the gather list (one at the usual load)
             for (int lo = 0; lo < total; lo += kResidentGather) {
                 const int m = total - lo < kResidentGather ? total - lo : kResidentGather;
-                // spikes lo .. lo + m of the step into the gather list; a slot's entries may
-                // predate its header, so each is checked
+                // spikes lo .. lo + m of the step into the gather list; a slot's entries
+                // may predate its header, so each is checked
                 if (cnt > 0) {
                     const int j0 = lo > off ? lo - off : 0;
                     const int j1 = min(static_cast<int>(cnt), lo + m - off);
@@ -531,75 +611,41 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                     const int32_t src_base = s_base[ql];
                     for (int j = j0; j < j1; ++j) {
                         uint32_t v = j == 0 ? h.y : j == 1 ? h.z : h.w;
-                        if (j >= 3 || !entry_ok(v, etag)) {
-                            if (!wait_entry(j < 3 ? sl + 1 + j : ob + j, etag, v, a)) {
-                                atomicOr(&ctl->err, kErrTimeout);
-                                late = true;
-                                v = 0;
-                            }
+                        int32_t s_id = -1;  // no segment if the wait gives up
+                        if ((j >= 3 || !entry_ok(v, etag)) && !wait_entry(j < 3 ? sl + 1 + j : ob + j, etag, v, a)) {
+                            atomicOr(&ctl->err, kErrTimeout);
+                            late = true;
+                        } else {
+                            s_id = src_base + static_cast<int32_t>(v & 0x3FFu);
                         }
-                        const int32_t s_id = src_base + static_cast<int32_t>(v & 0x3FFu);
                         t_glist[off + j - lo] = s_id;
-                        if (ql == p) {
-                            // this CTA's own spikes of step t go into the raster, in slot order
-                            const uint64_t pos = static_cast<uint64_t>(cursor) + static_cast<uint64_t>(off + j);
-                            if (pos < a.rast_cap) {
-                                a.rast_nrn[pos] = s_id;
-                                a.rast_t[pos] = static_cast<int32_t>(t);
-                            }
-                        }
                     }
                 }
                 group_sync(bar, nbar);
-                // every spike's segment in this block's region, from the shared tables (the
-                // group's offset plus the lengths of the group's earlier senders); thread gt
-                // takes spikes gt * kper .. + kper, so that a prefix over threads orders them
-                const int G = nbar, gt = ql;
+                // every spike's segment, thread gt taking spikes gt * kper .. + kper, so
+                // that a prefix over threads orders them
                 const int kper = (m + G - 1) / G;
                 uint32_t mine = 0;
                 for (int q = 0; q < kper; ++q) {
                     const int j = gt * kper + q;
                     if (j >= m) break;
                     uint32_t st = 0, ln = 0;
-                    const int s = t_glist[j];
-                    if (static_cast<uint32_t>(s) < static_cast<uint64_t>(a.n)) {
-                        const uint32_t c = s_coarse[s >> 5];
-                        if (c & kResidentGroupFlag) {  // an escaped length in the group: exact offsets
-                            const uint32_t *o = a.res_offt + static_cast<int64_t>(p) * (a.n + 1) + s;
-                            st = __ldcg(o);
-                            ln = __ldcg(o + 1) - st;
-                        } else {
-                            const uint4 *gl = reinterpret_cast<const uint4 *>(s_lens + (s & ~31));
-                            const uint4 lo4 = gl[0], hi4 = gl[1];
-                            const uint32_t wv8[8] = {lo4.x, lo4.y, lo4.z, lo4.w, hi4.x, hi4.y, hi4.z, hi4.w};
-                            const int before_s = s & 31;
-                            uint32_t acc = 0;
-#pragma unroll
-                            for (int k = 0; k < 8; ++k) {
-                                const int nb = min(max(before_s - 4 * k, 0), 4);
-                                const uint32_t mask = nb == 4 ? 0xFFFFFFFFu : ((1u << (8 * nb)) - 1u);
-                                acc = __dp4a(wv8[k] & mask, 0x01010101u, acc);
-                            }
-                            st = (c & ~kResidentGroupFlag) + acc;
-                            ln = s_lens[s];
-                        }
-                    }
+                    res_segment(a, s_coarse, s_lens, p, t_glist[j], st, ln);
                     t_sstart[j] = st;
                     t_soff[j] = ln;
                     mine += ln;
                 }
-                // prefix of the segment lengths over the spikes: the flattened synapse list
                 uint32_t sincl = mine;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, sincl, o);
                     if (lane >= o) sincl += v;
                 }
-                if (lane == 31) t_wsum[tw] = static_cast<int32_t>(sincl);
+                if (lane == 31) t_wsum[8 + tw] = static_cast<int32_t>(sincl);
                 group_sync(bar, nbar);
                 uint32_t run = 0, Tt = 0;
                 for (int w = 0; w < TW; ++w) {
-                    const uint32_t v = static_cast<uint32_t>(t_wsum[w]);
+                    const uint32_t v = static_cast<uint32_t>(t_wsum[8 + w]);
                     run += w < tw ? v : 0u;
                     Tt += v;
                 }
@@ -609,54 +655,14 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                     if (j >= m) break;
                     const uint32_t ln = t_soff[j];
                     t_soff[j] = run;
-                    // chunks of 32 synapses whose first synapse lies in this segment
                     for (uint32_t k = (run + 31u) >> kJmapShift; k < static_cast<uint32_t>(kJmap) &&
                                                                  (k << kJmapShift) < run + ln; ++k)
                         t_jmap[k] = static_cast<uint16_t>(j);
                     run += ln;
                 }
                 group_sync(bar, nbar);
-                // every delivery thread takes synapses gt, gt + G, ... of the flattened list;
-                // a synapse is one 8-byte record (weight, local target | delay << 16)
-                const int2 *rec8 = reinterpret_cast<const int2 *>(a.res_rec);
-                for (uint32_t e0 = 0; e0 < Tt; e0 += static_cast<uint32_t>(G) * kResU) {
-                    int2 rv[kResU];
-#pragma unroll
-                    for (int u = 0; u < kResU; ++u) {
-                        const uint32_t e = e0 + static_cast<uint32_t>(gt + G * u);
-                        rv[u] = make_int2(0, 0);
-                        if (e < Tt) {
-                            // the last spike whose segment starts at or before e: from the spike
-                            // holding e's chunk start, a short walk forward (segments of empty
-                            // spikes share their offset)
-                            int lo_j;
-                            if ((e >> kJmapShift) < static_cast<uint32_t>(kJmap)) {
-                                lo_j = t_jmap[e >> kJmapShift];
-                            } else {
-                                int lo = 0, hi = m - 1;
-                                while (lo < hi) {
-                                    const int mid = (lo + hi + 1) >> 1;
-                                    if (t_soff[mid] <= e) lo = mid;
-                                    else hi = mid - 1;
-                                }
-                                lo_j = lo;
-                            }
-                            while (lo_j + 1 < m && t_soff[lo_j + 1] <= e) ++lo_j;
-                            const int64_t idx = rbase + t_sstart[lo_j] + (e - t_soff[lo_j]);
-                            rv[u] = __ldcg(rec8 + idx);
-                        }
-                    }
-#pragma unroll
-                    for (int u = 0; u < kResU; ++u) {
-                        const int lt = rv[u].y & 0xFFFF;
-                        if (rv[u].x == 0 || lt >= width) continue;
-                        const int d = static_cast<int>(static_cast<uint32_t>(rv[u].y) >> 16);
-                        if (full_ring || d < rows)
-                            atomicAdd(s_ring + ((t + d) & rmask) * stride + lt, rv[u].x);
-                        else
-                            red_add_s32(a.ring + ((t + d) & kDMask) * npad + base + lt, rv[u].x);
-                    }
-                }
+                res_adds(a, s_ring, t_sstart, t_soff, t_jmap, m, Tt, gt, G, rbase, base, width, t, rows, stride,
+                         full_ring);
                 group_sync(bar, nbar);  // every add of this pass is done; the list may be rewritten
             }
             if (group_sync_or(bar, nbar, late)) {
@@ -669,12 +675,7 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
     if (!full_ring) __threadfence();  // the long-delay adds before the ring write-back reads them
     __syncthreads();
     if (ld_volatile_shared(&s_misc->abort)) return;  // a wait timed out: the error is recorded, the state is void
-    if (p == 0 && threadIdx.x == 0) {
-        const uint32_t cursor = s_misc->cur_val[static_cast<uint32_t>(n_steps + 1) & 3];
-        ctl->cursor = cursor;
-        if (cursor > a.rast_cap) atomicOr(&ctl->err, kErrRaster);
-        ctl->t_base = tend;
-    }
+    if (p == 0 && threadIdx.x == 0) ctl->t_base = tend;  // the raster cursor advanced atomically
 
     // ---- write the state after tend steps back to the arena ----
     if (active) {
