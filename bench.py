@@ -53,13 +53,13 @@ WORKLOAD = "pd_full"
 METRIC = "synaptic events/s and real-time factor (full microcircuit, 1 GB300), % HBM roofline"
 
 
-def _kernel_sources_hash() -> str:
-    """Hash of the kernel sources' code lines (comment-only and blank lines ignored)."""
+def _kernel_sources_hash(files=("kernels.cu", "internal.hpp")) -> str:
+    """Hash of the code lines (comment-only and blank lines ignored) of kernel sources."""
     import hashlib
 
     csrc = os.path.join(ROOT, "paper_2405_02019_gb300", "csrc")
     lines = []
-    for f in ("kernels.cu", "resident.cu", "internal.hpp"):
+    for f in files:
         for line in open(os.path.join(csrc, f), encoding="utf-8"):
             code = line.strip()
             if code and not code.startswith("//"):
@@ -67,14 +67,22 @@ def _kernel_sources_hash() -> str:
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
 
 
+# the sources each recorded kernel is built from
+_RESIDENT_KERNELS = ("k_resident", "k_deliver_regions")
+
+
 def _recorded_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu record, only if the kernel sources
+    """DRAM bytes per launch from the committed ncu record, only if the kernel's sources
     are unchanged since it was taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("kernels_sha256_16") != _kernel_sources_hash() or kernel not in d:
+    if kernel in _RESIDENT_KERNELS:
+        valid = d.get("resident_sha256_16") == _kernel_sources_hash(("resident.cu", "internal.hpp"))
+    else:
+        valid = d.get("kernels_sha256_16") == _kernel_sources_hash()
+    if not valid or kernel not in d:
         return None
     return d[kernel].get("dram_bytes_per_launch")
 
