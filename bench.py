@@ -1,12 +1,12 @@
 """Benchmark of the full-scale Potjans-Diesmann microcircuit step loop on GB300.
 
-One bench step = 1,024 simulation steps of 0.1 ms (102.4 ms of biological time, one
-CUDA-graph replay) of the full microcircuit (77,169 neurons, 284,811,022 synapses,
+One bench step = 1,024 simulation steps of 0.1 ms (102.4 ms of biological time: one
+launch of the resident engine, by default, or one CUDA-graph replay) of the full microcircuit (77,169 neurons, 284,811,022 synapses,
 seed 1 + rank), so the default --steps 100 covers the paper's 10 s runs (§4).  Prints
 one JSON line.
 
   value     recurrent synaptic events/s (sum of the spikers' out-degrees / seconds),
-            device-timed with CUDA events around snn_step_n graph replays
+            device-timed with CUDA events around the snn_step_n calls
   rtf       real-time factor = wall time / biological time (§4.2)
   events_incl_thalamic  value plus the thalamic drive's expected input events
             (N_b K_ext,b nu_th per biological second, over the same wall time)
@@ -841,7 +841,8 @@ def main():
     ap.add_argument("--regions", type=int, default=1, help="saturating delivery on block-major records (0: skip)")
     ap.add_argument("--seeds", type=int, default=10, help="network instances timed for the mean RTF (0: none)")
     ap.add_argument("--seed-steps", type=int, default=10, help="bench steps timed per instance")
-    ap.add_argument("--engine", default="default", choices=["default", "graph", "persistent", "pipelined", "resident"])
+    ap.add_argument("--engine", default="resident", choices=["default", "graph", "persistent", "pipelined", "resident"],
+                    help="engine of the headline step loop (the resident engine: one launch per 1,024 steps)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

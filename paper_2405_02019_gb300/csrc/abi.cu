@@ -813,8 +813,11 @@ int snn_build_network(const snn_spec *spec, void *dev_arena, uint64_t arena_byte
             a.res_stride = static_cast<int32_t>(width);
             a.res_rows = snn::resident_rows(static_cast<int>(width), spec->smem_ring_rows, net->n);
             a.neuron_warps = static_cast<int32_t>((width + 127) / 128);
-            // two delivery teams, each with a lane per mailbox
-            a.delivery_warps = 2 * std::max(snn::kResidentTeamWarps, (B + 31) / 32);
+            // two delivery teams, each with a lane per mailbox, and up to kResidentTeamWarps
+            // warps each where the CTA has room (more warps share a step's synapse loads)
+            const int need = 2 * ((B + 31) / 32);
+            a.delivery_warps = std::max(need, std::min(2 * snn::kResidentTeamWarps,
+                                                       (snn::kResidentMaxWarps - a.neuron_warps) & ~1));
             if (a.neuron_warps + a.delivery_warps > snn::kResidentMaxWarps) {
                 snn_destroy(net);
                 return fail(SNN_ENOTSUP, "the resident engine's CTA would exceed its warp limit for this network");

@@ -114,8 +114,8 @@ inline int max_target_blocks(int64_t n)
 constexpr int kResidentMaxWidth = 1024;      // neurons per block (8 neuron warps x 128)
 constexpr int kResidentMaxBlocks = 256;      // blocks (CTAs, at most one per SM)
 constexpr int kResidentAlign = 32;           // block boundaries are multiples of 32
-constexpr int kResidentMaxWarps = 16;        // neuron warps + delivery warps per CTA
-constexpr int kResidentTeamWarps = 4;        // delivery warps per team (at least; two teams)
+constexpr int kResidentMaxWarps = 20;        // neuron warps + delivery warps per CTA
+constexpr int kResidentTeamWarps = 8;        // delivery warps per team where the CTA has room (two teams)
 constexpr int kResidentMboxWords = kResidentMaxWidth + 4;  // u32 words of one outbox (entries of a step)
 constexpr int kResidentSlotWords = 4;        // u32 words of one inbox slot: header and three entries
 constexpr int64_t kResidentMaxSteps = int64_t{1} << 19;     // steps per launch (mailbox tags count them)

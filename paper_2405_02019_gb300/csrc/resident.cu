@@ -147,8 +147,8 @@ __host__ __device__ inline ResLayout res_layout(int rows, int stride, int lens_s
     L.coarse = res_up16(L.lens + size_t(lens_stride));                            // u32 [coarse_stride]
     L.thr = res_up16(L.coarse + sizeof(uint32_t) * size_t(coarse_stride));        // u64 [8][24]
     L.base = res_up16(L.thr + sizeof(uint64_t) * SNN_MAX_POPS * kPK);             // int32 [blocks + 1]
-    L.wsum = res_up16(L.base + sizeof(int32_t) * (kResidentMaxBlocks + 1));       // int32 [2 teams][16] warp sums
-    L.own = res_up16(L.wsum + sizeof(int32_t) * 2 * 16);                          // u16 [2][stride]
+    L.wsum = res_up16(L.base + sizeof(int32_t) * (kResidentMaxBlocks + 1));       // int32 [2 teams][32] warp sums
+    L.own = res_up16(L.wsum + sizeof(int32_t) * 2 * 32);                          // u16 [2][stride]
     L.glist = res_up16(L.own + sizeof(uint16_t) * 2 * stride);                    // int32 [2 teams][gather]
     L.sstart = res_up16(L.glist + sizeof(int32_t) * 2 * kResidentGather);         // u32 [2][gather] segment starts
     L.soff = res_up16(L.sstart + sizeof(uint32_t) * 2 * kResidentGather);         // u32 [2][gather] flattened offsets
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
         const int tw = dw - team * TW;  // warp within the team
         const int ql = tw * 32 + lane;  // the sender whose slot this lane polls
         const int bar = 2 + team, nbar = TW * 32;
-        int32_t *t_wsum = s_wsum + team * 16;
+        int32_t *t_wsum = s_wsum + team * 32;  // [0, 16): counts, [16, 32): segment lengths
         int32_t *t_glist = s_glist + team * kResidentGather;
         uint32_t *t_sstart = s_sstart + team * kResidentGather;
         uint32_t *t_soff = s_soff + team * kResidentGather;
@@ -641,11 +641,11 @@ __global__ void __launch_bounds__(kResidentMaxThreads, 1) k_resident(const StepA
                     const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, sincl, o);
                     if (lane >= o) sincl += v;
                 }
-                if (lane == 31) t_wsum[8 + tw] = static_cast<int32_t>(sincl);
+                if (lane == 31) t_wsum[16 + tw] = static_cast<int32_t>(sincl);
                 group_sync(bar, nbar);
                 uint32_t run = 0, Tt = 0;
                 for (int w = 0; w < TW; ++w) {
-                    const uint32_t v = static_cast<uint32_t>(t_wsum[8 + w]);
+                    const uint32_t v = static_cast<uint32_t>(t_wsum[16 + w]);
                     run += w < tw ? v : 0u;
                     Tt += v;
                 }
