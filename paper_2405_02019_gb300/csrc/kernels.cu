@@ -704,15 +704,16 @@ __global__ void __launch_bounds__(kStepMaxThreads, 1) k_persistent(const StepArg
 // Each sender's row is grouped by target block, so CTA p reads, for every sender, only
 // the segment that lands in its block (row_ptr[s] + seg[s][p] .. + seg[s][p + 1]); a
 // segment is a whole number of aligned quads of records (zero-weight padding).  Per
-// pass the CTA stages up to kBlockedBatch senders' segments (first quad, quad count and
-// the exclusive prefix of the counts) in shared memory, which makes the pass one stream
-// of quads.  The
-// stream is taken in windows of kBlockedWindow quads; for a window the record-array
-// index of every quad is written into a shared table, after which the quads are
-// independent work: warp w takes rounds w, w + 32, ... of 32 consecutive quads, in
-// sets of kBlockedRounds / 2 rounds whose loads (per quad 8 bytes of records and 16 of
-// int32 weights, or one 16-byte unit of records and bfloat16 weights) are issued while
-// the previous set's weights are added.
+// pass the CTA stages up to kBlockedBatch senders' nonempty segments (first quad and
+// the exclusive prefix of the quad counts, compacted) in shared memory, which makes the
+// pass one stream of quads.  The stream is taken in windows of kBlockedMapWindow quads
+// (one per pass at the microcircuit's sizes); a map gives the segment holding every
+// 16th quad of the window, from which a quad's segment is a short forward walk.  The
+// quads are then independent work: warp w takes rounds w, w + 32, ... of 32 consecutive
+// quads, in sets of kBlockedRounds / 2 rounds whose loads (per quad 8 bytes of records
+// and 16 of int32 weights, one 16-byte unit of records and bfloat16 weights, or 32
+// bytes of (weight, record) pairs) are issued while the previous set's weights are
+// added.
 // With many senders the weights of delays up to kBlockedBinDelays are summed per (delay,
 // local target) in shared memory and each nonzero sum is added to its ring entry once at
 // the end; only this CTA writes these ring columns during the launch, so that final add
@@ -725,18 +726,36 @@ __global__ void __launch_bounds__(kStepMaxThreads, 1) k_persistent(const StepArg
 constexpr int kBlockedWarps = kBlockedThreads / 32;
 // dynamic shared memory of k_deliver_blocked, in bytes from its start
 // kW: width of the bins (kBlockMaxWidth)
-template <int kW>
-struct BlockedSmem {
-    static constexpr size_t seg_q = sizeof(int32_t) * (kBlockedBinDelays + 1) * kW;    // after the bins
-    static constexpr size_t pfx = seg_q + sizeof(uint32_t) * kBlockedBatch;          // first quad per sender
-    static constexpr size_t nq = pfx + sizeof(int32_t) * kBlockedBatch;              // quad prefix per sender
-    static constexpr size_t warp = nq + sizeof(int32_t) * kBlockedBatch;             // quads per sender
-    static constexpr size_t qidx = warp + sizeof(int32_t) * kBlockedWarps;           // scan scratch
-    static constexpr size_t total = qidx + sizeof(uint32_t) * kBlockedWindow;
+constexpr int kBlockedMapWindow = 32768;     // quads of a pass mapped to their segments at once
+constexpr int kBlockedChunkShift = 5;        // the map gives the segment of every 32nd quad (a round's first)
+constexpr int kBlockedChunks = kBlockedMapWindow >> kBlockedChunkShift;  // map entries per window
+constexpr int kBlockedTableWindow = 8192;    // quads of a pass whose record-array index is tabled at once
+// How a format locates a window's quads: BLOCKED8 (two 16-byte loads per quad, on
+// consecutive lanes) through a table of every quad's record-array index, the others
+// through the map of segments per round (measured faster for each).
+template <int FMT>
+struct BlockedCfg {
+    static constexpr bool table = FMT == SNN_RECORD_BLOCKED8;
+    static constexpr size_t index_bytes = table ? sizeof(uint32_t) * kBlockedTableWindow
+                                                : sizeof(uint16_t) * kBlockedChunks;
 };
-constexpr size_t kBlockedSmemBytes = BlockedSmem<kBlockMaxWidth>::total;
-static_assert(kBlockedSmemBytes <= 232448, "blocked delivery: shared memory above the 227 KB opt-in limit");
-static_assert(kBlockedWindow >= kBlockedThreads, "the scan output must fit the window table");
+// Table formats stage every sender (empty segments too) with its quad count; map formats
+// only the nonempty segments, followed by 32 INT32_MAX starts.
+template <int kW, int FMT>
+struct BlockedSmem {
+    static constexpr bool table = BlockedCfg<FMT>::table;
+    static constexpr size_t seg_q = sizeof(int32_t) * (kBlockedBinDelays + 1) * kW;    // after the bins
+    static constexpr size_t pfx = seg_q + sizeof(uint32_t) * kBlockedBatch;          // first quad per segment
+    static constexpr size_t nq = pfx + sizeof(int32_t) * (kBlockedBatch + (table ? 0 : 32));  // quad prefix
+    static constexpr size_t warp = nq + (table ? sizeof(int32_t) * kBlockedBatch : 0);  // quads per sender
+    static constexpr size_t index = warp + (table ? sizeof(int32_t) : sizeof(int2)) * kBlockedWarps;  // scan scratch
+    static constexpr size_t total = index + BlockedCfg<FMT>::index_bytes;             // table or map
+};
+template <int FMT>
+constexpr size_t blocked_smem_bytes() { return BlockedSmem<kBlockMaxWidth, FMT>::total; }
+static_assert(blocked_smem_bytes<SNN_RECORD_BLOCKED8>() <= 232448 && blocked_smem_bytes<SNN_RECORD_BLOCKED6>() <= 232448,
+              "blocked delivery: shared memory above the 227 KB opt-in limit");
+static_assert(kBlockedBatch <= 65536, "segment numbers are 16-bit in the map");
 static_assert(kBlockedBatch % kBlockedThreads == 0, "staged senders per thread");
 static_assert(kBlockedBinDelays >= 1 && kBlockedBinDelays < kDMax && kBlockMaxWidth % 4 == 0, "bins");
 
@@ -790,15 +809,76 @@ __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *out,
     return warp_sums[kBlockedWarps - 1];
 }
 
+// Exclusive prefix sums of two values per thread over the CTA; returns this thread's
+// prefixes and sets `total` to the sums over the CTA.
+__device__ __forceinline__ int2 block_exclusive_scan2(int2 v, int2 *warp_sums, int2 &total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int2 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t yx = __shfl_up_sync(0xffffffffu, x.x, o);
+        const int32_t yy = __shfl_up_sync(0xffffffffu, x.y, o);
+        if (lane >= o) {
+            x.x += yx;
+            x.y += yy;
+        }
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int2 w = lane < kBlockedWarps ? warp_sums[lane] : make_int2(0, 0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t yx = __shfl_up_sync(0xffffffffu, w.x, o);
+            const int32_t yy = __shfl_up_sync(0xffffffffu, w.y, o);
+            if (lane >= o) {
+                w.x += yx;
+                w.y += yy;
+            }
+        }
+        if (lane < kBlockedWarps) warp_sums[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    const int2 before = warp > 0 ? warp_sums[warp - 1] : make_int2(0, 0);
+    total = warp_sums[kBlockedWarps - 1];
+    return make_int2(before.x + x.x - v.x, before.y + x.y - v.y);
+}
+
+// A pass's compacted segments in shared memory: segment k's first quad in the record
+// arrays and its first quad in the pass's stream (32 entries past the last segment hold
+// INT32_MAX); jmap[c]: the segment holding the window's quad w0 + 32 c, where w0 is a
+// multiple of kBlockedMapWindow; or qidx[e - w0]: quad e's record-array index.
+struct BlockedPass {
+    const uint32_t *seg_q;
+    const int32_t *pfx;
+    const uint16_t *jmap;
+    const uint32_t *qidx;
+};
+
+// Record-array quad of stream quad eb + lane, for a round of 32 quads starting at eb, a
+// multiple of 32 inside the current window (every lane of the warp calls it).  The map
+// gives the segment k0 holding eb; the next 32 segments' starts, one per lane, mark the
+// quads of the round where a segment begins, and a lane's segment is k0 plus the marks at
+// or below it.
+__device__ __forceinline__ uint32_t blocked_round_quad(const BlockedPass &ps, int32_t eb, int lane)
+{
+    const int k0 = ps.jmap[(eb >> kBlockedChunkShift) & (kBlockedChunks - 1)];
+    const int32_t st = ps.pfx[k0 + 1 + lane] - eb;  // >= 1: segment k0 holds eb
+    const uint32_t marks = __reduce_or_sync(0xffffffffu, st < 32 ? 1u << st : 0u);
+    const int k = k0 + __popc(marks & ((2u << lane) - 1u));
+    return ps.seg_q[k] + static_cast<uint32_t>(eb + lane - ps.pfx[k]);
+}
+
 // bfloat16 current (pA) -> 2^-12 pA, as the SNN_RECORD_PACKED_BF16 read-back
 __device__ __forceinline__ int32_t bf16_fx(uint32_t h)
 {
     return __float2int_rn(__fmul_rn(__uint_as_float((h & 0xFFFFu) << 16), 4096.0f));
 }
 
-// Quads [w0, w1) of the staged stream; qidx[e - w0] is quad e's index in the record
-// arrays: BLOCKED6 reads 8 bytes of records and 16 of int32 weights per quad, BLOCKED4
-// one 16-byte unit of records and bfloat16 weights.  The window is taken in sets of
+// Quads [w0, w1) of the staged stream, located through the pass's map: BLOCKED6 reads 8
+// bytes of records and 16 of int32 weights per quad, BLOCKED4 one 16-byte unit of
+// records and bfloat16 weights, BLOCKED8 32 bytes of (weight, record) pairs.  The window is taken in sets of
 // kBlockedRounds / 2 rounds, software-pipelined: the loads of the next set are in flight
 // while the current set's weights are added, so the record stream never drains inside
 // a window.
@@ -810,7 +890,7 @@ constexpr int kBlockedSet = kBlockedRounds / 2;  // rounds per pipelined set
 //   BLOCKED4: va = the 16-byte unit (records, then bfloat16 currents);
 //   BLOCKED8: va, vb = the 32-byte quad of (int32 weight, uint32 record) pairs.
 template <int FMT>
-__device__ __forceinline__ void blocked_load_set(const StepArgs &a, const uint32_t *qidx, int32_t w0, int32_t w1,
+__device__ __forceinline__ void blocked_load_set(const StepArgs &a, const BlockedPass &ps, int32_t w0, int32_t w1,
                                                  int32_t e0, uint4 (&va)[kBlockedSet], uint4 (&vb)[kBlockedSet])
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -819,29 +899,31 @@ __device__ __forceinline__ void blocked_load_set(const StepArgs &a, const uint32
     const uint4 *q16 = reinterpret_cast<const uint4 *>(a.blk_rec);
 #pragma unroll
     for (int k = 0; k < kBlockedSet; ++k) {
-        // round k of a set is quads e0 + 32 * (warp + kBlockedWarps * k) + lane: the warps
-        // of the CTA interleave, so that a window's rounds spread evenly over them
-        const int32_t e = e0 + 32 * (warp + kBlockedWarps * k) + lane;
+        // round k of a set is quads eb .. eb + 32, eb = e0 + 32 * (warp + kBlockedWarps * k):
+        // the warps of the CTA interleave, so that a window's rounds spread evenly over them
+        const int32_t eb = e0 + 32 * (warp + kBlockedWarps * k);
+        const int32_t e = eb + lane;
         va[k] = make_uint4(0, 0, 0, 0);
         vb[k] = make_uint4(0, 0, 0, 0);
-        if (FMT == SNN_RECORD_BLOCKED8) {
-            // the round's 32 quads as 64 16-byte halves, consecutive halves on consecutive
-            // lanes (so one load instruction reads whole lines of a segment): lane l takes
-            // halves l and 32 + l
+        if (BlockedCfg<FMT>::table) {
+            // BLOCKED8: the round's 32 quads as 64 16-byte halves, consecutive halves on
+            // consecutive lanes (so one load instruction reads whole lines of a segment):
+            // lane l takes halves l and 32 + l, of quads l / 2 and 16 + l / 2
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
-                const int32_t hq = 32 * j + lane;  // half within the round
-                const int32_t eq = e0 + 32 * (warp + kBlockedWarps * k) + (hq >> 1);
+                const int32_t eq = eb + 16 * j + (lane >> 1);
                 if (eq < w1) {
-                    const uint4 v = __ldcs(q16 + 2 * uint64_t(qidx[eq - w0]) + (hq & 1));
+                    const uint4 v = __ldcs(q16 + 2 * uint64_t(ps.qidx[eq - w0]) + (lane & 1));
                     if (j == 0) va[k] = v;
                     else vb[k] = v;
                 }
             }
             continue;
         }
+        if (eb >= w1) continue;  // the whole warp
+        const uint32_t qe = blocked_round_quad(ps, eb, lane);
         if (e < w1) {
-            const uint32_t q = qidx[e - w0];
+            const uint32_t q = qe;
             if (FMT == SNN_RECORD_BLOCKED4) {
                 va[k] = __ldcs(q16 + q);
             } else if (FMT == SNN_RECORD_BLOCKED8) {
@@ -894,23 +976,153 @@ __device__ __forceinline__ void blocked_apply_set(const StepArgs &a, int32_t *bi
 }
 
 template <bool kAggregate, int FMT, int kW>
-__device__ __forceinline__ void blocked_window(const StepArgs &a, int32_t *bins, const uint32_t *qidx, int32_t w0,
+__device__ __forceinline__ void blocked_window(const StepArgs &a, int32_t *bins, const BlockedPass &ps, int32_t w0,
                                                int32_t w1, int64_t t, int32_t base)
 {
     constexpr int32_t kStep = kBlockedThreads * kBlockedSet;
     uint4 aA[kBlockedSet], bA[kBlockedSet], aB[kBlockedSet], bB[kBlockedSet];
     int32_t e0 = w0;
-    blocked_load_set<FMT>(a, qidx, w0, w1, e0, aA, bA);
+    blocked_load_set<FMT>(a, ps, w0, w1, e0, aA, bA);
     for (;;) {
-        if (e0 + kStep < w1) blocked_load_set<FMT>(a, qidx, w0, w1, e0 + kStep, aB, bB);
+        if (e0 + kStep < w1) blocked_load_set<FMT>(a, ps, w0, w1, e0 + kStep, aB, bB);
         blocked_apply_set<kAggregate, FMT, kW>(a, bins, t, base, aA, bA);
         e0 += kStep;
         if (e0 >= w1) break;
-        if (e0 + kStep < w1) blocked_load_set<FMT>(a, qidx, w0, w1, e0 + kStep, aA, bA);
+        if (e0 + kStep < w1) blocked_load_set<FMT>(a, ps, w0, w1, e0 + kStep, aA, bA);
         blocked_apply_set<kAggregate, FMT, kW>(a, bins, t, base, aB, bB);
         e0 += kStep;
         if (e0 >= w1) break;
     }
+}
+
+// One pass of the table formats over senders spk[0 .. nb): every sender's segment (first
+// quad, quad count, prefix of the counts) in the staging tables, then per window of
+// kBlockedTableWindow quads the record-array index of every quad.
+template <int FMT, int kW>
+__device__ __forceinline__ void blocked_pass_table(const StepArgs &a, uint8_t *sm, int32_t *bins, const int32_t *spk,
+                                                   int nb, int p, bool aggregate, int64_t t, int32_t base)
+{
+    using SL = BlockedSmem<kW, FMT>;
+    constexpr int kPer = kBlockedBatch / kBlockedThreads;  // senders staged per thread
+    uint32_t *seg_q = reinterpret_cast<uint32_t *>(sm + SL::seg_q);   // [kBlockedBatch]
+    int32_t *pfx = reinterpret_cast<int32_t *>(sm + SL::pfx);         // [kBlockedBatch]
+    int32_t *seg_nq = reinterpret_cast<int32_t *>(sm + SL::nq);       // [kBlockedBatch]
+    int32_t *warp_sums = reinterpret_cast<int32_t *>(sm + SL::warp);  // [kBlockedWarps]
+    uint32_t *qidx = reinterpret_cast<uint32_t *>(sm + SL::index);    // [kBlockedTableWindow]
+    const int tid = threadIdx.x;
+    const int64_t stride = a.n_blocks + 1;
+    // thread tid stages senders tid * kPer .. + kPer (consecutive, for the scan)
+    int32_t mine = 0;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int j = tid * kPer + i;
+        int32_t nq = 0;
+        if (j < nb) {
+            const int32_t s = __ldcg(spk + j);
+            const uint16_t *sg = a.blk_seg + static_cast<int64_t>(s) * stride + p;
+            const int32_t o0 = __ldg(sg), o1 = __ldg(sg + 1);
+            seg_q[j] = static_cast<uint32_t>((__ldg(a.row_ptr + s) + o0) / kBlockQuad);
+            nq = (o1 - o0) / kBlockQuad;
+        }
+        seg_nq[j] = nq;
+        mine += nq;
+    }
+    // the window table is idle here: it holds the scan's per-thread output
+    int32_t *scan_out = reinterpret_cast<int32_t *>(qidx);
+    const int32_t total = block_exclusive_scan(mine, scan_out, warp_sums);
+    {
+        int32_t run = scan_out[tid];
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            pfx[tid * kPer + i] = run;
+            run += seg_nq[tid * kPer + i];
+        }
+    }
+    __syncthreads();
+    for (int32_t w0 = 0; w0 < total; w0 += kBlockedTableWindow) {
+        const int32_t w1 = total - w0 < kBlockedTableWindow ? total : w0 + kBlockedTableWindow;
+        // record-array index of every quad of the window
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int j = tid * kPer + i;
+            if (j >= nb) break;
+            const int32_t lo = max(pfx[j], w0), hi = min(pfx[j] + seg_nq[j], w1);
+            const uint32_t q0 = seg_q[j] - static_cast<uint32_t>(pfx[j]);
+            for (int32_t e = lo; e < hi; ++e) qidx[e - w0] = q0 + static_cast<uint32_t>(e);
+        }
+        __syncthreads();
+        const BlockedPass ps{seg_q, pfx, nullptr, qidx};
+        if (aggregate) blocked_window<true, FMT, kW>(a, bins, ps, w0, w1, t, base);
+        else blocked_window<false, FMT, kW>(a, bins, ps, w0, w1, t, base);
+        __syncthreads();  // the table is rebuilt for the next window
+    }
+}
+
+// One pass of the map formats over senders spk[0 .. nb): the nonempty segments, compacted
+// in sender order, then per window of kBlockedMapWindow quads the segment holding every
+// 32nd quad.
+template <int FMT, int kW>
+__device__ __forceinline__ void blocked_pass_map(const StepArgs &a, uint8_t *sm, int32_t *bins, const int32_t *spk,
+                                                 int nb, int p, bool aggregate, int64_t t, int32_t base)
+{
+    using SL = BlockedSmem<kW, FMT>;
+    constexpr int kPer = kBlockedBatch / kBlockedThreads;  // senders staged per thread
+    uint32_t *seg_q = reinterpret_cast<uint32_t *>(sm + SL::seg_q);  // [kBlockedBatch]
+    int32_t *pfx = reinterpret_cast<int32_t *>(sm + SL::pfx);        // [kBlockedBatch + 32]
+    int2 *warp_sums = reinterpret_cast<int2 *>(sm + SL::warp);       // [kBlockedWarps]
+    uint16_t *jmap = reinterpret_cast<uint16_t *>(sm + SL::index);   // [kBlockedChunks]
+    const int tid = threadIdx.x;
+    const int64_t stride = a.n_blocks + 1;
+    // thread tid stages senders tid * kPer .. + kPer (consecutive, for the scan)
+    uint32_t sq[kPer];
+    int32_t nq[kPer];
+    int2 mine = make_int2(0, 0);  // (quads, nonempty segments)
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int j = tid * kPer + i;
+        sq[i] = 0;
+        nq[i] = 0;
+        if (j < nb) {
+            const int32_t s = __ldcg(spk + j);
+            const uint16_t *sg = a.blk_seg + static_cast<int64_t>(s) * stride + p;
+            const int32_t o0 = __ldg(sg), o1 = __ldg(sg + 1);
+            sq[i] = static_cast<uint32_t>((__ldg(a.row_ptr + s) + o0) / kBlockQuad);
+            nq[i] = (o1 - o0) / kBlockQuad;
+        }
+        mine.x += nq[i];
+        mine.y += nq[i] > 0 ? 1 : 0;
+    }
+    int2 total;
+    const int2 at = block_exclusive_scan2(mine, warp_sums, total);
+    // the nonempty segments, in sender order (the scan's scratch is read by now)
+    {
+        int32_t run = at.x, k = at.y;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i)
+            if (nq[i] > 0) {
+                seg_q[k] = sq[i];
+                pfx[k] = run;
+                run += nq[i];
+                ++k;
+            }
+        if (tid < 32) pfx[total.y + tid] = INT32_MAX;  // past the last segment
+    }
+    for (int32_t w0 = 0; w0 < total.x; w0 += kBlockedMapWindow) {
+        const int32_t w1 = total.x - w0 < kBlockedMapWindow ? total.x : w0 + kBlockedMapWindow;
+        __syncthreads();  // the segments are written; the previous window's map is free
+        // the segment holding every 32nd quad of the window
+        for (int k = tid; k < total.y; k += kBlockedThreads) {
+            const int32_t lo = max(pfx[k], w0), hi = min(pfx[k + 1], w1);
+            constexpr int32_t kC = 1 << kBlockedChunkShift;
+            for (int32_t c = (lo - w0 + kC - 1) >> kBlockedChunkShift; w0 + (c << kBlockedChunkShift) < hi; ++c)
+                jmap[c] = static_cast<uint16_t>(k);
+        }
+        __syncthreads();
+        const BlockedPass ps{seg_q, pfx, jmap, nullptr};
+        if (aggregate) blocked_window<true, FMT, kW>(a, bins, ps, w0, w1, t, base);
+        else blocked_window<false, FMT, kW>(a, bins, ps, w0, w1, t, base);
+    }
+    __syncthreads();  // the segment tables are rewritten by the next pass
 }
 
 template <int FMT>
@@ -918,15 +1130,10 @@ __global__ void __launch_bounds__(kBlockedThreads, 1)
     k_deliver_blocked(const StepArgs a, const int32_t *list, int64_t n_list, int64_t t_list, int k)
 {
     constexpr int kW = kBlockMaxWidth;
-    using SL = BlockedSmem<kW>;
+    using CF = BlockedCfg<FMT>;
     extern __shared__ int4 smem4[];
     uint8_t *sm = reinterpret_cast<uint8_t *>(smem4);
-    int32_t *bins = reinterpret_cast<int32_t *>(sm);                       // [kBlockedBinDelays + 1][kW]
-    uint32_t *seg_q = reinterpret_cast<uint32_t *>(sm + SL::seg_q);        // [kBlockedBatch]
-    int32_t *pfx = reinterpret_cast<int32_t *>(sm + SL::pfx);              // [kBlockedBatch]
-    int32_t *seg_nq = reinterpret_cast<int32_t *>(sm + SL::nq);            // [kBlockedBatch]
-    int32_t *warp_sums = reinterpret_cast<int32_t *>(sm + SL::warp);       // [kBlockedWarps]
-    uint32_t *qidx = reinterpret_cast<uint32_t *>(sm + SL::qidx);          // [kBlockedWindow]
+    int32_t *bins = reinterpret_cast<int32_t *>(sm);  // [kBlockedBinDelays + 1][kW]
 
     int64_t t;
     const int32_t *spk;
@@ -952,58 +1159,14 @@ __global__ void __launch_bounds__(kBlockedThreads, 1)
     const int32_t width = a.blk_off[p + 1] - base;
     const bool aggregate = nspk >= kBlockedAggregateMin;
     const int tid = threadIdx.x;
-    const int64_t stride = a.n_blocks + 1;
-    constexpr int kPer = kBlockedBatch / kBlockedThreads;  // senders staged per thread
 
     if (aggregate)
         for (int j = tid; j < (kBlockedBinDelays + 1) * kW / 4; j += kBlockedThreads) smem4[j] = make_int4(0, 0, 0, 0);
 
     for (int64_t b0 = 0; b0 < nspk; b0 += kBlockedBatch) {
         const int nb = static_cast<int>(nspk - b0 < kBlockedBatch ? nspk - b0 : kBlockedBatch);
-        // thread tid stages senders tid * kPer .. + kPer (consecutive, for the scan)
-        int32_t mine = 0;
-#pragma unroll
-        for (int i = 0; i < kPer; ++i) {
-            const int j = tid * kPer + i;
-            int32_t nq = 0;
-            if (j < nb) {
-                const int32_t s = __ldcg(spk + b0 + j);
-                const uint16_t *sg = a.blk_seg + static_cast<int64_t>(s) * stride + p;
-                const int32_t o0 = __ldg(sg), o1 = __ldg(sg + 1);
-                seg_q[j] = static_cast<uint32_t>((__ldg(a.row_ptr + s) + o0) / kBlockQuad);
-                nq = (o1 - o0) / kBlockQuad;
-            }
-            seg_nq[j] = nq;
-            mine += nq;
-        }
-        // the window table is idle here: it holds the scan's per-thread output
-        int32_t *scan_out = reinterpret_cast<int32_t *>(qidx);
-        const int32_t total = block_exclusive_scan(mine, scan_out, warp_sums);
-        {
-            int32_t run = scan_out[tid];
-#pragma unroll
-            for (int i = 0; i < kPer; ++i) {
-                pfx[tid * kPer + i] = run;
-                run += seg_nq[tid * kPer + i];
-            }
-        }
-        __syncthreads();
-        for (int32_t w0 = 0; w0 < total; w0 += kBlockedWindow) {
-            const int32_t w1 = total - w0 < kBlockedWindow ? total : w0 + kBlockedWindow;
-            // record-array index of every quad of the window
-#pragma unroll
-            for (int i = 0; i < kPer; ++i) {
-                const int j = tid * kPer + i;
-                if (j >= nb) break;
-                const int32_t lo = max(pfx[j], w0), hi = min(pfx[j] + seg_nq[j], w1);
-                const uint32_t q0 = seg_q[j] - static_cast<uint32_t>(pfx[j]);
-                for (int32_t e = lo; e < hi; ++e) qidx[e - w0] = q0 + static_cast<uint32_t>(e);
-            }
-            __syncthreads();
-            if (aggregate) blocked_window<true, FMT, kW>(a, bins, qidx, w0, w1, t, base);
-            else blocked_window<false, FMT, kW>(a, bins, qidx, w0, w1, t, base);
-            __syncthreads();  // the table is rebuilt for the next window
-        }
+        if (CF::table) blocked_pass_table<FMT, kW>(a, sm, bins, spk + b0, nb, p, aggregate, t, base);
+        else blocked_pass_map<FMT, kW>(a, sm, bins, spk + b0, nb, p, aggregate, t, base);
     }
     if (!aggregate) return;
     // add the sums of delays 1..kBlockedBinDelays to their ring rows; width is a multiple
@@ -1086,15 +1249,15 @@ void launch_deliver_list(const StepArgs &a, const int32_t *list, int64_t n, int6
 
 int prepare_blocked_kernel()
 {
-    const int bytes = static_cast<int>(kBlockedSmemBytes);
     cudaError_t e = cudaFuncSetAttribute(k_deliver_blocked<SNN_RECORD_BLOCKED6>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(blocked_smem_bytes<SNN_RECORD_BLOCKED6>()));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_deliver_blocked<SNN_RECORD_BLOCKED4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 bytes);
+                                 static_cast<int>(blocked_smem_bytes<SNN_RECORD_BLOCKED4>()));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_deliver_blocked<SNN_RECORD_BLOCKED8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 bytes);
+                                 static_cast<int>(blocked_smem_bytes<SNN_RECORD_BLOCKED8>()));
     return static_cast<int>(e);
 }
 
@@ -1102,11 +1265,11 @@ void launch_deliver_blocked(const StepArgs &a, const int32_t *list, int64_t n, i
 {
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (a.format == SNN_RECORD_BLOCKED4)
-        k_deliver_blocked<SNN_RECORD_BLOCKED4><<<a.n_blocks, kBlockedThreads, kBlockedSmemBytes, st>>>(a, list, n, t, k);
+        k_deliver_blocked<SNN_RECORD_BLOCKED4><<<a.n_blocks, kBlockedThreads, blocked_smem_bytes<SNN_RECORD_BLOCKED4>(), st>>>(a, list, n, t, k);
     else if (a.format == SNN_RECORD_BLOCKED8)
-        k_deliver_blocked<SNN_RECORD_BLOCKED8><<<a.n_blocks, kBlockedThreads, kBlockedSmemBytes, st>>>(a, list, n, t, k);
+        k_deliver_blocked<SNN_RECORD_BLOCKED8><<<a.n_blocks, kBlockedThreads, blocked_smem_bytes<SNN_RECORD_BLOCKED8>(), st>>>(a, list, n, t, k);
     else
-        k_deliver_blocked<SNN_RECORD_BLOCKED6><<<a.n_blocks, kBlockedThreads, kBlockedSmemBytes, st>>>(a, list, n, t, k);
+        k_deliver_blocked<SNN_RECORD_BLOCKED6><<<a.n_blocks, kBlockedThreads, blocked_smem_bytes<SNN_RECORD_BLOCKED6>(), st>>>(a, list, n, t, k);
 }
 
 int deliver_list_blocks_per_sm()

@@ -892,6 +892,42 @@ def test_blocked_deliver_spikes_matches_oracle_network(model, tiny, nspk, fmt):
     net.close()
 
 
+@pytest.mark.parametrize("fmt", [BLK, snn.RECORD_BLOCKED4, snn.RECORD_BLOCKED8])
+def test_blocked_deliver_spikes_beyond_one_map_window(model, fmt):
+    """A target block whose segments in one 2,048-sender pass hold more quads than the
+    kernel maps at once (32,768): every sender has 80 synapses into targets 0..31 (one
+    block that the cut cannot narrow), every other sender a few more elsewhere, so that
+    other blocks see empty segments between nonempty ones; repeated senders, two passes."""
+    m = model
+    rng = np.random.default_rng(77)
+    n = 2600
+    pre, post, w, d = [], [], [], []
+    for s in range(n):
+        L = 80 + (s % 7)
+        pre += [s] * L
+        post += list(rng.integers(0, 32, L))
+        if s % 2 == 0:
+            pre += [s] * 5
+            post += list(rng.integers(1000, n, 5))
+    k = len(pre)
+    w = list(rng.integers(-200_000, 300_000, k))
+    d = list(rng.integers(1, 64, k))
+    u0 = rng.uniform(0, 10, n).astype(np.float32)
+    custom = dict(pre=pre, post=post, w_fx=w, delay=d, u0=u0, pop_offsets=[0, 325, 650, 975, 1300, 1625, 1950, 2275, n])
+    onet = oracle.network_from_edges(n, pre, post, w, d, u0, custom["pop_offsets"])
+    if fmt == snn.RECORD_BLOCKED4:
+        onet = oracle.with_weights(onet, oracle.quantize_bf16(onet.w_fx))
+    net = snn.Network(m, custom=custom, record_format=fmt)
+    spikers = rng.integers(0, n, 3000).astype(np.int32)
+    t = 5
+    net.deliver_spikes(torch.from_numpy(spikers).cuda(), t)
+    torch.cuda.synchronize()
+    npad = int(net.layout().n_neurons_padded)
+    ring = net.device_view("ring", torch.int32, 64 * npad).cpu().numpy().reshape(64, npad).astype(np.int64)
+    assert np.array_equal(ring, _expected_ring(onet, spikers, t, npad))
+    net.close()
+
+
 @pytest.mark.parametrize("n", [1, 13, 517, 2000])
 def test_blocked_ragged_counts_no_synapses(n):
     """No synapses (blocks cut by width alone: 768, 768, 464 for 2,000 neurons)."""
