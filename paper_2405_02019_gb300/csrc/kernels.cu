@@ -729,14 +729,13 @@ constexpr int kBlockedWarps = kBlockedThreads / 32;
 constexpr int kBlockedMapWindow = 32768;     // quads of a pass mapped to their segments at once
 constexpr int kBlockedChunkShift = 5;        // the map gives the segment of every 32nd quad (a round's first)
 constexpr int kBlockedChunks = kBlockedMapWindow >> kBlockedChunkShift;  // map entries per window
-constexpr int kBlockedTableWindow = 8192;    // quads of a pass whose record-array index is tabled at once
 // How a format locates a window's quads: BLOCKED8 (two 16-byte loads per quad, on
 // consecutive lanes) through a table of every quad's record-array index, the others
 // through the map of segments per round (measured faster for each).
 template <int FMT>
 struct BlockedCfg {
     static constexpr bool table = FMT == SNN_RECORD_BLOCKED8;
-    static constexpr size_t index_bytes = table ? sizeof(uint32_t) * kBlockedTableWindow
+    static constexpr size_t index_bytes = table ? sizeof(uint32_t) * kBlockedWindow
                                                 : sizeof(uint16_t) * kBlockedChunks;
 };
 // Table formats stage every sender (empty segments too) with its quad count; map formats
@@ -997,7 +996,7 @@ __device__ __forceinline__ void blocked_window(const StepArgs &a, int32_t *bins,
 
 // One pass of the table formats over senders spk[0 .. nb): every sender's segment (first
 // quad, quad count, prefix of the counts) in the staging tables, then per window of
-// kBlockedTableWindow quads the record-array index of every quad.
+// kBlockedWindow quads the record-array index of every quad.
 template <int FMT, int kW>
 __device__ __forceinline__ void blocked_pass_table(const StepArgs &a, uint8_t *sm, int32_t *bins, const int32_t *spk,
                                                    int nb, int p, bool aggregate, int64_t t, int32_t base)
@@ -1008,7 +1007,7 @@ __device__ __forceinline__ void blocked_pass_table(const StepArgs &a, uint8_t *s
     int32_t *pfx = reinterpret_cast<int32_t *>(sm + SL::pfx);         // [kBlockedBatch]
     int32_t *seg_nq = reinterpret_cast<int32_t *>(sm + SL::nq);       // [kBlockedBatch]
     int32_t *warp_sums = reinterpret_cast<int32_t *>(sm + SL::warp);  // [kBlockedWarps]
-    uint32_t *qidx = reinterpret_cast<uint32_t *>(sm + SL::index);    // [kBlockedTableWindow]
+    uint32_t *qidx = reinterpret_cast<uint32_t *>(sm + SL::index);    // [kBlockedWindow]
     const int tid = threadIdx.x;
     const int64_t stride = a.n_blocks + 1;
     // thread tid stages senders tid * kPer .. + kPer (consecutive, for the scan)
@@ -1039,8 +1038,8 @@ __device__ __forceinline__ void blocked_pass_table(const StepArgs &a, uint8_t *s
         }
     }
     __syncthreads();
-    for (int32_t w0 = 0; w0 < total; w0 += kBlockedTableWindow) {
-        const int32_t w1 = total - w0 < kBlockedTableWindow ? total : w0 + kBlockedTableWindow;
+    for (int32_t w0 = 0; w0 < total; w0 += kBlockedWindow) {
+        const int32_t w1 = total - w0 < kBlockedWindow ? total : w0 + kBlockedWindow;
         // record-array index of every quad of the window
 #pragma unroll
         for (int i = 0; i < kPer; ++i) {
